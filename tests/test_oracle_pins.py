@@ -1,0 +1,433 @@
+"""Pins of the FP64 oracle against what the paper and the mathematics fix.
+
+Each test names the passage it pins.  None of them retypes the oracle's
+formula: they use closed forms (cos^N, the Gaussian, the normalised blur of
+scipy.ndimage), exact rational arithmetic (math.comb / Fraction), values
+the paper prints (tests/golden/), invariants (shift, scale, transpose,
+flip, Prop. 2.1) and brute force on tiny images (two independent
+formulations that must agree).
+"""
+from fractions import Fraction
+from math import comb, pi, sqrt, log, exp
+
+import numpy as np
+import pytest
+from scipy import ndimage
+
+import oracle
+from conftest import golden
+from paper_1203_5128_gb300 import synth
+
+
+# ------------------------------------------------------------------ helpers
+
+def exact_tail(N, j):
+    """sum_{n=0}^{j} C(N, n) / 2^N as an exact rational."""
+    if j < 0:
+        return Fraction(0)
+    return Fraction(sum(comb(N, n) for n in range(min(j, N) + 1)), 2 ** N)
+
+
+def small_image(H, W, seed):
+    return synth.g8(H, W, seed).astype(np.float64)
+
+
+# ------------------------------------------------------------------ P1
+@pytest.mark.parametrize("N", [1, 2, 7, 30, 264, 1053, 4096])
+def test_p1_binomial_expansion_equals_raised_cosine(N):
+    """eq. (expansion): sum_n 2^-N C(N,n) cos((2n-N) s / (sqrt(N) sigma_r))
+    equals cos(s / (sqrt(N) sigma_r))^N (the de Moivre power of cos)."""
+    sr = 10.0
+    smax = 0.5 * pi * sqrt(N) * sr
+    s = np.linspace(-smax, smax, 2001)
+    lhs = oracle.phi(s, N, 0, sr)
+    rhs = np.cos(s / (sqrt(N) * sr)) ** N
+    # each term's phase reaches N*pi/2 and carries a rounding of that size
+    tol = 1e-12 + 4 * (N * pi / 2) * 2.0 ** -53
+    assert np.max(np.abs(lhs - rhs)) < tol
+
+
+def test_p1_weights_match_exact_binomials():
+    """The log-domain weights are 2^-N C(N, n) (eq. (expansion))."""
+    for N in [1, 5, 64, 263, 1000]:
+        w = np.exp(oracle.log_weights(N))
+        for n in range(0, N + 1, max(1, N // 37)):
+            ex = Fraction(comb(N, n), 2 ** N)
+            if ex == 0:
+                continue
+            assert abs(w[n] - float(ex)) <= 1e-12 * float(ex)
+
+
+# ------------------------------------------------------------------ P2
+def test_p2_gaussian_limit():
+    """eq. (RCconv): cos(s/(sqrt(N) sigma_r))^N -> exp(-s^2/(2 sigma_r^2));
+    the sup error on [-T, T] falls as N grows, roughly like 1/N."""
+    sr, T = 10.0, 255.0
+    s = np.linspace(-T, T, 4001)
+    g = np.exp(-s ** 2 / (2 * sr ** 2))
+    errs = []
+    for N in [264, 528, 1056, 2112]:
+        errs.append(np.max(np.abs(oracle.phi(s, N, 0, sr) - g)))
+    assert all(b < a for a, b in zip(errs, errs[1:]))
+    for N, e in zip([264, 528, 1056, 2112], errs):
+        assert e * N < 0.5          # O(1/N) with a modest constant
+    assert errs[-1] < 2e-4
+
+
+# ------------------------------------------------------------------ P3
+@pytest.mark.parametrize("T,sr", [(255.0, 10.0), (255.0, 30.0), (200.0, 5.0),
+                                  (65535.0, 2000.0), (37.5, 11.0), (255.0, 100.0)])
+def test_p3_positive_monotone_at_n0(T, sr):
+    """Sec. 1.3: N >= N0 = 4T^2/(pi^2 sigma_r^2) keeps the argument of the
+    raised cosine in [-pi/2, pi/2], hence phi >= 0 and non-increasing on
+    [0, T]; one order less leaves that interval."""
+    N = oracle.order(T, sr)
+    assert T / (sqrt(N) * sr) <= pi / 2 + 1e-15
+    s = np.linspace(0.0, T, 4001)
+    ph = oracle.phi(s, N, 0, sr)
+    assert np.all(ph >= -1e-13)
+    assert np.all(np.diff(ph) <= 1e-13)
+    if N > 1:
+        assert T / (sqrt(N - 1) * sr) > pi / 2
+
+
+def test_p3_order_fails_below_threshold():
+    """One order below N0, cos^N leaves [-pi/2, pi/2] inside [0, T]: for even
+    N it turns back up (not monotone), for odd N it turns negative."""
+    for T, sr in [(255.0, 30.0), (255.0, 20.0)]:
+        N = oracle.order(T, sr) - 1
+        s = np.linspace(0.0, T, 20001)
+        ph = oracle.phi(s, N, 0, sr)
+        assert np.any(np.diff(ph) > 0) or np.any(ph < 0)
+
+
+# ------------------------------------------------------------------ P4
+def test_p4_table1():
+    """Table 1 (Sec. 1.3): N0 for T = 255.  The table rounds 0.405 (T/sigma_r)^2;
+    the oracle's N = ceil(4T^2/(pi^2 sigma_r^2)) is the table value or one
+    two more: ceil adds up to one and 4/pi^2 = 0.40528 exceeds 0.405 by
+    2.8e-4 (T/sigma_r)^2, 0.73 at sigma_r = 5."""
+    for sr, n0 in golden("table1_n0.txt"):
+        sr, n0 = float(sr), int(n0)
+        assert round(0.405 * (255.0 / sr) ** 2) == n0
+        N = oracle.order(255.0, sr)
+        slack = (4.0 / pi ** 2 - 0.405) * (255.0 / sr) ** 2
+        assert 0 <= N - n0 <= 1.5 + slack
+        assert abs(oracle.n0(255.0, sr) - n0) < 0.5 + slack
+
+
+# ------------------------------------------------------------------ P5
+@pytest.mark.parametrize("N", [1, 2, 3, 10, 29, 66, 119, 184, 263, 264, 436, 1053])
+@pytest.mark.parametrize("eps", [1e-1, 5e-2, 1e-2, 5e-3, 1e-3])
+def test_p5_trunc_rule_exact(N, eps):
+    """eq. (trunc): M is the smallest index with sum_{n<=M+1} w_n > eps/2;
+    then the dropped mass 2 sum_{n<M} w_n <= eps (the bound after eq. (approx))."""
+    M = oracle.trunc_m(N, eps)
+    e = Fraction(eps)
+    assert exact_tail(N, M + 1) > e / 2 or M == N // 2
+    if M > 0:
+        assert not exact_tail(N, M) > e / 2
+    assert 2 * exact_tail(N, M - 1) <= e
+
+
+@pytest.mark.parametrize("N,eps", [(263, 0.005), (264, 0.01), (66, 0.01), (436, 0.05)])
+def test_p5_truncated_kernel_within_eps(N, eps):
+    """|phi(s) - phi_eps(s)| <= eps for all s (Sec. 3, after eq. (approx))."""
+    sr = 10.0
+    M = oracle.trunc_m(N, eps)
+    s = np.linspace(-600.0, 600.0, 6001)
+    d = np.abs(oracle.phi(s, N, 0, sr) - oracle.phi(s, N, M, sr))
+    assert d.max() <= eps
+
+
+def test_p5_table3_and_fig1():
+    """Table 3 (Sec. 3): N - 2M = 43, 36, 29 at sigma_r = 10, 12, 15 from the
+    printed N0 (263, 184, 119) under eq. (trunc) with eps = 0.01 (the
+    printed 0.05 does not reproduce the row).  Fig. 1: N = 263, eps = 0.005
+    gives M = 108 under eq. (trunc); the caption's 111 (42 kept terms) is
+    the per-side reading sum_{n<M} w_n <= eps, which is checked exactly."""
+    rows = {float(r[0]): (int(r[1]), int(r[2])) for r in golden("table3_truncation.txt")}
+    for sr in (10.0, 12.0, 15.0):
+        before, after = rows[sr]
+        M = oracle.trunc_m(before, 0.01)
+        assert before - 2 * M == after
+    fig = {r[0]: r[1] for r in golden("fig1_caption.txt")}
+    N, eps = int(fig["N"]), float(fig["eps"])
+    assert oracle.trunc_m(N, eps) == 108
+    M_side = max(m for m in range(N // 2 + 1) if exact_tail(N, m - 1) <= Fraction(fig["eps"]))
+    assert M_side == int(fig["M_printed"])
+    assert N - 2 * M_side + 1 == int(fig["kept_printed"])
+
+
+# ------------------------------------------------------------------ P6
+def test_p6_chernoff_bound_holds():
+    """Sec. 3: sum_{n<=M} 2^-N C(N,n) <= exp(-(N-2M)^2/(4N)) (a valid, loose
+    form of the Chernoff/Hoeffding bound), and the M of eq. (Chernoff)
+    keeps the tail below eps/2."""
+    for N in [10, 50, 101, 264, 436, 1053]:
+        for M in range(0, N // 2 + 1, max(1, N // 23)):
+            assert float(exact_tail(N, M)) <= exp(-(N - 2 * M) ** 2 / (4.0 * N)) * (1 + 1e-12)
+        for eps in [0.1, 0.01, 0.001]:
+            M = oracle.chernoff_m(N, eps)
+            assert exact_tail(N, M) <= Fraction(eps) / 2 or M == 0
+            m_real = 0.5 * (N - sqrt(4 * N * log(2 / eps)))
+            assert M == max(0, min(N // 2, int(np.floor(m_real))))
+
+
+def test_p6_fig9_order_jump():
+    """Fig. 9: under Algorithm 2 the effective order N - 2M jumps up as sigma_r
+    drops to 10, where rule (c) (Chernoff) replaces rule (b) (eq. (trunc))."""
+    eps = 0.01
+    k = {}
+    for sr in [9.5, 10.0, 10.01, 10.5, 12.0]:
+        N = oracle.order(255.0, sr)
+        M = oracle.alg2_m(N, sr, eps)
+        k[sr] = N - 2 * M
+    assert k[10.0] > 1.5 * k[10.01]
+    assert k[9.5] > k[10.0] > k[10.01] > k[10.5] > k[12.0]
+    # the bands of Algorithm 2
+    assert oracle.alg2_m(300, 41.0, eps) == 0
+    assert oracle.alg2_m(300, 40.0, eps) == oracle.trunc_m(300, eps)
+    assert oracle.alg2_m(300, 10.0, eps) == oracle.chernoff_m(300, eps)
+    # 16-bit images compare sigma_r on the 8-bit scale
+    assert oracle.alg2_m(436, 2000.0, eps, 65535.0) == oracle.chernoff_m(436, eps)
+
+
+# ------------------------------------------------------------------ P7
+def test_p7_coefficient_facts():
+    """Sec. 3: weights positive, sum to one, smallest 2^-N, largest
+    ~ sqrt(2/(pi N)) (Stirling).  The printed smallest/largest ratio
+    (pi N 2^(2N-1))^(-1/2) equals 2^-N sqrt(2/(pi N)), the product of the two;
+    the ratio itself is 2^-N sqrt(pi N / 2), which is what is pinned here."""
+    prev = None
+    for N in [16, 64, 256, 1024, 4096]:
+        lw = oracle.log_weights(N)
+        w = np.exp(lw)
+        assert np.all(np.isfinite(lw))   # positive; 2^-N underflows FP64 past N = 1074
+        # log weights are differences of lgamma values of size N log N
+        tol = 1e-13 + 4 * N * log(N) * 2.0 ** -52
+        assert abs(np.sum(w) - 1.0) < tol
+        assert abs(lw[0] + N * log(2.0)) < 1e-9 and abs(lw[N] + N * log(2.0)) < 1e-9
+        rel = abs(w.max() / sqrt(2.0 / (pi * N)) - 1.0)
+        log_ratio = lw[0] - lw[N // 2]
+        rel2 = abs(log_ratio - (-N * log(2.0) + 0.5 * log(pi * N / 2.0)))
+        printed = -0.5 * (log(pi * N) + (2 * N - 1) * log(2.0))
+        assert abs(log_ratio - printed - log(pi * N / 2.0)) < 0.5 / N   # Stirling O(1/N)
+        if prev is not None:
+            assert rel < prev[0] and rel2 < prev[1]
+        prev = (rel, rel2)
+    assert prev[0] < 1e-4 and prev[1] < 1e-4
+
+
+# ------------------------------------------------------------------ P8
+def _fixed(f, sigma_s, sr, eps, T, rule="alg2", vr=255.0):
+    return oracle.resolve(f, sigma_s, sr, eps, t_mode="fixed", t_fixed=T, rule=rule,
+                          value_range=vr)
+
+
+def test_p8_shift_and_scale_covariance():
+    """The filter commutes with f -> f + c and with (f, sigma_r, T) ->
+    (a f, a sigma_r, a T) (N unchanged since T/sigma_r is unchanged)."""
+    f = small_image(19, 23, 11)
+    p = _fixed(f, 1.7, 25.0, 0.01, 255.0)
+    base = oracle.shiftable(f, 1.7, 25.0, p)
+    sh = oracle.shiftable(f + 1000.0, 1.7, 25.0, p)
+    assert np.max(np.abs(sh - 1000.0 - base)) < 1e-8
+    a = 3.5
+    p2 = _fixed(a * f, 1.7, a * 25.0, 0.01, a * 255.0, vr=a * 255.0)
+    assert np.array_equal(p2.N, p.N) and np.array_equal(p2.M, p.M)
+    sc = oracle.shiftable(a * f, 1.7, a * 25.0, p2)
+    assert np.max(np.abs(sc / a - base)) < 1e-9
+
+
+def test_p8_transpose_and_flip():
+    f = small_image(17, 29, 12)
+    p = _fixed(f, 2.2, 30.0, 0.0, 255.0)
+    base = oracle.shiftable(f, 2.2, 30.0, p)
+    assert np.max(np.abs(oracle.shiftable(f.T.copy(), 2.2, 30.0, p) - base.T)) < 1e-9
+    assert np.max(np.abs(oracle.shiftable(f[::-1].copy(), 2.2, 30.0, p) - base[::-1])) < 1e-9
+    assert np.max(np.abs(oracle.shiftable(f[:, ::-1].copy(), 2.2, 30.0, p) - base[:, ::-1])) < 1e-9
+
+
+# ------------------------------------------------------------------ P9
+def test_p9_constant_image():
+    """A constant image passes through unchanged; its exact T is 0 (eq.
+    (bound)) and the order drops to N = 1."""
+    f = np.full((13, 21), 77.25)
+    p = oracle.resolve(f, 3.0, 10.0, 0.01, t_mode="global")
+    assert float(p.T[0, 0]) == 0.0 and int(p.N[0, 0]) == 1
+    out = oracle.shiftable(f, 3.0, 10.0, p)
+    assert np.max(np.abs(out - 77.25)) < 1e-12
+    pt = oracle.resolve(f, 3.0, 10.0, 0.01, t_mode="tile", t_tile=8)
+    assert np.max(np.abs(oracle.shiftable(f, 3.0, 10.0, pt) - 77.25)) < 1e-12
+
+
+# ------------------------------------------------------------------ P10
+@pytest.mark.parametrize("shape,sigma_s", [((31, 40), 2.0), ((20, 9), 1.3)])
+def test_p10_large_sigma_r_is_normalised_blur(shape, sigma_s):
+    """sigma_r -> infinity: the range kernel tends to 1 and eq. (BF) becomes
+    the Gaussian blur normalised by the blur of the indicator of the image,
+    computed here with scipy.ndimage (zero padding outside the image)."""
+    f = small_image(*shape, seed=5)
+    sr = 1e6
+    p = _fixed(f, sigma_s, sr, 0.0, 255.0)
+    out = oracle.shiftable(f, sigma_s, sr, p)
+    R = oracle.radius(sigma_s)
+    k = np.exp(-np.arange(-R, R + 1) ** 2 / (2 * sigma_s ** 2))
+    def blur(x):
+        x = ndimage.correlate1d(x, k, axis=1, mode="constant", cval=0.0)
+        return ndimage.correlate1d(x, k, axis=0, mode="constant", cval=0.0)
+    ref = blur(f) / blur(np.ones_like(f))
+    assert np.max(np.abs(out - ref)) < 1e-4
+    dg = oracle.direct(f, sigma_s, sr, gauss=True)
+    assert np.max(np.abs(dg - ref)) < 1e-4
+
+
+# ------------------------------------------------------------------ P11
+CASES = [
+    # H, W, sigma_s, sigma_r, eps, t_mode, rule, tile
+    (16, 16, 1.0, 20.0, 0.0, "fixed", "alg2", 64),
+    (16, 16, 2.0, 12.0, 0.01, "global", "alg2", 64),
+    (23, 37, 1.5, 8.0, 0.01, "global", "chernoff", 64),
+    (23, 37, 1.2, 30.0, 0.05, "tile", "trunc", 8),
+    (40, 17, 0.9, 50.0, 0.01, "tile", "alg2", 16),
+    (64, 64, 2.5, 15.0, 0.01, "global", "trunc", 64),
+]
+
+
+@pytest.mark.parametrize("case", CASES)
+def test_p11_shiftable_equals_direct_phi(case):
+    """Sec. 1.2: with phi_eps as the range kernel, SHIFTABLE-BF (modulate,
+    filter, demodulate) is an exact rewriting of the direct sum of eq. (BF);
+    the two independent formulations agree to rounding."""
+    H, W, ss, sr, eps, mode, rule, tile = case
+    f = small_image(H, W, seed=H * 31 + W)
+    p = oracle.resolve(f, ss, sr, eps, t_mode=mode, rule=rule, t_tile=tile)
+    a, num_a, den_a, _ = oracle.shiftable(f, ss, sr, p, return_parts=True)
+    b, num_b, den_b, _ = oracle.direct(f, ss, sr, p, return_parts=True)
+    assert np.max(np.abs(den_a - den_b) / np.abs(den_b).max()) < 1e-10
+    assert np.max(np.abs(num_a - num_b) / np.abs(num_b).max()) < 1e-10
+    assert np.max(np.abs(a - b)) < 1e-8 * 255
+
+
+def test_p11_points_subset_matches_image():
+    f = small_image(30, 30, 3)
+    p = oracle.resolve(f, 2.0, 20.0, 0.01, t_mode="tile", t_tile=16)
+    full = oracle.direct(f, 2.0, 20.0, p)
+    ys = np.array([0, 5, 29, 17, 16, 15])
+    xs = np.array([0, 29, 3, 16, 15, 16])
+    pts = oracle.direct(f, 2.0, 20.0, p, points=(ys, xs))
+    assert np.array_equal(pts, full[ys, xs])
+
+
+# ------------------------------------------------------------------ P12
+@pytest.mark.parametrize("H,W,R", [(16, 16, 1), (23, 37, 2), (37, 23, 5), (9, 50, 9),
+                                   (5, 7, 12), (1, 40, 3), (40, 1, 3), (64, 48, 15)])
+def test_p12_max_filter(H, W, R):
+    """Prop. MAX-FILTER and Appendix: the van Herk / Gil-Werman filter equals
+    the brute-force windowed max (and min) exactly, with about three max
+    operations per point independent of R; Prop. 2.1 (sign corrected, the
+    printed T = max_x [f - max f] is <= 0): max_x (M - f) == max_x (f - m)."""
+    f = np.random.default_rng(H * 100 + W + R).uniform(0, 255, (H, W))
+    f[H // 2, :] = 255.0     # ties and flat runs
+    Mb, mb = oracle.maxmin_brute(f, R)
+    Mv, mv, ops = oracle.maxmin_vhgw(f, R)
+    assert np.array_equal(Mb, Mv) and np.array_equal(mb, mv)
+    Wn = 2 * R + 1
+    padded_rows = -(-(W + 2 * R) // Wn) * Wn
+    padded_cols = -(-(H + 2 * R) // Wn) * Wn
+    per_point_bound = 2 * (2 * (H * padded_rows + W * padded_cols) + 2 * H * W)
+    assert ops <= per_point_bound
+    if H * W > 1:
+        assert np.max(Mv - f) == np.max(f - mv)
+
+
+def test_p12_three_ops_per_point():
+    """Appendix: the 1-D MAX-FILTER takes at most 3 max operations per point
+    (2 for the running maxima, 1 to combine), whatever the window size."""
+    for R in [1, 4, 20]:
+        H, W = 1, 105 * (2 * R + 1) - 2 * R   # padded row length is a multiple of 2R+1
+        f = np.random.default_rng(R).uniform(0, 1, (H, W))
+        _, _, ops = oracle.maxmin_vhgw(f, R)
+        # per filter: the rows (one of length W) plus W columns of length 1,
+        # each padded to one window (2 * 2R running maxima + 1 combine)
+        row_ops = ops / 2 - W * (4 * R + 1)
+        assert 2.0 < row_ops / W <= 3.0
+
+
+def test_p12_t_modes():
+    """eq. (bound): T is the largest |f(x-y) - f(x)| over the window; the
+    per-tile T of every tile is at most the global T and their max is it."""
+    f = small_image(50, 70, 9)
+    R = 4
+    Tg = oracle.t_global(f, R)
+    Tt = oracle.t_tiles(f, R, 16, 16)
+    assert Tt.max() == Tg
+    brute = 0.0
+    for i in range(50):
+        for j in range(70):
+            win = f[max(0, i - R):i + R + 1, max(0, j - R):j + R + 1]
+            brute = max(brute, np.max(np.abs(win - f[i, j])))
+    assert Tg == np.float32(brute)
+
+
+# ------------------------------------------------------------------ P13 (reported)
+def test_p13_direct_vs_shiftable_reported(capsys):
+    """Not pinned by the paper (its images are missing): the divergence of
+    the truncated shiftable filter from the direct Gaussian filter shrinks
+    as eps -> 0 and is reported."""
+    f = small_image(40, 40, 21)
+    ss, sr = 2.0, 20.0
+    ref = oracle.direct(f, ss, sr, gauss=True)
+    d = {}
+    for eps in [0.05, 0.01, 0.0]:
+        p = oracle.resolve(f, ss, sr, eps, t_mode="global", rule="trunc")
+        d[eps] = np.max(np.abs(oracle.shiftable(f, ss, sr, p) - ref))
+    print("max |shiftable - direct gaussian| by eps:", d)
+    assert d[0.0] <= d[0.05] + 1e-9
+    assert d[0.0] < 2.0
+
+
+# ------------------------------------------------------------------ P14
+@pytest.mark.parametrize("mode", ["fixed", "global"])
+def test_p14_gradient_forms_and_fd(mode):
+    """Gradient of L = sum u * out (T, N, M fixed): the shiftable form equals
+    the direct-form derivative, and both match central finite differences
+    (h = 1e-3, FP64) of the oracle forward."""
+    f = small_image(14, 17, 8)
+    ss, sr, eps = 1.3, 25.0, 0.01
+    p = oracle.resolve(f, ss, sr, eps, t_mode=mode)
+    u = np.random.default_rng(1).normal(size=f.shape)
+    gs = oracle.grad_shiftable(f, u, ss, sr, p)
+    gd = oracle.grad_direct(f, u, ss, sr, p)
+    scale = np.max(np.abs(gd))
+    assert np.max(np.abs(gs - gd)) < 1e-9 * scale
+    h = 1e-3
+    rng = np.random.default_rng(2)
+    for _ in range(6):
+        i, j = rng.integers(0, 14), rng.integers(0, 17)
+        fp, fm = f.copy(), f.copy()
+        fp[i, j] += h
+        fm[i, j] -= h
+        Lp = np.sum(u * oracle.shiftable(fp, ss, sr, p))
+        Lm = np.sum(u * oracle.shiftable(fm, ss, sr, p))
+        fd = (Lp - Lm) / (2 * h)
+        assert abs(fd - gs[i, j]) < 1e-6 * scale + 1e-6 * abs(fd)
+
+
+def test_p14_gradient_per_tile():
+    """Per-tile kernels: the gradient sums each block's contribution; checked
+    against central differences."""
+    f = small_image(16, 16, 4)
+    ss, sr = 1.0, 20.0
+    p = oracle.resolve(f, ss, sr, 0.01, t_mode="tile", t_tile=8)
+    u = np.random.default_rng(3).normal(size=f.shape)
+    gs = oracle.grad_shiftable(f, u, ss, sr, p)
+    h = 1e-3
+    for (i, j) in [(0, 0), (7, 8), (8, 7), (15, 3), (9, 9)]:
+        fp, fm = f.copy(), f.copy()
+        fp[i, j] += h
+        fm[i, j] -= h
+        fd = (np.sum(u * oracle.shiftable(fp, ss, sr, p)) -
+              np.sum(u * oracle.shiftable(fm, ss, sr, p))) / (2 * h)
+        assert abs(fd - gs[i, j]) < 1e-6 * np.max(np.abs(gs)) + 1e-6 * abs(fd)
