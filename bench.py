@@ -1,0 +1,353 @@
+#!/usr/bin/env python
+"""Throughput of the shiftable bilateral filter on one GB300 (or N replicas).
+
+Workload (the headline metric): one 4096 x 4096 8-bit-range image (seeded
+G8 generator), sigma_s = 8 (R = 24), sigma_r = 10.
+  * tuned: Algorithm 2 of the paper -- exact T (Algorithm 1), eps = 1e-2
+    truncation by the sigma_r <= 10 rule (Chernoff) -- with the plane type and
+    filter of the fastest built variant;
+  * plain: the unaccelerated method, T = 255, no truncation, FP32 planes.
+A step is one bf_execute (T, N/M/weights, fused filter) of one image with its
+input resident in HBM; the L2 is flushed (256 MB write) before every timed
+step and the flush is outside the timed interval.  `value` is tuned Mpixel/s
+summed over ranks (replicas, weak scaling).  `e2e` is the same metric through
+bf_execute_host (host buffers, both copies inside the timed region).
+
+  python bench.py [--gpus N --steps K --warmup W] [--impl reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "Mpixel/s at 4096² σ_r=10: tuned vs plain FP32, max-abs err ≤0.5 gray level"
+H = W = 4096
+SIGMA_S, SIGMA_R, EPS, SEED = 8.0, 10.0, 0.01, 5
+TUNED = dict(t_mode="global", trunc_rule="alg2", plane_dtype="fp32", filter="fir")
+PLAIN = dict(t_mode="fixed", t_fixed=255.0, trunc_rule="alg2", plane_dtype="fp32", filter="fir")
+SM_COUNT_NOMINAL = 152
+FP32_LANES_PER_SM = 128
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--plain-steps", type=int, default=3)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    return ap.parse_args()
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return json.load(fh), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.idx), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append((float(parts[1]), float(parts[2]), parts[5:9]))
+            except ValueError:
+                continue
+        os.unlink(self.path)
+        if not rows:
+            return None
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for _, _, fl in rows for i, v in enumerate(fl)
+                          if v.lower() in ("active", "0x1", "1")})
+        return {"sm_mhz": statistics.median(r[0] for r in rows),
+                "sm_max_mhz": max(r[1] for r in rows),
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ------------------------------------------------------------------ CPU oracle
+def cpu_oracle_run(f_np, seconds_target: float):
+    """Times the FP64 oracle (SHIFTABLE-BF, Algorithm 2 parameters from the
+    oracle itself) on a centred crop of the image, sized to take about
+    `seconds_target`.  Returns (Mpx/s, crop side, seconds, threads)."""
+    import numpy as np
+    import oracle
+    p = oracle.resolve(f_np, SIGMA_S, SIGMA_R, EPS, t_mode="global", rule="alg2")
+    f64 = np.ascontiguousarray(f_np, dtype=np.float64)
+    g = oracle.taps(SIGMA_S, p.R)
+    lib = oracle._load()
+    out = np.empty_like(f64)
+
+    def run(side):
+        y0 = (H - side) // 2
+        t0 = time.perf_counter()
+        lib.orc_shiftable_block(oracle._p(f64), H, W, oracle._p(g), p.R, int(p.N[0, 0]),
+                                int(p.M[0, 0]), SIGMA_R, y0, y0 + side, y0, y0 + side,
+                                oracle._p(out), None, None)
+        return time.perf_counter() - t0
+
+    side = 32
+    dt = run(side)
+    # cost ~ (side + 2R)^2: grow the crop to the time target
+    while dt < seconds_target / 3 and side < 1024:
+        side *= 2
+        dt = run(side)
+    return side * side / dt / 1e6, side, dt, oracle.num_threads()
+
+
+def reference_arm(args, rank: int):
+    import numpy as np
+    from paper_1203_5128_gb300 import synth
+    if rank != 0:
+        return
+    f_np = synth.g8(H, W, seed=SEED)
+    import oracle
+    p = oracle.resolve(f_np, SIGMA_S, SIGMA_R, EPS, t_mode="global", rule="alg2")
+    f64 = np.ascontiguousarray(f_np, dtype=np.float64)
+    g = oracle.taps(SIGMA_S, p.R)
+    lib = oracle._load()
+    out = np.empty_like(f64)
+    side = 96
+    y0 = (H - side) // 2
+
+    def step():
+        lib.orc_shiftable_block(oracle._p(f64), H, W, oracle._p(g), p.R, int(p.N[0, 0]),
+                                int(p.M[0, 0]), SIGMA_R, y0, y0 + side, y0, y0 + side,
+                                oracle._p(out), None, None)
+    for _ in range(args.warmup):
+        step()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        step()
+    dt = time.perf_counter() - t0
+    v = side * side * args.steps / dt / 1e6
+    sample = "centred %dx%d crop of the 4096^2 image per step (FP64 oracle, N=%d M=%d)" % (
+        side, side, int(p.N[0, 0]), int(p.M[0, 0]))
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "Mpixel/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": dt * 1e3 / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": workload_config(),
+            "cpu_baseline": {"value": v, "unit": "Mpixel/s", "cores": oracle.num_threads(),
+                             "kind": "oracle", "sample": sample},
+            "e2e": {"value": v, "unit": "Mpixel/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def workload_config():
+    return {"workload": "4096x4096 G8 8-bit image, sigma_s=8 (R=24), sigma_r=10; tuned = "
+                        "Algorithm 2 (exact T, eps=1e-2) vs plain (T=255, eps=0, FP32)",
+            "H": H, "W": W, "sigma_s": SIGMA_S, "sigma_r": SIGMA_R, "eps": EPS,
+            "seed": SEED, "tuned": TUNED, "plain": PLAIN,
+            "l2": "flushed (256 MB write) before every timed step, outside the timed interval"}
+
+
+# ------------------------------------------------------------------ GPU arm
+def fp32_instr_per_px(N, M, R):
+    """Algorithmic FP32 instructions per output pixel of the FIR filter with F
+    pairs and z zero-frequency terms: per pair 4 planes x 2 passes x (2R+1)
+    FMAs, 2 plane products, 4 demodulation FMAs and 1 weight; per zero term
+    2 planes x 2 passes x (2R+1) + 2; plus 3 for the normalisation."""
+    F = (N - M) - N // 2
+    z = 1 if N % 2 == 0 else 0
+    taps = 2 * R + 1
+    return F * (8 * taps + 7) + z * (4 * taps + 2) + 3
+
+
+def main():
+    args = parse()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        reference_arm(args, rank)
+        return
+
+    import numpy as np
+    import torch
+    import paper_1203_5128_gb300 as bf
+    from paper_1203_5128_gb300 import synth
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    def max_over_ranks(x: float) -> float:
+        if dist is None:
+            return x
+        t = torch.tensor([x], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    f_np = synth.g8(H, W, seed=SEED)
+    f = torch.from_numpy(f_np).cuda()
+    out = torch.empty_like(f)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def timed(plan, steps, warmup):
+        for _ in range(warmup):
+            bf.bf_execute(plan, f, out)
+        barrier()
+        bf.bf_set_timing(plan, True)
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+               for _ in range(steps)]
+        for a, b in evs:
+            flush.zero_()
+            a.record(stream)
+            bf.bf_execute(plan, f, out)
+            b.record(stream)
+        barrier()
+        total = sum(a.elapsed_time(b) for a, b in evs)
+        kms, cnt = bf.bf_get_timing(plan)
+        bf.bf_set_timing(plan, False)
+        return total, kms, cnt
+
+    # ---- tuned (the headline)
+    tuned = bf.bf_plan(H, W, SIGMA_S, SIGMA_R, EPS, **TUNED)
+    bf.bf_execute(tuned, f, out)
+    torch.cuda.synchronize()
+    info_t = bf.bf_get_info(tuned)
+    clock = ClockSampler(torch.cuda.current_device()) if rank == 0 else None
+    if clock:
+        clock.start()
+    total_ms, kms, cnt = timed(tuned, args.steps, args.warmup)
+    clocks = clock.stop() if clock else None
+    total_ms = max_over_ranks(total_ms)
+    px = H * W
+    value = world * px * args.steps / (total_ms * 1e3)
+    launches_per_step = 3 if TUNED["t_mode"] != "fixed" else 2
+
+    # ---- plain FP32 (context for the metric's ratio)
+    plain = bf.bf_plan(H, W, SIGMA_S, SIGMA_R, 0.0, **PLAIN)
+    bf.bf_execute(plain, f, out)
+    torch.cuda.synchronize()
+    info_p = bf.bf_get_info(plain)
+    p_steps = max(1, min(args.plain_steps, args.steps))
+    p_ms, p_kms, p_cnt = timed(plain, p_steps, 1)
+    p_ms = max_over_ranks(p_ms)
+    plain_value = world * px * p_steps / (p_ms * 1e3)
+
+    # ---- end to end through the host entry point (pinned host buffers)
+    f_host = torch.from_numpy(f_np).pin_memory()
+    o_host = torch.empty_like(f_host).pin_memory()
+    bf.bf_execute_host(tuned, f_host, o_host)
+    e2e_steps = max(1, min(args.steps, 5))
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        bf.bf_execute_host(tuned, f_host, o_host)
+    e2e_s = max_over_ranks(time.perf_counter() - t0)
+    e2e_value = world * px * e2e_steps / (e2e_s * 1e6)
+
+    if rank != 0:
+        if dist is not None:
+            dist.destroy_process_group()
+        return
+
+    # ---- roofline of the dominant kernel (K3, fused filter): FP32 pipe
+    pk, pk_kind = peaks()
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    mhz = float(pk.get("sm_max_mhz", 2070.0))
+    peak_tinst = sms * FP32_LANES_PER_SM * mhz * 1e6 / 1e12
+    T_, N_, M_ = bf.bf_get_sets(tuned)
+    instr = fp32_instr_per_px(int(N_[0]), int(M_[0]), info_t.R) * px
+    k3_ms = kms[2] / max(cnt, 1)
+    achieved = instr / (k3_ms * 1e-3) / 1e12
+    roof = {"bound": "alu", "achieved": achieved, "peak": peak_tinst, "unit": "Tinstr/s (FP32)",
+            "frac": achieved / peak_tinst, "traffic": None,
+            "kernel": "k_fwd32 (fused modulate/FIR/demodulate)",
+            "peak_source": "%d SMs x %d FP32 lanes x %.0f MHz (%s sm_max_mhz)" % (
+                sms, FP32_LANES_PER_SM, mhz, pk_kind),
+            "algorithmic_instr_per_launch": instr,
+            "launch_ms": k3_ms,
+            "hbm_bytes_per_launch": 8 * px,
+            "hbm_frac": (8 * px / (k3_ms * 1e-3) / 1e9) / float(pk.get("hbm_gbs", 6783.5))}
+    p_k3 = p_kms[2] / max(p_cnt, 1)
+    p_instr = fp32_instr_per_px(info_p.N, info_p.M, info_p.R) * px
+
+    cpu = None
+    if not args.no_cpu_baseline and world == 1:
+        v, side, dt, thr = cpu_oracle_run(f_np, args.cpu_seconds)
+        cpu = {"value": v, "unit": "Mpixel/s", "cores": thr, "kind": "oracle",
+               "sample": "centred %dx%d crop of the tuned workload (FP64 shiftable oracle, "
+                         "%.1f s)" % (side, side, dt)}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": "Mpixel/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic", "config": workload_config(),
+        "roofline": roof, "cpu_baseline": cpu,
+        "e2e": {"value": e2e_value, "unit": "Mpixel/s", "h2d_bytes_per_step": 4 * px,
+                "d2h_bytes_per_step": 4 * px},
+        "gpu_launches": launches_per_step * args.steps,
+        "clocks": clocks,
+        "tuned": {"T": float(T_[0]), "N": int(N_[0]), "M": int(M_[0]), "K": info_t.K,
+                  "kernel_ms": {"range": kms[0] / max(cnt, 1), "params": kms[1] / max(cnt, 1),
+                                "forward": k3_ms}},
+        "plain": {"value": plain_value, "ms_per_step": p_ms / p_steps, "N": info_p.N,
+                  "K": info_p.K, "forward_ms": p_k3,
+                  "fp32_frac": p_instr / (p_k3 * 1e-3) / 1e12 / peak_tinst},
+        "speedup_vs_plain": value / plain_value,
+    }
+    print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

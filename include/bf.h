@@ -1,0 +1,194 @@
+/*
+ * bf.h -- C ABI of the GB300 shiftable O(1) Gaussian bilateral filter.
+ *
+ * The filter is the one of Chaudhury, "Acceleration of the shiftable O(1)
+ * algorithm for bilateral filtering and non-local means" (arXiv:1203.5128):
+ *
+ *   out(x) = sum_y g_s(x-y) phi(f(y)-f(x)) f(y) / sum_y g_s(x-y) phi(f(y)-f(x))
+ *
+ * (eq. (BF), Sec. 1) with the Gaussian range kernel replaced by the truncated
+ * raised cosine phi_eps of eq. (approx) (Sec. 3), evaluated by SHIFTABLE-BF
+ * (Sec. 1.2: modulate, Gaussian-filter, demodulate, normalise), with T from
+ * the windowed max filter of Algorithm 1 (Sec. 2) and N, M from Algorithm 2.
+ *
+ * Conventions shared by every entry point
+ *   - Images are float32, row-major, H rows by W columns; `pitch` is the row
+ *     stride in ELEMENTS (>= W).  The caller owns every image buffer.
+ *   - Pointers named *_dev are device pointers (cudaMalloc / torch tensors on
+ *     the plan's device); pointers named *_host are host pointers.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream).  All device work is enqueued on it and the call returns
+ *     without synchronising, unless the comment says otherwise.  Results are
+ *     valid once the stream has reached the work.
+ *   - A plan owns its device workspace (parameter tables, T words, status
+ *     word), allocated in bf_plan and freed in bf_destroy.  bf_execute and
+ *     bf_backward allocate nothing.  One plan must not be used on two
+ *     streams at the same time.
+ *   - Errors are returned as bf_status codes, never as exceptions.  Argument
+ *     errors are detected on the host before anything is enqueued.
+ *     Data-dependent failures (order above the plan's cap, a bounded wait
+ *     that ran out) are recorded in the plan's device status word and read
+ *     with bf_get_device_status.
+ *   - Borders: sums run over in-image pixels only (clipped windows), the
+ *     window is the (2R+1)^2 square with R = ceil(3 sigma_s).
+ */
+#ifndef BF_H
+#define BF_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct bf_plan_s *bf_plan_t; /* opaque; owned by the library */
+
+typedef enum bf_status {
+    BF_OK = 0,
+    BF_ERR_INVALID_ARG = 1,     /* bad size, sigma, eps, pointer or option   */
+    BF_ERR_ORDER_TOO_LARGE = 2, /* N would exceed the plan's cap (n_max)     */
+    BF_ERR_ALLOC = 3,           /* device or host allocation failed          */
+    BF_ERR_CUDA = 4,            /* a CUDA runtime call failed                */
+    BF_ERR_TIMEOUT = 5,         /* a bounded device wait ran out             */
+    BF_ERR_NO_FORWARD = 6,      /* bf_backward before any bf_execute         */
+    BF_ERR_NOT_SUPPORTED = 7,   /* option combination not built              */
+    BF_ERR_DEVICE_STATUS = 8    /* the device status word holds an error     */
+} bf_status;
+
+/* How T (Sec. 2) is obtained. */
+enum {
+    BF_T_FIXED = 0,  /* T = t_fixed (the "global [0,T]" of the earlier method) */
+    BF_T_GLOBAL = 1, /* exact T of eq. (bound) by Algorithm 1, one per image    */
+    BF_T_TILE = 2    /* T per t_tile x t_tile block of outputs, own N and M      */
+};
+
+/* Which M (Sec. 3). */
+enum {
+    BF_RULE_ALG2 = 0,    /* Algorithm 2 step 4: sigma_r bands (8-bit scale)   */
+    BF_RULE_TRUNC = 1,   /* eq. (trunc)                                       */
+    BF_RULE_CHERNOFF = 2 /* eq. (Chernoff), floored                           */
+};
+
+/* Spatial filter of the modulated planes (step 3 of SHIFTABLE-BF). */
+enum { BF_FILTER_AUTO = 0, BF_FILTER_FIR = 1, BF_FILTER_YVV = 2 };
+
+/* Storage / multiply type of the modulated planes. */
+enum { BF_PLANES_FP32 = 0, BF_PLANES_BF16 = 1, BF_PLANES_FP16 = 2 };
+
+/* Device status bits (bf_get_device_status). */
+enum {
+    BF_DEV_ORDER_TOO_LARGE = 1u << 0, /* some T gave N > cap: those outputs = f */
+    BF_DEV_TIMEOUT = 1u << 1,         /* a bounded wait ran out                  */
+    BF_DEV_BAD_WORK = 1u << 2         /* a work item failed its range check      */
+};
+
+typedef struct bf_options {
+    int t_mode;          /* BF_T_*; default BF_T_GLOBAL                           */
+    float t_fixed;       /* T for BF_T_FIXED; <= 0 means value_range              */
+    float value_range;   /* image range (255, 65535); default 255.  Sets the
+                            centring constant and the 8-bit scale of the
+                            Algorithm 2 bands (sigma_r * 255 / value_range).      */
+    int trunc_rule;      /* BF_RULE_*; default BF_RULE_ALG2                       */
+    int filter;          /* BF_FILTER_*; default AUTO (= FIR)                     */
+    int plane_dtype;     /* BF_PLANES_*; default FP32                             */
+    int n_max;           /* cap on N; default 4096                                */
+    int t_tile;          /* T-tile side for BF_T_TILE; default 64 (multiple of 64) */
+    long long spin_limit;/* iteration bound of device waits; default 1<<22        */
+    int reserved[8];     /* must be zero                                          */
+} bf_options;
+
+/* Fills *opt with the defaults listed above. */
+void bf_options_init(bf_options *opt);
+
+/* Creates a plan for H x W images (Algorithm 2 inputs: sigma_s, sigma_r,
+ * tolerance eps in [0, 1)).  opt may be NULL (defaults).  Selects the
+ * device current on the calling thread, allocates the plan's workspace and
+ * uploads the spatial taps.  Synchronous.  On error *out is set to NULL. */
+bf_status bf_plan(int H, int W, double sigma_s, double sigma_r, double eps,
+                  const bf_options *opt, bf_plan_t *out);
+
+/* Algorithm 2 on one image: T (Algorithm 1), N and M (steps 3-4), then
+ * SHIFTABLE-BF with phi_eps (Sec. 1.2), writing out_dev.  f_dev and out_dev
+ * are H x W float32 device images with row pitches f_pitch and out_pitch
+ * (elements); they must not overlap.  Asynchronous on `stream`. */
+bf_status bf_execute(bf_plan_t plan, const float *f_dev, size_t f_pitch,
+                     float *out_dev, size_t out_pitch, void *stream);
+
+/* bf_execute on host images (contiguous, pitch W): copies f_host to a
+ * plan-owned device buffer, filters, copies the result to out_host and
+ * synchronises `stream` before returning.  The device buffers are
+ * allocated by the first call on a plan and reused. */
+bf_status bf_execute_host(bf_plan_t plan, const float *f_host, float *out_host,
+                          void *stream);
+
+/* Gradient of L = sum_x grad_out(x) out(x) with respect to f, with T, N, M
+ * (and the denominator guard) held at the values the last bf_execute of this
+ * plan produced on device (not in the paper; derived from eqs. (f1)-(f2)).
+ * f_dev must be the image of that bf_execute.  All three images share
+ * `pitch`.  Returns BF_ERR_NO_FORWARD if the plan has not been executed. */
+bf_status bf_backward(bf_plan_t plan, const float *f_dev, const float *grad_out_dev,
+                      float *grad_in_dev, size_t pitch, void *stream);
+
+/* Algorithm 2 on n images, each with its own plan (sizes, sigmas, eps),
+ * in one persistent launch fed by a tile work queue.  Images are contiguous
+ * (pitch = W of their plan).  All plans must share t_mode, plane_dtype and
+ * filter.  The results equal n bf_execute calls bit for bit. */
+bf_status bf_execute_batch(int n, const bf_plan_t *plans, const float *const *f_dev,
+                           float *const *out_dev, void *stream);
+
+typedef struct bf_info {
+    int H, W, R;            /* plan sizes; R = ceil(3 sigma_s)                 */
+    int n_sets;             /* parameter sets: 1, or the number of T-tiles      */
+    float T;                /* T of the last execute (max over T-tiles)         */
+    int N, M, K;            /* N, M, K = N-2M+1 of the set with the largest N   */
+    long long n_guarded;    /* outputs where the denominator guard fired        */
+    long long terms_total;  /* sum over sets of K (work measure)                */
+    unsigned device_status; /* BF_DEV_* bits (not cleared)                      */
+    int filter, plane_dtype, t_mode;
+    int tile_h, tile_w;     /* output tile of the forward kernel                */
+} bf_info;
+
+/* Synchronises the plan's last stream and reports the parameters the last
+ * bf_execute produced. */
+bf_status bf_get_info(bf_plan_t plan, bf_info *info);
+
+/* Copies the per-set parameters of the last execute to host arrays of
+ * n_sets entries each (any pointer may be NULL).  Synchronising. */
+bf_status bf_get_sets(bf_plan_t plan, float *T, int *N, int *M, int n_sets);
+
+/* Synchronises, returns BF_ERR_DEVICE_STATUS if the device status word has
+ * any bit set (the bits go to *bits when bits != NULL) and clears it. */
+bf_status bf_get_device_status(bf_plan_t plan, unsigned *bits);
+
+/* Frees the plan and its workspace (synchronises its last stream). */
+void bf_destroy(bf_plan_t plan);
+
+/* Static text for a status code. */
+const char *bf_status_string(bf_status s);
+
+/* ---- device timing of the plan's own launches -------------------------- */
+
+/* on != 0: every later bf_execute of this plan records CUDA events on its
+ * stream around K1 (range/T), K2 (N, M, weights) and K3 (fused filter), up
+ * to 4096 executes.  Costs four event records per execute. */
+bf_status bf_set_timing(bf_plan_t plan, int on);
+
+/* Synchronises and returns, summed over the executes recorded since the
+ * last call, the device milliseconds of ms[0] = K1, ms[1] = K2, ms[2] = K3
+ * and their number in *count; then forgets them. */
+bf_status bf_get_timing(bf_plan_t plan, double *ms, int *count);
+
+/* ---- single steps of the path (tests and profiling) ------------------- */
+
+/* Windowed max and min of f over the clipped (2R+1)^2 square (Prop.
+ * MAX-FILTER, Algorithm 1 steps 2-3, by the van Herk / Gil-Werman running
+ * maxima of the Appendix).  Mx_dev and mn_dev are H x W with row pitch
+ * `pitch` like f_dev.  Asynchronous. */
+bf_status bf_maxmin(const float *f_dev, int H, int W, size_t pitch, int R,
+                    float *Mx_dev, float *mn_dev, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* BF_H */

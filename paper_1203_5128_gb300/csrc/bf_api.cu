@@ -1,0 +1,513 @@
+// C ABI of libbf: plans, Algorithm 2 on the device, status and info.
+//
+// bf_execute enqueues, on the caller's stream and without host
+// synchronisation: K1 (local range -> T, Algorithm 1) unless T is fixed, K2
+// (N, M, pair table, Algorithm 2 steps 3-5) and the fused forward K3
+// (SHIFTABLE-BF, Sec. 1.2).  K3 reads the term count from device memory, so
+// a data-dependent N never round-trips through the host.
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <new>
+
+#include "bf_internal.cuh"
+
+using namespace bf;
+
+namespace bf {
+// Defined in the translation units of the other kernels.
+cudaError_t launch_backward(bf_plan_s* p, const float* f, const float* gout, float* gin,
+                            size_t pitch, cudaStream_t s);
+}
+
+struct bf_plan_s {
+    int H, W, R;
+    double sigma_s, sigma_r, eps;
+    bf_options opt;
+    int device;
+    int n_sets, sets_x, sets_y, set_tile;
+    int n_cap, cap_pairs;
+    float c0;
+    int th, tw;
+    unsigned* d_T;
+    SetHdr* d_hdr;
+    Pair* d_pairs;
+    float* d_taps;
+    double* d_logfact;
+    unsigned* d_status;
+    unsigned long long* d_nguard;
+    float* d_hin;
+    float* d_hout;
+    float* d_bwd;            // backward scratch (out, den), allocated on first use
+    int executed;
+    cudaStream_t last;
+    int timing;              // record events around the kernels
+    int n_timed;
+    cudaEvent_t* ev;         // 4 per recorded execute
+};
+
+namespace {
+
+constexpr double kPi = 3.14159265358979323846;
+constexpr int kMaxTimed = 4096;
+
+int order_of(double T, double sigma_r)
+{
+    // same arithmetic as the device (K2): N = max(1, ceil(4 T^2 / (pi^2 sigma_r^2)))
+    const double n0 = (4.0 * T * T) / (kPi * kPi * sigma_r * sigma_r);
+    const double c = ceil(n0);
+    if (c < 1.0) return 1;
+    if (c > 1e9) return 1000000000;
+    return (int)c;
+}
+
+bf_status cuda_status(cudaError_t e) { return e == cudaSuccess ? BF_OK : BF_ERR_CUDA; }
+
+#define BF_CUDA(call)                                      \
+    do {                                                   \
+        cudaError_t e_ = (call);                           \
+        if (e_ != cudaSuccess) return BF_ERR_CUDA;         \
+    } while (0)
+
+void free_plan(bf_plan_s* p)
+{
+    if (!p) return;
+    cudaFree(p->d_T);
+    cudaFree(p->d_hdr);
+    cudaFree(p->d_pairs);
+    cudaFree(p->d_taps);
+    cudaFree(p->d_logfact);
+    cudaFree(p->d_status);
+    cudaFree(p->d_nguard);
+    cudaFree(p->d_hin);
+    cudaFree(p->d_hout);
+    cudaFree(p->d_bwd);
+    if (p->ev) {
+        for (int i = 0; i < 4 * kMaxTimed; ++i)
+            if (p->ev[i]) cudaEventDestroy(p->ev[i]);
+        free(p->ev);
+    }
+    free(p);
+}
+
+ParamsArgs params_args(bf_plan_s* p)
+{
+    ParamsArgs a;
+    a.T = reinterpret_cast<const float*>(p->d_T);
+    a.n_sets = p->n_sets;
+    a.sigma_r = p->sigma_r;
+    a.eps = p->eps;
+    a.value_range = p->opt.value_range;
+    a.rule = p->opt.trunc_rule;
+    a.n_cap = p->n_cap;
+    a.cap_pairs = p->cap_pairs;
+    a.logfact = p->d_logfact;
+    a.ln2 = log(2.0);
+    a.hdr = p->d_hdr;
+    a.pairs = p->d_pairs;
+    a.status = p->d_status;
+    return a;
+}
+
+}  // namespace
+
+namespace bf {
+
+FwdArgs forward_args(bf_plan_s* p, const float* f, size_t fp, float* out, size_t op)
+{
+    FwdArgs a;
+    a.f = f;
+    a.f_pitch = fp;
+    a.out = out;
+    a.out_pitch = op;
+    a.H = p->H;
+    a.W = p->W;
+    a.R = p->R;
+    a.taps = p->d_taps;
+    a.hdr = p->d_hdr;
+    a.pairs = p->d_pairs;
+    a.cap_pairs = p->cap_pairs;
+    a.set_tile = p->opt.t_mode == BF_T_TILE ? p->set_tile : 0;
+    a.sets_x = p->sets_x;
+    a.c0 = 0.5f * p->opt.value_range;
+    a.n_guarded = p->d_nguard;
+    a.den_out = nullptr;
+    a.den_pitch = 0;
+    return a;
+}
+
+// Event k (0..3) of the current timed execute, or null when not timing.
+static cudaEvent_t timing_event(bf_plan_s* p, int k)
+{
+    if (!p->timing || p->n_timed >= kMaxTimed) return nullptr;
+    return p->ev[4 * p->n_timed + k];
+}
+
+static cudaError_t mark(bf_plan_s* p, int k, cudaStream_t s)
+{
+    cudaEvent_t e = timing_event(p, k);
+    return e ? cudaEventRecord(e, s) : cudaSuccess;
+}
+
+// Steps 1-5 of Algorithm 2 (T, N, M, pair table) on the plan's device.
+cudaError_t enqueue_params(bf_plan_s* p, const float* f, size_t fp, cudaStream_t s)
+{
+    cudaError_t e = mark(p, 0, s);
+    if (e != cudaSuccess) return e;
+    if (p->opt.t_mode != BF_T_FIXED) {
+        e = cudaMemsetAsync(p->d_T, 0, sizeof(unsigned) * p->n_sets, s);
+        if (e != cudaSuccess) return e;
+        e = launch_local_range(f, fp, p->H, p->W, p->R,
+                               p->opt.t_mode == BF_T_TILE ? p->set_tile : 0, p->sets_x, p->d_T, s);
+        if (e != cudaSuccess) return e;
+    }
+    e = cudaMemsetAsync(p->d_nguard, 0, sizeof(unsigned long long), s);
+    if (e != cudaSuccess) return e;
+    e = mark(p, 1, s);
+    if (e != cudaSuccess) return e;
+    e = launch_params(params_args(p), s);
+    if (e != cudaSuccess) return e;
+    return mark(p, 2, s);
+}
+
+}  // namespace bf
+
+extern "C" {
+
+void bf_options_init(bf_options* o)
+{
+    if (!o) return;
+    memset(o, 0, sizeof(*o));
+    o->t_mode = BF_T_GLOBAL;
+    o->t_fixed = 0.f;
+    o->value_range = 255.f;
+    o->trunc_rule = BF_RULE_ALG2;
+    o->filter = BF_FILTER_AUTO;
+    o->plane_dtype = BF_PLANES_FP32;
+    o->n_max = 4096;
+    o->t_tile = 64;
+    o->spin_limit = 1ll << 22;
+}
+
+const char* bf_status_string(bf_status s)
+{
+    switch (s) {
+    case BF_OK: return "ok";
+    case BF_ERR_INVALID_ARG: return "invalid argument";
+    case BF_ERR_ORDER_TOO_LARGE: return "order N above the plan's cap";
+    case BF_ERR_ALLOC: return "allocation failed";
+    case BF_ERR_CUDA: return "CUDA runtime error";
+    case BF_ERR_TIMEOUT: return "bounded device wait ran out";
+    case BF_ERR_NO_FORWARD: return "backward before any forward";
+    case BF_ERR_NOT_SUPPORTED: return "option combination not supported";
+    case BF_ERR_DEVICE_STATUS: return "device status word holds an error";
+    }
+    return "unknown status";
+}
+
+bf_status bf_plan(int H, int W, double sigma_s, double sigma_r, double eps, const bf_options* opt,
+                  bf_plan_t* out)
+{
+    if (!out) return BF_ERR_INVALID_ARG;
+    *out = nullptr;
+    bf_options o;
+    if (opt) o = *opt;
+    else bf_options_init(&o);
+    if (H < 1 || W < 1 || H > (1 << 16) || W > (1 << 16)) return BF_ERR_INVALID_ARG;
+    if (!(sigma_s > 0.0) || !(sigma_r > 0.0) || !(eps >= 0.0) || !(eps < 1.0))
+        return BF_ERR_INVALID_ARG;
+    if (!isfinite(sigma_s) || !isfinite(sigma_r)) return BF_ERR_INVALID_ARG;
+    if (o.t_mode < BF_T_FIXED || o.t_mode > BF_T_TILE) return BF_ERR_INVALID_ARG;
+    if (o.trunc_rule < BF_RULE_ALG2 || o.trunc_rule > BF_RULE_CHERNOFF) return BF_ERR_INVALID_ARG;
+    if (!(o.value_range > 0.f) || !isfinite(o.value_range)) return BF_ERR_INVALID_ARG;
+    if (o.n_max < 1) return BF_ERR_INVALID_ARG;
+    if (o.n_max > 4096) return BF_ERR_NOT_SUPPORTED;
+    for (int i = 0; i < 8; ++i)
+        if (o.reserved[i]) return BF_ERR_INVALID_ARG;
+    if (o.filter == BF_FILTER_AUTO) o.filter = BF_FILTER_FIR;
+    if (o.filter != BF_FILTER_FIR) return BF_ERR_NOT_SUPPORTED;
+    if (o.plane_dtype != BF_PLANES_FP32) return BF_ERR_NOT_SUPPORTED;
+    if (o.t_mode == BF_T_TILE && (o.t_tile < 64 || o.t_tile % 64)) return BF_ERR_INVALID_ARG;
+    if (o.t_mode == BF_T_FIXED && !(o.t_fixed > 0.f)) o.t_fixed = o.value_range;
+    if (o.spin_limit <= 0) o.spin_limit = 1ll << 22;
+
+    const double Rr = ceil(3.0 * sigma_s);
+    if (Rr > 1000.0) return BF_ERR_NOT_SUPPORTED;
+    const int R = (int)Rr;
+    if (o.t_mode != BF_T_FIXED && R > range_max_radius()) return BF_ERR_NOT_SUPPORTED;
+    int th = 0, tw = 0;
+    fwd32_tile(R, &th, &tw);
+    if (!th) return BF_ERR_NOT_SUPPORTED;
+
+    const double Tcap = o.t_mode == BF_T_FIXED ? (double)o.t_fixed : (double)o.value_range;
+    int n_cap = order_of(Tcap, sigma_r);
+    if (o.t_mode == BF_T_FIXED && n_cap > o.n_max) return BF_ERR_ORDER_TOO_LARGE;
+    if (n_cap > o.n_max) n_cap = o.n_max;
+
+    bf_plan_s* p = (bf_plan_s*)calloc(1, sizeof(bf_plan_s));
+    if (!p) return BF_ERR_ALLOC;
+    p->H = H;
+    p->W = W;
+    p->R = R;
+    p->sigma_s = sigma_s;
+    p->sigma_r = sigma_r;
+    p->eps = eps;
+    p->opt = o;
+    p->th = th;
+    p->tw = tw;
+    p->c0 = 0.5f * o.value_range;
+    if (cudaGetDevice(&p->device) != cudaSuccess) {
+        free(p);
+        return BF_ERR_CUDA;
+    }
+    if (o.t_mode == BF_T_TILE) {
+        p->set_tile = o.t_tile;
+        p->sets_x = (W + o.t_tile - 1) / o.t_tile;
+        p->sets_y = (H + o.t_tile - 1) / o.t_tile;
+    } else {
+        p->set_tile = 0;
+        p->sets_x = p->sets_y = 1;
+    }
+    p->n_sets = p->sets_x * p->sets_y;
+    p->n_cap = n_cap;
+    p->cap_pairs = n_cap / 2 + 1;
+
+    bool ok = true;
+    ok &= cudaMalloc(&p->d_T, sizeof(unsigned) * p->n_sets) == cudaSuccess;
+    ok &= cudaMalloc(&p->d_hdr, sizeof(SetHdr) * p->n_sets) == cudaSuccess;
+    ok &= cudaMalloc(&p->d_pairs, sizeof(Pair) * (size_t)p->n_sets * p->cap_pairs) == cudaSuccess;
+    ok &= cudaMalloc(&p->d_taps, sizeof(float) * (2 * R + 1)) == cudaSuccess;
+    ok &= cudaMalloc(&p->d_logfact, sizeof(double) * (n_cap + 1)) == cudaSuccess;
+    ok &= cudaMalloc(&p->d_status, sizeof(unsigned)) == cudaSuccess;
+    ok &= cudaMalloc(&p->d_nguard, sizeof(unsigned long long)) == cudaSuccess;
+    if (!ok) {
+        free_plan(p);
+        return BF_ERR_ALLOC;
+    }
+    // spatial taps g(k) = exp(-k^2 / (2 sigma_s^2)) and the log(k!) table
+    float* taps = (float*)malloc(sizeof(float) * (2 * R + 1));
+    double* lf = (double*)malloc(sizeof(double) * (n_cap + 1));
+    if (!taps || !lf) {
+        free(taps);
+        free(lf);
+        free_plan(p);
+        return BF_ERR_ALLOC;
+    }
+    for (int k = -R; k <= R; ++k)
+        taps[k + R] = (float)exp(-(double)k * (double)k / (2.0 * sigma_s * sigma_s));
+    for (int k = 0; k <= n_cap; ++k) lf[k] = lgamma((double)k + 1.0);
+    ok &= cudaMemcpy(p->d_taps, taps, sizeof(float) * (2 * R + 1), cudaMemcpyHostToDevice) ==
+          cudaSuccess;
+    ok &= cudaMemcpy(p->d_logfact, lf, sizeof(double) * (n_cap + 1), cudaMemcpyHostToDevice) ==
+          cudaSuccess;
+    ok &= cudaMemset(p->d_status, 0, sizeof(unsigned)) == cudaSuccess;
+    ok &= cudaMemset(p->d_nguard, 0, sizeof(unsigned long long)) == cudaSuccess;
+    free(taps);
+    free(lf);
+    if (o.t_mode == BF_T_FIXED) {
+        float T = o.t_fixed;
+        ok &= cudaMemcpy(p->d_T, &T, sizeof(float), cudaMemcpyHostToDevice) == cudaSuccess;
+    }
+    if (!ok) {
+        free_plan(p);
+        return BF_ERR_CUDA;
+    }
+    *out = p;
+    return BF_OK;
+}
+
+bf_status bf_execute(bf_plan_t p, const float* f, size_t fp, float* out, size_t op, void* stream)
+{
+    if (!p || !f || !out) return BF_ERR_INVALID_ARG;
+    if (fp < (size_t)p->W || op < (size_t)p->W) return BF_ERR_INVALID_ARG;
+    if ((const void*)f == (const void*)out) return BF_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    BF_CUDA(cudaSetDevice(p->device));
+    BF_CUDA(enqueue_params(p, f, fp, s));
+    BF_CUDA(launch_fwd32(forward_args(p, f, fp, out, op), s));
+    BF_CUDA(mark(p, 3, s));
+    if (p->timing && p->n_timed < kMaxTimed) ++p->n_timed;
+    p->executed = 1;
+    p->last = s;
+    return BF_OK;
+}
+
+bf_status bf_execute_host(bf_plan_t p, const float* fh, float* oh, void* stream)
+{
+    if (!p || !fh || !oh) return BF_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    BF_CUDA(cudaSetDevice(p->device));
+    const size_t bytes = sizeof(float) * (size_t)p->H * p->W;
+    if (!p->d_hin) {
+        if (cudaMalloc(&p->d_hin, bytes) != cudaSuccess) return BF_ERR_ALLOC;
+        if (cudaMalloc(&p->d_hout, bytes) != cudaSuccess) return BF_ERR_ALLOC;
+    }
+    BF_CUDA(cudaMemcpyAsync(p->d_hin, fh, bytes, cudaMemcpyHostToDevice, s));
+    bf_status st = bf_execute(p, p->d_hin, p->W, p->d_hout, p->W, stream);
+    if (st != BF_OK) return st;
+    BF_CUDA(cudaMemcpyAsync(oh, p->d_hout, bytes, cudaMemcpyDeviceToHost, s));
+    BF_CUDA(cudaStreamSynchronize(s));
+    return BF_OK;
+}
+
+bf_status bf_backward(bf_plan_t p, const float* f, const float* gout, float* gin, size_t pitch,
+                      void* stream)
+{
+    if (!p || !f || !gout || !gin) return BF_ERR_INVALID_ARG;
+    if (pitch < (size_t)p->W) return BF_ERR_INVALID_ARG;
+    if (!p->executed) return BF_ERR_NO_FORWARD;
+    cudaStream_t s = (cudaStream_t)stream;
+    BF_CUDA(cudaSetDevice(p->device));
+    cudaError_t e = launch_backward(p, f, gout, gin, pitch, s);
+    if (e == cudaErrorNotSupported) return BF_ERR_NOT_SUPPORTED;
+    if (e == cudaErrorMemoryAllocation) return BF_ERR_ALLOC;
+    BF_CUDA(e);
+    p->last = s;
+    return BF_OK;
+}
+
+bf_status bf_get_info(bf_plan_t p, bf_info* info)
+{
+    if (!p || !info) return BF_ERR_INVALID_ARG;
+    memset(info, 0, sizeof(*info));
+    info->H = p->H;
+    info->W = p->W;
+    info->R = p->R;
+    info->n_sets = p->n_sets;
+    info->filter = p->opt.filter;
+    info->plane_dtype = p->opt.plane_dtype;
+    info->t_mode = p->opt.t_mode;
+    info->tile_h = p->th;
+    info->tile_w = p->tw;
+    BF_CUDA(cudaSetDevice(p->device));
+    BF_CUDA(cudaStreamSynchronize(p->last));
+    if (!p->executed) return BF_OK;
+    SetHdr* h = (SetHdr*)malloc(sizeof(SetHdr) * p->n_sets);
+    if (!h) return BF_ERR_ALLOC;
+    unsigned long long ng = 0;
+    unsigned st = 0;
+    bool ok = cudaMemcpy(h, p->d_hdr, sizeof(SetHdr) * p->n_sets, cudaMemcpyDeviceToHost) ==
+              cudaSuccess;
+    ok &= cudaMemcpy(&ng, p->d_nguard, sizeof(ng), cudaMemcpyDeviceToHost) == cudaSuccess;
+    ok &= cudaMemcpy(&st, p->d_status, sizeof(st), cudaMemcpyDeviceToHost) == cudaSuccess;
+    if (!ok) {
+        free(h);
+        return BF_ERR_CUDA;
+    }
+    int best = 0;
+    long long terms = 0;
+    float Tm = 0.f;
+    for (int i = 0; i < p->n_sets; ++i) {
+        if (h[i].N > h[best].N) best = i;
+        if (h[i].T > Tm) Tm = h[i].T;
+        if (h[i].F >= 0) terms += h[i].N - 2 * h[i].M + 1;
+    }
+    info->T = Tm;
+    info->N = h[best].N;
+    info->M = h[best].M;
+    info->K = h[best].N - 2 * h[best].M + 1;
+    info->n_guarded = (long long)ng;
+    info->terms_total = terms;
+    info->device_status = st;
+    free(h);
+    return BF_OK;
+}
+
+bf_status bf_get_sets(bf_plan_t p, float* T, int* N, int* M, int n)
+{
+    if (!p || n != p->n_sets) return BF_ERR_INVALID_ARG;
+    if (!p->executed) return BF_ERR_NO_FORWARD;
+    BF_CUDA(cudaSetDevice(p->device));
+    BF_CUDA(cudaStreamSynchronize(p->last));
+    SetHdr* h = (SetHdr*)malloc(sizeof(SetHdr) * n);
+    if (!h) return BF_ERR_ALLOC;
+    if (cudaMemcpy(h, p->d_hdr, sizeof(SetHdr) * n, cudaMemcpyDeviceToHost) != cudaSuccess) {
+        free(h);
+        return BF_ERR_CUDA;
+    }
+    for (int i = 0; i < n; ++i) {
+        if (T) T[i] = h[i].T;
+        if (N) N[i] = h[i].N;
+        if (M) M[i] = h[i].M;
+    }
+    free(h);
+    return BF_OK;
+}
+
+bf_status bf_get_device_status(bf_plan_t p, unsigned* bits)
+{
+    if (!p) return BF_ERR_INVALID_ARG;
+    BF_CUDA(cudaSetDevice(p->device));
+    BF_CUDA(cudaStreamSynchronize(p->last));
+    unsigned st = 0;
+    BF_CUDA(cudaMemcpy(&st, p->d_status, sizeof(st), cudaMemcpyDeviceToHost));
+    BF_CUDA(cudaMemset(p->d_status, 0, sizeof(unsigned)));
+    if (bits) *bits = st;
+    return st ? BF_ERR_DEVICE_STATUS : BF_OK;
+}
+
+void bf_destroy(bf_plan_t p)
+{
+    if (!p) return;
+    cudaSetDevice(p->device);
+    cudaStreamSynchronize(p->last);
+    free_plan(p);
+}
+
+bf_status bf_set_timing(bf_plan_t p, int on)
+{
+    if (!p) return BF_ERR_INVALID_ARG;
+    BF_CUDA(cudaSetDevice(p->device));
+    if (on && !p->ev) {
+        p->ev = (cudaEvent_t*)calloc(4 * kMaxTimed, sizeof(cudaEvent_t));
+        if (!p->ev) return BF_ERR_ALLOC;
+        for (int i = 0; i < 4 * kMaxTimed; ++i) BF_CUDA(cudaEventCreate(&p->ev[i]));
+    }
+    p->timing = on ? 1 : 0;
+    p->n_timed = 0;
+    return BF_OK;
+}
+
+bf_status bf_get_timing(bf_plan_t p, double* ms, int* count)
+{
+    if (!p || !ms) return BF_ERR_INVALID_ARG;
+    BF_CUDA(cudaSetDevice(p->device));
+    BF_CUDA(cudaStreamSynchronize(p->last));
+    ms[0] = ms[1] = ms[2] = 0.0;
+    for (int i = 0; i < p->n_timed; ++i) {
+        float t;
+        for (int k = 0; k < 3; ++k) {
+            BF_CUDA(cudaEventElapsedTime(&t, p->ev[4 * i + k], p->ev[4 * i + k + 1]));
+            ms[k] += t;
+        }
+    }
+    if (count) *count = p->n_timed;
+    p->n_timed = 0;
+    return BF_OK;
+}
+
+bf_status bf_maxmin(const float* f, int H, int W, size_t pitch, int R, float* Mx, float* mn,
+                    void* stream)
+{
+    if (!f || !Mx || !mn || H < 1 || W < 1 || R < 0 || pitch < (size_t)W)
+        return BF_ERR_INVALID_ARG;
+    if (R > range_max_radius()) return BF_ERR_NOT_SUPPORTED;
+    return cuda_status(launch_maxmin(f, pitch, H, W, R, Mx, mn, (cudaStream_t)stream));
+}
+
+bf_status bf_execute_batch(int n, const bf_plan_t* plans, const float* const* f,
+                           float* const* out, void* stream)
+{
+    (void)n; (void)plans; (void)f; (void)out; (void)stream;
+    return BF_ERR_NOT_SUPPORTED;
+}
+
+}  // extern "C"
+
+namespace bf {
+cudaError_t launch_backward(bf_plan_s*, const float*, const float*, float*, size_t, cudaStream_t)
+{
+    return cudaErrorNotSupported;
+}
+}  // namespace bf

@@ -1,0 +1,320 @@
+// K3: fused SHIFTABLE-BF forward with FP32 planes and an exact FIR Gaussian.
+//
+// Sec. 1.2 of the paper (eqs. (f1), (f2) and the four-step procedure): for
+// each kept term of phi_eps (eq. (approx)) form the planes f cos(w f),
+// f sin(w f), cos(w f), sin(w f), filter them with the spatial Gaussian
+// (eq. (GF)), demodulate with cos(w f(x)), sin(w f(x)) and accumulate the
+// numerator and the denominator; out = num / den.  Terms n and N-n are folded
+// (cos is even: their contributions are equal), so a pair carries 2 w_n.
+//
+// GB300 form, one CTA per TH x TW block of outputs, one launch per image:
+//   * the block plus its R halo of the centred image f - c0 is staged in
+//     shared memory once; HBM sees f once and out once;
+//   * per pair: (1) every halo pixel gets cos / sin of its phase, computed as
+//     an FP32 head + tail product (FMA TwoProduct) reduced by 2 pi in two
+//     parts (Cody-Waite) and evaluated on the SFU; (2) rows are filtered with
+//     a register-blocked FIR (8 outputs per thread, 8 inputs per step, taps
+//     zero-padded so that no branch guards the window); (3) columns likewise,
+//     then the demodulation FMAs go straight into num / den registers;
+//   * out-of-image pixels have all four planes zero (clipped windows);
+//   * a pixel whose den <= 1e-6 (g * 1_Omega) keeps f (the paper is silent).
+#include <math.h>
+
+#include "bf_internal.cuh"
+
+namespace bf {
+namespace {
+
+constexpr double kTwoPi = 6.283185307179586476925286766559;
+constexpr float k2PiHi = (float)kTwoPi;
+constexpr float k2PiLo = (float)(kTwoPi - (double)(float)kTwoPi);
+constexpr float kInv2Pi = (float)(1.0 / kTwoPi);
+
+// cos and sin of (om_hi + om_lo) * v.
+__device__ __forceinline__ void phase_cs(float v, float om_hi, float om_lo, float& c, float& s)
+{
+    const float p = __fmul_rn(om_hi, v);
+    float e = fmaf(om_hi, v, -p);           // exact rounding error of p
+    e = fmaf(om_lo, v, e);                  // + tail of omega
+    const float q = rintf(__fmul_rn(p, kInv2Pi));
+    float r = fmaf(-q, k2PiHi, p);
+    r = fmaf(-q, k2PiLo, r);
+    r = __fadd_rn(r, e);
+    __sincosf(r, &s, &c);
+}
+
+// Element j (0..7, a compile-time constant after unrolling) of the pair (a, b).
+__device__ __forceinline__ float pick8(const float4& a, const float4& b, int j)
+{
+    switch (j) {
+    case 0: return a.x;
+    case 1: return a.y;
+    case 2: return a.z;
+    case 3: return a.w;
+    case 4: return b.x;
+    case 5: return b.y;
+    case 6: return b.z;
+    default: return b.w;
+    }
+}
+
+// Shared-memory geometry for a tile of TH x TW outputs and radius R.
+struct Geo {
+    int R, nch, RH, RW, RWp, RHp, ngz;
+    __host__ __device__ Geo(int R_, int TH, int TW)
+    {
+        R = R_;
+        nch = (2 * R + 15) / 8;                 // 8-wide steps covering 2R+8 inputs
+        RH = TH + 2 * R;
+        RW = TW + 2 * R;
+        RWp = TW - 8 + 8 * nch + 4;             // +4 words: rows 16 B aligned, banks staggered
+        RHp = TH - 8 + 8 * nch;
+        ngz = 8 * nch + 16;
+    }
+    __host__ __device__ size_t floats(int TW) const
+    {
+        return 3 * (size_t)RH * RWp + 4 * (size_t)RHp * TW + (size_t)ngz;
+    }
+};
+
+template <int TH, int TW>
+__global__ void __launch_bounds__(TH * TW / 8, 1) k_fwd32(FwdArgs a)
+{
+    constexpr int NT = TH * TW / 8;
+    constexpr int NW = NT / 32;
+    extern __shared__ __align__(16) float sm[];
+    const Geo G(a.R, TH, TW);
+    const int R = a.R;
+    float* fsm = sm;                              // RH x RWp  centred f, 0 outside
+    float* csm = fsm + (size_t)G.RH * G.RWp;      // RH x RWp  cos
+    float* ssm = csm + (size_t)G.RH * G.RWp;      // RH x RWp  sin
+    float* hsm = ssm + (size_t)G.RH * G.RWp;      // 4 x RHp x TW  row-filtered planes
+    float* gz = hsm + 4 * (size_t)G.RHp * TW;     // taps, gz[t + 8] = g(t - R), 0 outside [0, 2R]
+    const size_t hplane = (size_t)G.RHp * TW;
+
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int by = blockIdx.y * TH, bx = blockIdx.x * TW;
+    const int gy0 = by - R, gx0 = bx - R;
+
+    const int set = a.set_tile ? (by / a.set_tile) * a.sets_x + (bx / a.set_tile) : 0;
+    const SetHdr hd = a.hdr[set];
+
+    // my vertical item: column o, rows rb*8 .. rb*8+7 of the block
+    const int o = tid % TW, rb = tid / TW;
+    const int gx = bx + o;
+
+    if (hd.F < 0) {          // order above the cap: pass the image through
+        for (int i = 0; i < 8; ++i) {
+            const int gy = by + rb * 8 + i;
+            if (gy < a.H && gx < a.W)
+                a.out[(size_t)gy * a.out_pitch + gx] = a.f[(size_t)gy * a.f_pitch + gx];
+        }
+        return;
+    }
+
+    // stage the centred block + halo (and zero the padding columns)
+    for (int r = warp; r < G.RH; r += NW) {
+        const int gy = gy0 + r;
+        const bool rin = gy >= 0 && gy < a.H;
+        for (int col = lane; col < G.RWp; col += 32) {
+            const int x = gx0 + col;
+            float v = 0.f;
+            if (rin && col < G.RW && x >= 0 && x < a.W)
+                v = __ldg(a.f + (size_t)gy * a.f_pitch + x) - a.c0;
+            fsm[r * G.RWp + col] = v;
+        }
+    }
+    for (int i = tid; i < G.ngz; i += NT) {
+        const int t = i - 8;
+        gz[i] = (t >= 0 && t <= 2 * R) ? a.taps[t] : 0.f;
+    }
+    // rows RH..RHp-1 of the row-filtered planes stay zero for the whole launch
+    for (int i = tid; i < (G.RHp - G.RH) * TW; i += NT)
+        for (int q = 0; q < 4; ++q) hsm[q * hplane + (size_t)G.RH * TW + i] = 0.f;
+
+    // clipped Gaussian mass of my outputs (denominator guard)
+    float cmass = 0.f;
+    for (int t = -R; t <= R; ++t)
+        if (gx + t >= 0 && gx + t < a.W) cmass += a.taps[t + R];
+
+    float num[8], den[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) num[i] = den[i] = 0.f;
+
+    __syncthreads();
+
+    const Pair* pr = a.pairs + (size_t)set * a.cap_pairs;
+    const int K = hd.F + hd.z;
+    for (int k = 0; k < K; ++k) {
+        float om_hi = 0.f, om_lo = 0.f, Wk = hd.w0;
+        if (k < hd.F) {
+            const Pair p = pr[k];
+            om_hi = p.om_hi;
+            om_lo = p.om_lo;
+            Wk = p.W;
+        }
+
+        // (1) modulate: cos / sin of every in-image halo pixel, 0 elsewhere
+        for (int r = warp; r < G.RH; r += NW) {
+            const int gy = gy0 + r;
+            const bool rin = gy >= 0 && gy < a.H;
+            for (int col = lane; col < G.RWp; col += 32) {
+                const int x = gx0 + col;
+                float c = 0.f, s = 0.f;
+                if (rin && col < G.RW && x >= 0 && x < a.W)
+                    phase_cs(fsm[r * G.RWp + col], om_hi, om_lo, c, s);
+                csm[r * G.RWp + col] = c;
+                ssm[r * G.RWp + col] = s;
+            }
+        }
+        __syncthreads();
+
+        // (2) rows: item (r, cb) -> 8 outputs of row r, columns cb*8 .. cb*8+7
+        for (int it = tid; it < G.RH * (TW / 8); it += NT) {
+            const int r = it / (TW / 8), cb = it - r * (TW / 8);
+            const float* fr = fsm + r * G.RWp + cb * 8;
+            const float* cr = csm + r * G.RWp + cb * 8;
+            const float* sr = ssm + r * G.RWp + cb * 8;
+            float acc[4][8];
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+#pragma unroll
+                for (int i = 0; i < 8; ++i) acc[q][i] = 0.f;
+            for (int ch = 0; ch < G.nch; ++ch) {
+                const int a0 = ch * 8;
+                float g[15];
+#pragma unroll
+                for (int d = 0; d < 15; ++d) g[d] = gz[a0 + d + 1];   // tap a0 + d - 7
+                const float4 c0 = *(const float4*)(cr + a0), c1 = *(const float4*)(cr + a0 + 4);
+                const float4 s0 = *(const float4*)(sr + a0), s1 = *(const float4*)(sr + a0 + 4);
+                const float4 f0 = *(const float4*)(fr + a0), f1 = *(const float4*)(fr + a0 + 4);
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                    const float cj = pick8(c0, c1, j), sj = pick8(s0, s1, j);
+                    const float fj = pick8(f0, f1, j);
+                    const float A = fj * cj, B = fj * sj;
+#pragma unroll
+                    for (int i = 0; i < 8; ++i) {
+                        const float w = g[j - i + 7];
+                        acc[0][i] = fmaf(w, A, acc[0][i]);
+                        acc[1][i] = fmaf(w, B, acc[1][i]);
+                        acc[2][i] = fmaf(w, cj, acc[2][i]);
+                        acc[3][i] = fmaf(w, sj, acc[3][i]);
+                    }
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                float* hp = hsm + q * hplane + (size_t)r * TW + cb * 8;
+                *(float4*)hp = make_float4(acc[q][0], acc[q][1], acc[q][2], acc[q][3]);
+                *(float4*)(hp + 4) = make_float4(acc[q][4], acc[q][5], acc[q][6], acc[q][7]);
+            }
+        }
+        __syncthreads();
+
+        // (3) columns of my item, then demodulate into num / den
+        {
+            float acc[4][8];
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+#pragma unroll
+                for (int i = 0; i < 8; ++i) acc[q][i] = 0.f;
+            const float* h0 = hsm + (size_t)(rb * 8) * TW + o;
+            for (int ch = 0; ch < G.nch; ++ch) {
+                const int a0 = ch * 8;
+                float g[15];
+#pragma unroll
+                for (int d = 0; d < 15; ++d) g[d] = gz[a0 + d + 1];
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                    const float* hj = h0 + (size_t)(a0 + j) * TW;
+                    const float hA = hj[0], hB = hj[hplane], hC = hj[2 * hplane],
+                                hD = hj[3 * hplane];
+#pragma unroll
+                    for (int i = 0; i < 8; ++i) {
+                        const float w = g[j - i + 7];
+                        acc[0][i] = fmaf(w, hA, acc[0][i]);
+                        acc[1][i] = fmaf(w, hB, acc[1][i]);
+                        acc[2][i] = fmaf(w, hC, acc[2][i]);
+                        acc[3][i] = fmaf(w, hD, acc[3][i]);
+                    }
+                }
+            }
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                const int ry = rb * 8 + i + R;
+                const float c = csm[ry * G.RWp + o + R], s = ssm[ry * G.RWp + o + R];
+                num[i] = fmaf(Wk, fmaf(c, acc[0][i], s * acc[1][i]), num[i]);
+                den[i] = fmaf(Wk, fmaf(c, acc[2][i], s * acc[3][i]), den[i]);
+            }
+        }
+        __syncthreads();
+    }
+
+    // normalise (eq. (f1) over eq. (f2)) with the guard, write out
+    if (gx < a.W) {
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            const int gy = by + rb * 8 + i;
+            if (gy >= a.H) continue;
+            float rmass = 0.f;
+            for (int t = -R; t <= R; ++t)
+                if (gy + t >= 0 && gy + t < a.H) rmass += a.taps[t + R];
+            float v;
+            if (den[i] > kGuard * rmass * cmass) {
+                v = __fdiv_rn(num[i], den[i]) + a.c0;
+            } else {
+                v = a.f[(size_t)gy * a.f_pitch + gx];
+                atomicAdd(a.n_guarded, 1ull);
+            }
+            a.out[(size_t)gy * a.out_pitch + gx] = v;
+            if (a.den_out) a.den_out[(size_t)gy * a.den_pitch + gx] = den[i];
+        }
+    }
+}
+
+template <int TH, int TW>
+cudaError_t launch_tile(const FwdArgs& a, cudaStream_t s)
+{
+    const Geo G(a.R, TH, TW);
+    const size_t smem = G.floats(TW) * sizeof(float);
+    cudaError_t e = cudaFuncSetAttribute(k_fwd32<TH, TW>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    dim3 grid((a.W + TW - 1) / TW, (a.H + TH - 1) / TH);
+    k_fwd32<TH, TW><<<grid, TH * TW / 8, smem, s>>>(a);
+    return cudaGetLastError();
+}
+
+constexpr size_t kSmemLimit = 227 * 1024;
+
+}  // namespace
+
+size_t fwd32_smem(int R, int th, int tw)
+{
+    return Geo(R, th, tw).floats(tw) * sizeof(float);
+}
+
+void fwd32_tile(int R, int* th, int* tw)
+{
+    static const int shapes[][2] = {{64, 32}, {32, 32}, {16, 16}};
+    for (auto& sh : shapes)
+        if (fwd32_smem(R, sh[0], sh[1]) <= kSmemLimit) {
+            *th = sh[0];
+            *tw = sh[1];
+            return;
+        }
+    *th = *tw = 0;
+}
+
+cudaError_t launch_fwd32(const FwdArgs& a, cudaStream_t s)
+{
+    int th, tw;
+    fwd32_tile(a.R, &th, &tw);
+    if (th == 64 && tw == 32) return launch_tile<64, 32>(a, s);
+    if (th == 32 && tw == 32) return launch_tile<32, 32>(a, s);
+    if (th == 16 && tw == 16) return launch_tile<16, 16>(a, s);
+    return cudaErrorInvalidValue;
+}
+
+}  // namespace bf

@@ -1,0 +1,89 @@
+// Internal declarations shared by the CUDA translation units of libbf.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "bf.h"
+
+namespace bf {
+
+// One parameter set (Algorithm 2, steps 3-5) as the forward kernels read it.
+// F folded frequency pairs (n and N-n, weight 2 w_n) follow in the pair
+// table; z = 1 when the zero frequency n = N/2 is kept (weight w0).
+// F < 0 marks a set whose N exceeded the plan's cap.
+struct SetHdr {
+    int N, M, F, z;
+    float w0, T, pad0, pad1;
+};
+
+// Pair k of a set: omega = (2n - N) / (sqrt(N) sigma_r) > 0 split into an
+// FP32 head and tail (hi + lo), and the folded weight W = 2 w_n.
+struct Pair {
+    float om_hi, om_lo, W, pad;
+};
+
+// Device status bits (mirrors BF_DEV_* of bf.h).
+constexpr unsigned kDevOrder = 1u << 0;
+constexpr unsigned kDevTimeout = 1u << 1;
+constexpr unsigned kDevBadWork = 1u << 2;
+
+// Denominator guard (the paper is silent): where den <= kGuard * (g * 1_Omega)
+// the output is f(x).
+constexpr float kGuard = 1e-6f;
+
+// ---- launchers (each in its own translation unit) ------------------------
+
+// K1: local range r(x) = max(M(x) - f(x), f(x) - m(x)) reduced to one
+// non-negative float per T-set (atomicMax on the bit pattern).  Tbits must be
+// zeroed first.  set_tile == 0: one set for the whole image.
+cudaError_t launch_local_range(const float* f, size_t pitch, int H, int W, int R,
+                               int set_tile, int sets_x, unsigned* Tbits, cudaStream_t s);
+
+// Largest R whose K1 staging fits in shared memory.
+int range_max_radius();
+
+// K1 as images: windowed max and min (testing entry point).
+cudaError_t launch_maxmin(const float* f, size_t pitch, int H, int W, int R, float* Mx,
+                          float* mn, cudaStream_t s);
+
+// K2: N, M and the pair table for every set from its T.
+struct ParamsArgs {
+    const float* T;        // [n_sets]
+    int n_sets;
+    double sigma_r, eps, value_range;
+    int rule;
+    int n_cap;             // largest N the pair table can hold
+    int cap_pairs;         // pairs per set in the table
+    const double* logfact; // log(k!) for k = 0..n_cap (host lgamma)
+    double ln2;
+    SetHdr* hdr;
+    Pair* pairs;
+    unsigned* status;
+};
+cudaError_t launch_params(const ParamsArgs& a, cudaStream_t s);
+
+// K3 (FP32 planes, FIR): fused modulate / filter / demodulate / normalise.
+struct FwdArgs {
+    const float* f;
+    size_t f_pitch;
+    float* out;
+    size_t out_pitch;
+    int H, W, R;
+    const float* taps;      // 2R+1 FP32 spatial taps g(k)
+    const SetHdr* hdr;
+    const Pair* pairs;
+    int cap_pairs;
+    int set_tile;           // 0: single set; else T-tile side
+    int sets_x;
+    float c0;               // centring constant (value_range / 2)
+    unsigned long long* n_guarded;
+    float* den_out;         // optional: den per pixel (backward)
+    size_t den_pitch;
+};
+// Output tile of the FP32 kernel for a given R (0 if unsupported).
+void fwd32_tile(int R, int* th, int* tw);
+size_t fwd32_smem(int R, int th, int tw);
+cudaError_t launch_fwd32(const FwdArgs& a, cudaStream_t s);
+
+}  // namespace bf

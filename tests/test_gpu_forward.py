@@ -1,0 +1,210 @@
+"""GPU parity of the forward path (K1 max/min + T, K2 N/M/weights, K3 fused
+FP32 filter) against the FP64 oracle, through the C ABI.
+
+Bars: the max/min filter, T, N and M are bit-exact (max and min are exact in
+any precision; N and M are integer decisions taken in FP64 on both sides).
+The filtered image matches the oracle run with the same (T, N, M) to
+max-abs 1e-3 gray levels (8-bit images).  At full size the oracle is
+evaluated at sampled pixels with its direct form (which the oracle pins
+show equal to its shiftable form to 1e-10).
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1203_5128_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+TOL8 = 1e-3           # gray levels, 8-bit images, FP32 planes
+
+
+@pytest.fixture(scope="module")
+def bf():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need CUDA"
+    from paper_1203_5128_gb300 import build
+    build.build()
+    import paper_1203_5128_gb300 as m
+    return m
+
+
+def to_dev(a):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).cuda()
+
+
+def check_sets(bf, plan, p):
+    T, N, M = bf.bf_get_sets(plan)
+    assert np.array_equal(T, p.T.ravel()), (T, p.T.ravel())
+    assert np.array_equal(N, p.N.ravel().astype(np.int32)), (N, p.N.ravel())
+    assert np.array_equal(M, p.M.ravel().astype(np.int32)), (M, p.M.ravel())
+
+
+def run(bf, f_np, ss, sr, eps, mode="global", rule="alg2", tile=64, vr=255.0, t_fixed=None):
+    import torch
+    H, W = f_np.shape
+    kw = dict(t_mode=mode, trunc_rule=rule, t_tile=tile, value_range=vr)
+    if t_fixed is not None:
+        kw["t_fixed"] = t_fixed
+    plan = bf.bf_plan(H, W, ss, sr, eps, **kw)
+    out = bf.bf_execute(plan, to_dev(f_np))
+    torch.cuda.synchronize()
+    p = oracle.resolve(f_np, ss, sr, eps, t_mode=mode, rule=rule, t_tile=tile,
+                       value_range=vr, t_fixed=t_fixed)
+    check_sets(bf, plan, p)
+    return plan, out.cpu().numpy().astype(np.float64), p
+
+
+# ---------------------------------------------------------------- K1
+@pytest.mark.parametrize("H,W,R", [(16, 16, 1), (23, 37, 2), (100, 77, 9), (1, 40, 3),
+                                   (40, 1, 3), (5, 7, 12), (300, 257, 24), (64, 64, 48),
+                                   (97, 131, 0)])
+def test_maxmin_bitwise(bf, H, W, R):
+    """Prop. MAX-FILTER / Appendix: exact windowed max and min."""
+    import torch
+    f = np.random.default_rng(H * W + R).uniform(0, 255, (H, W)).astype(np.float32)
+    f[H // 2, :] = 255.0
+    Mx, mn = bf.bf_maxmin(to_dev(f), R)
+    torch.cuda.synchronize()
+    Mb, mb = oracle.maxmin_brute(f, R)
+    assert np.array_equal(Mx.cpu().numpy(), Mb.astype(np.float32))
+    assert np.array_equal(mn.cpu().numpy(), mb.astype(np.float32))
+
+
+def test_maxmin_pitched(bf):
+    import torch
+    big = np.random.default_rng(7).uniform(0, 255, (70, 100)).astype(np.float32)
+    t = to_dev(big)[:, 5:86]              # pitch 100, width 81
+    Mx, mn = bf.bf_maxmin(t, 6)
+    torch.cuda.synchronize()
+    Mb, mb = oracle.maxmin_brute(big[:, 5:86], 6)
+    assert np.array_equal(Mx.cpu().numpy(), Mb.astype(np.float32))
+    assert np.array_equal(mn.cpu().numpy(), mb.astype(np.float32))
+
+
+# ---------------------------------------------------------------- K1 + K2 + K3
+SMALL = [
+    # H, W, sigma_s, sigma_r, eps, mode, rule, tile, value_range, t_fixed
+    (256, 256, 3.0, 30.0, 0.0, "fixed", "alg2", 64, 255.0, 255.0),     # configs[0]
+    (100, 77, 2.0, 15.0, 0.01, "global", "trunc", 64, 255.0, None),     # ragged tiles
+    (130, 200, 1.5, 12.0, 0.01, "tile", "alg2", 64, 255.0, None),       # per-tile T
+    (90, 150, 2.5, 8.0, 0.01, "global", "alg2", 64, 255.0, None),       # Chernoff band
+    (70, 64, 4.0, 45.0, 0.05, "tile", "alg2", 128, 255.0, None),        # M = 0 band
+    (1, 300, 2.0, 20.0, 0.01, "global", "alg2", 64, 255.0, None),       # one row
+    (300, 1, 2.0, 20.0, 0.01, "global", "alg2", 64, 255.0, None),       # one column
+    (10, 13, 5.0, 20.0, 0.01, "global", "alg2", 64, 255.0, None),       # R > image
+    (65, 97, 10.0, 20.0, 0.01, "global", "trunc", 64, 255.0, None),     # R = 30
+    (48, 52, 16.0, 40.0, 0.01, "global", "trunc", 64, 255.0, None),     # R = 48
+]
+
+
+@pytest.mark.parametrize("case", SMALL, ids=lambda c: "%dx%d_s%g_r%g_%s" % (c[0], c[1], c[2], c[3], c[5]))
+def test_forward_matches_oracle(bf, case):
+    H, W, ss, sr, eps, mode, rule, tile, vr, tf = case
+    f = synth.g8(H, W, seed=H + 3 * W)
+    _, out, p = run(bf, f, ss, sr, eps, mode, rule, tile, vr, tf)
+    ref = oracle.shiftable(f, ss, sr, p)
+    err = np.max(np.abs(out - ref))
+    assert err <= TOL8, "max-abs %.3g gray levels" % err
+
+
+def test_forward_pitched_and_stream(bf):
+    """Row pitch > W on input and output; work on a side stream; plan reuse."""
+    import torch
+    H, W = 120, 90
+    f = synth.g8(H, W, seed=17)
+    plan = bf.bf_plan(H, W, 2.0, 20.0, 0.01, t_mode="global")
+    big = torch.zeros((H, W + 13), device="cuda")
+    big[:, 4:4 + W] = to_dev(f)
+    fin = big[:, 4:4 + W]
+    outbig = torch.full((H, W + 7), -1.0, device="cuda")
+    out = outbig[:, 3:3 + W]
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        bf.bf_execute(plan, fin, out)
+    s.synchronize()
+    p = oracle.resolve(f, 2.0, 20.0, 0.01, t_mode="global")
+    ref = oracle.shiftable(f, 2.0, 20.0, p)
+    assert np.max(np.abs(out.cpu().numpy() - ref)) <= TOL8
+    ob = outbig.cpu().numpy()
+    assert np.all(ob[:, :3] == -1.0) and np.all(ob[:, 3 + W:] == -1.0)
+    # second image through the same plan
+    f2 = synth.g8(H, W, seed=18)
+    out2 = bf.bf_execute(plan, to_dev(f2))
+    torch.cuda.synchronize()
+    p2 = oracle.resolve(f2, 2.0, 20.0, 0.01, t_mode="global")
+    assert np.max(np.abs(out2.cpu().numpy() - oracle.shiftable(f2, 2.0, 20.0, p2))) <= TOL8
+
+
+def test_host_entry_point_matches_device(bf):
+    import torch
+    H, W = 64, 96
+    f = synth.g8(H, W, seed=23)
+    plan = bf.bf_plan(H, W, 2.0, 25.0, 0.01)
+    dev = bf.bf_execute(plan, to_dev(f)).cpu()
+    host = bf.bf_execute_host(plan, torch.from_numpy(f).pin_memory())
+    assert torch.equal(dev, host)
+
+
+def test_constant_image(bf):
+    """A constant image is a fixed point; T = 0 and N = 1 (Sec. 2, Sec. 1.3)."""
+    import torch
+    f = np.full((50, 70), 93.5, np.float32)
+    plan = bf.bf_plan(50, 70, 3.0, 10.0, 0.01)
+    out = bf.bf_execute(plan, to_dev(f))
+    torch.cuda.synchronize()
+    T, N, M = bf.bf_get_sets(plan)
+    assert T[0] == 0.0 and N[0] == 1
+    assert np.max(np.abs(out.cpu().numpy() - 93.5)) <= 1e-4
+
+
+def test_order_cap_passes_image_through(bf):
+    """N above the plan's cap: outputs = f and the device status says so."""
+    import torch
+    from paper_1203_5128_gb300 import _native as nat
+    f = synth.g8(64, 64, seed=5)
+    plan = bf.bf_plan(64, 64, 2.0, 5.0, 0.0, n_max=16)
+    out = bf.bf_execute(plan, to_dev(f))
+    torch.cuda.synchronize()
+    assert np.array_equal(out.cpu().numpy(), f)
+    assert bf.bf_get_device_status(plan) & nat.BF_DEV_ORDER_TOO_LARGE
+    assert bf.bf_get_device_status(plan) == 0      # cleared by the read
+    with pytest.raises(bf.BfError):
+        bf.bf_plan(64, 64, 2.0, 5.0, 0.0, t_mode="fixed", t_fixed=255.0, n_max=16)
+
+
+# ---------------------------------------------------------------- full sizes, sampled
+def sample_points(H, W, n, seed, tile=64, R=0):
+    rng = np.random.default_rng(seed)
+    ys = list(rng.integers(0, H, n))
+    xs = list(rng.integers(0, W, n))
+    # corners, borders, tile seams
+    for y, x in [(0, 0), (H - 1, W - 1), (0, W - 1), (H - 1, 0), (tile - 1, tile),
+                 (tile, tile - 1), (H // 2, 0), (0, W // 2), (R, R), (H - 1 - R, W - 1 - R)]:
+        ys.append(min(max(y, 0), H - 1))
+        xs.append(min(max(x, 0), W - 1))
+    return np.array(ys), np.array(xs)
+
+
+@pytest.mark.parametrize("ss", [5.0, 10.0])
+@pytest.mark.parametrize("sr", [10.0, 20.0])
+@pytest.mark.parametrize("mode", ["global", "tile"])
+def test_accelerated_1024_sampled(bf, ss, sr, mode):
+    """1024^2 G8, eps = 1e-2 (Algorithm 2), exact global or per-tile T."""
+    f = synth.g8(1024, 1024, seed=1)
+    plan, out, p = run(bf, f, ss, sr, 0.01, mode, "alg2", 64)
+    ys, xs = sample_points(1024, 1024, 120, seed=int(ss * 10 + sr), R=p.R)
+    ref = oracle.direct(f, ss, sr, p, points=(ys, xs))
+    err = np.max(np.abs(out[ys, xs] - ref))
+    assert err <= TOL8, "max-abs %.3g gray levels" % err
+
+
+def test_plain_1024_sampled(bf):
+    """1024^2 G8, the unaccelerated method: T = 255, no truncation."""
+    f = synth.g8(1024, 1024, seed=1)
+    plan, out, p = run(bf, f, 5.0, 10.0, 0.0, "fixed", "alg2", 64, 255.0, 255.0)
+    assert int(p.N[0, 0]) == 264 and int(p.M[0, 0]) == 0
+    ys, xs = sample_points(1024, 1024, 60, seed=3, R=p.R)
+    ref = oracle.direct(f, 5.0, 10.0, p, points=(ys, xs))
+    assert np.max(np.abs(out[ys, xs] - ref)) <= TOL8
