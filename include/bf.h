@@ -178,6 +178,34 @@ bf_status bf_set_timing(bf_plan_t plan, int on);
  * and their number in *count; then forgets them. */
 bf_status bf_get_timing(bf_plan_t plan, double *ms, int *count);
 
+/* ---- allocation-free variant ------------------------------------------- */
+
+/* The paper has no counterpart to this entry point; it exists for callers
+ * that cannot allocate device memory while they run -- for example a
+ * real-time imaging pipeline that reserves all of its GPU memory at start-up,
+ * or an application that owns the device's memory budget and only lends
+ * this library its image buffers -- and so cannot create a plan.
+ *
+ * It runs what bf_execute runs for a plan with t_mode = BF_T_GLOBAL,
+ * trunc_rule = BF_RULE_ALG2 and FP32 planes: T by Algorithm 1, N and M by
+ * Algorithm 2, then the fused filter, from f_dev into out_dev (device images,
+ * row pitches in elements), asynchronously on `stream`.  It allocates
+ * nothing: all scratch lives in one fixed-size static device array of the
+ * library (under 32 KB per GPU, held until the process exits).  Limits:
+ * R = ceil(3 sigma_s) <= 48 (else BF_ERR_NOT_SUPPORTED) and the order needed
+ * for an image within [0, value_range], ceil(4 value_range^2 / (pi^2
+ * sigma_r^2)), <= 1024 (else BF_ERR_ORDER_TOO_LARGE); pixels outside
+ * [0, value_range] may push N past the table, and then the output is a copy
+ * of the input.  The first call on a device looks up the array's device
+ * address (cudaGetSymbolAddress) with that device current; make that first
+ * call before any stream capture.  Every call reuses the same array and
+ * clears what must start at zero, so calls whose work overlaps on the GPU
+ * (two streams, or two host threads without ordering) race on it: the caller
+ * must order them. */
+bf_status bf_execute_noalloc(const float *f_dev, size_t f_pitch, float *out_dev,
+                             size_t out_pitch, int H, int W, double sigma_s,
+                             double sigma_r, double eps, float value_range, void *stream);
+
 /* ---- single steps of the path (tests and profiling) ------------------- */
 
 /* Windowed max and min of f over the clipped (2R+1)^2 square (Prop.

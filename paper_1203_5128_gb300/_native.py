@@ -75,6 +75,7 @@ PROTOTYPES = {
     "bf_status_string": (ctypes.c_char_p, [_I]),
     "bf_maxmin": (_I, [_P, _I, _I, _Z, _I, _P, _P, _P]),
     "bf_set_timing": (_I, [_P, _I]),
+    "bf_execute_noalloc": (_I, [_P, _Z, _P, _Z, _I, _I, _D, _D, _D, ctypes.c_float, _P]),
     "bf_get_timing": (_I, [_P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(_I)]),
 }
 
