@@ -4,8 +4,8 @@
 Workload (the headline metric): one 4096 x 4096 8-bit-range image (seeded
 G8 generator), sigma_s = 8 (R = 24), sigma_r = 10.
   * tuned: Algorithm 2 of the paper -- exact T (Algorithm 1), eps = 1e-2
-    truncation by the sigma_r <= 10 rule (Chernoff) -- with the plane type and
-    filter of the fastest built variant;
+    truncation by the sigma_r <= 10 rule (Chernoff) -- with FP16 planes
+    filtered on the tensor cores (FP32 phases, demodulation and accumulation);
   * plain: the unaccelerated method, T = 255, no truncation, FP32 planes.
 A step is one bf_execute (T, N/M/weights, fused filter) of one image with its
 input resident in HBM; the L2 is flushed (256 MB write) before every timed
@@ -33,7 +33,8 @@ if ROOT not in sys.path:
 METRIC = "Mpixel/s at 4096² σ_r=10: tuned vs plain FP32, max-abs err ≤0.5 gray level"
 H = W = 4096
 SIGMA_S, SIGMA_R, EPS, SEED = 8.0, 10.0, 0.01, 5
-TUNED = dict(t_mode="global", trunc_rule="alg2", plane_dtype="fp32", filter="fir")
+TUNED = dict(t_mode="global", trunc_rule="alg2", plane_dtype="fp16", filter="fir")
+TUNED_FP32 = dict(t_mode="global", trunc_rule="alg2", plane_dtype="fp32", filter="fir")
 PLAIN = dict(t_mode="fixed", t_fixed=255.0, trunc_rule="alg2", plane_dtype="fp32", filter="fir")
 SM_COUNT_NOMINAL = 152
 FP32_LANES_PER_SM = 128
@@ -182,9 +183,10 @@ def reference_arm(args, rank: int):
 
 def workload_config():
     return {"workload": "4096x4096 G8 8-bit image, sigma_s=8 (R=24), sigma_r=10; tuned = "
-                        "Algorithm 2 (exact T, eps=1e-2) vs plain (T=255, eps=0, FP32)",
+                        "Algorithm 2 (exact T, eps=1e-2), FP16 planes on tcgen05 vs plain "
+                        "(T=255, eps=0, FP32 planes)",
             "H": H, "W": W, "sigma_s": SIGMA_S, "sigma_r": SIGMA_R, "eps": EPS,
-            "seed": SEED, "tuned": TUNED, "plain": PLAIN,
+            "seed": SEED, "tuned": TUNED, "tuned_fp32": TUNED_FP32, "plain": PLAIN,
             "l2": "flushed (256 MB write) before every timed step, outside the timed interval"}
 
 
@@ -198,6 +200,15 @@ def fp32_instr_per_px(N, M, R):
     z = 1 if N % 2 == 0 else 0
     taps = 2 * R + 1
     return F * (8 * taps + 7) + z * (4 * taps + 2) + 3
+
+
+def fir_flops_per_px(N, M, R):
+    """Algorithmic tensor work of the separable Gaussian per output pixel:
+    per kept pair 4 planes x 2 passes x (2R+1) multiply-adds (2 flops each),
+    per zero-frequency term the same (its planes are filtered too)."""
+    F = (N - M) - N // 2
+    z = 1 if N % 2 == 0 else 0
+    return (F + z) * 4 * 2 * (2 * R + 1) * 2
 
 
 def main():
@@ -271,6 +282,16 @@ def main():
     value = world * px * args.steps / (total_ms * 1e3)
     launches_per_step = 3 if TUNED["t_mode"] != "fixed" else 2
 
+    # ---- the same Algorithm 2 with FP32 planes (the fused FP32 path)
+    t32 = bf.bf_plan(H, W, SIGMA_S, SIGMA_R, EPS, **TUNED_FP32)
+    bf.bf_execute(t32, f, out)
+    torch.cuda.synchronize()
+    info_32 = bf.bf_get_info(t32)
+    s32 = max(1, min(args.plain_steps, args.steps))
+    t32_ms, t32_kms, t32_cnt = timed(t32, s32, 1)
+    t32_ms = max_over_ranks(t32_ms)
+    t32_value = world * px * s32 / (t32_ms * 1e3)
+
     # ---- plain FP32 (context for the metric's ratio)
     plain = bf.bf_plan(H, W, SIGMA_S, SIGMA_R, 0.0, **PLAIN)
     bf.bf_execute(plain, f, out)
@@ -298,24 +319,33 @@ def main():
             dist.destroy_process_group()
         return
 
-    # ---- roofline of the dominant kernel (K3, fused filter): FP32 pipe
+    # ---- roofline of the dominant kernel: K3-tc (tensor cores, FP16 planes)
     pk, pk_kind = peaks()
     sms = torch.cuda.get_device_properties(0).multi_processor_count
     mhz = float(pk.get("sm_max_mhz", 2070.0))
     peak_tinst = sms * FP32_LANES_PER_SM * mhz * 1e6 / 1e12
+    peak_tc = float(pk.get("bf16_tflops", 1900.0))       # FP16 dense rate = BF16 rate
     T_, N_, M_ = bf.bf_get_sets(tuned)
-    instr = fp32_instr_per_px(int(N_[0]), int(M_[0]), info_t.R) * px
     k3_ms = kms[2] / max(cnt, 1)
-    achieved = instr / (k3_ms * 1e-3) / 1e12
-    roof = {"bound": "alu", "achieved": achieved, "peak": peak_tinst, "unit": "Tinstr/s (FP32)",
-            "frac": achieved / peak_tinst, "traffic": None,
-            "kernel": "k_fwd32 (fused modulate/FIR/demodulate)",
-            "peak_source": "%d SMs x %d FP32 lanes x %.0f MHz (%s sm_max_mhz)" % (
-                sms, FP32_LANES_PER_SM, mhz, pk_kind),
-            "algorithmic_instr_per_launch": instr,
+    flops = fir_flops_per_px(int(N_[0]), int(M_[0]), info_t.R) * px
+    achieved = flops / (k3_ms * 1e-3) / 1e12
+    roof = {"bound": "tensor", "achieved": achieved, "peak": peak_tc, "unit": "TFLOP/s",
+            "frac": achieved / peak_tc, "traffic": None,
+            "kernel": "k_fwd_tc<fp16> (modulate / tcgen05 Toeplitz FIR / demodulate)",
+            "peak_source": "%s bf16_tflops (FP16 and BF16 share the dense tensor rate)" % pk_kind,
+            "algorithmic_flops_per_launch": flops,
             "launch_ms": k3_ms,
             "hbm_bytes_per_launch": 8 * px,
             "hbm_frac": (8 * px / (k3_ms * 1e-3) / 1e9) / float(pk.get("hbm_gbs", 6783.5))}
+    # the fused FP32 path on the same parameters, against the FP32 pipe
+    T32, N32, M32 = bf.bf_get_sets(t32)
+    k32_ms = t32_kms[2] / max(t32_cnt, 1)
+    i32 = fp32_instr_per_px(int(N32[0]), int(M32[0]), info_32.R) * px
+    roof32 = {"bound": "alu", "achieved": i32 / (k32_ms * 1e-3) / 1e12, "peak": peak_tinst,
+              "unit": "Tinstr/s (FP32)", "frac": i32 / (k32_ms * 1e-3) / 1e12 / peak_tinst,
+              "kernel": "k_fwd32 (FP32 planes, SIMT FIR)", "launch_ms": k32_ms,
+              "peak_source": "%d SMs x %d FP32 lanes x %.0f MHz (%s sm_max_mhz)" % (
+                  sms, FP32_LANES_PER_SM, mhz, pk_kind)}
     p_k3 = p_kms[2] / max(p_cnt, 1)
     p_instr = fp32_instr_per_px(info_p.N, info_p.M, info_p.R) * px
 
@@ -329,7 +359,7 @@ def main():
     line = {
         "metric": METRIC, "value": value, "unit": "Mpixel/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f16",
         "data": "synthetic", "config": workload_config(),
         "roofline": roof, "cpu_baseline": cpu,
         "e2e": {"value": e2e_value, "unit": "Mpixel/s", "h2d_bytes_per_step": 4 * px,
@@ -342,6 +372,7 @@ def main():
         "plain": {"value": plain_value, "ms_per_step": p_ms / p_steps, "N": info_p.N,
                   "K": info_p.K, "forward_ms": p_k3,
                   "fp32_frac": p_instr / (p_k3 * 1e-3) / 1e12 / peak_tinst},
+        "tuned_fp32": {"value": t32_value, "ms_per_step": t32_ms / s32, "roofline": roof32},
         "speedup_vs_plain": value / plain_value,
     }
     print(json.dumps(line), flush=True)

@@ -18,7 +18,8 @@ OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libbf.so")
 INCLUDE = os.path.join(ROOT, "include")
 
-SOURCES = ["bf_api.cu", "bf_range.cu", "bf_params.cu", "bf_fwd32.cu", "bf_noalloc.cu"]
+SOURCES = ["bf_api.cu", "bf_range.cu", "bf_params.cu", "bf_fwd32.cu", "bf_fwd_tc.cu",
+           "bf_noalloc.cu"]
 HEADERS = ["bf_internal.cuh"]
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

@@ -227,8 +227,12 @@ bf_status bf_plan(int H, int W, double sigma_s, double sigma_r, double eps, cons
         if (o.reserved[i]) return BF_ERR_INVALID_ARG;
     if (o.filter == BF_FILTER_AUTO) o.filter = BF_FILTER_FIR;
     if (o.filter != BF_FILTER_FIR) return BF_ERR_NOT_SUPPORTED;
-    if (o.plane_dtype != BF_PLANES_FP32) return BF_ERR_NOT_SUPPORTED;
+    if (o.plane_dtype < BF_PLANES_FP32 || o.plane_dtype > BF_PLANES_FP16) return BF_ERR_INVALID_ARG;
     if (o.t_mode == BF_T_TILE && (o.t_tile < 64 || o.t_tile % 64)) return BF_ERR_INVALID_ARG;
+    // the 16-bit planes run on the tensor cores with 128 x 32 output tiles,
+    // which must nest inside the T-tiles
+    if (o.plane_dtype != BF_PLANES_FP32 && o.t_mode == BF_T_TILE && o.t_tile % 128)
+        return BF_ERR_INVALID_ARG;
     if (o.t_mode == BF_T_FIXED && !(o.t_fixed > 0.f)) o.t_fixed = o.value_range;
     if (o.spin_limit <= 0) o.spin_limit = 1ll << 22;
 
@@ -237,7 +241,11 @@ bf_status bf_plan(int H, int W, double sigma_s, double sigma_r, double eps, cons
     const int R = (int)Rr;
     if (o.t_mode != BF_T_FIXED && R > range_max_radius()) return BF_ERR_NOT_SUPPORTED;
     int th = 0, tw = 0;
-    fwd32_tile(R, &th, &tw);
+    if (o.plane_dtype == BF_PLANES_FP32) {
+        fwd32_tile(R, &th, &tw);
+    } else if (R <= fwd_tc_max_radius()) {
+        fwd_tc_tile(&th, &tw);
+    }
     if (!th) return BF_ERR_NOT_SUPPORTED;
 
     const double Tcap = o.t_mode == BF_T_FIXED ? (double)o.t_fixed : (double)o.value_range;
@@ -325,7 +333,12 @@ bf_status bf_execute(bf_plan_t p, const float* f, size_t fp, float* out, size_t 
     cudaStream_t s = (cudaStream_t)stream;
     BF_CUDA(cudaSetDevice(p->device));
     BF_CUDA(enqueue_params(p, f, fp, s));
-    BF_CUDA(launch_fwd32(forward_args(p, f, fp, out, op), s));
+    if (p->opt.plane_dtype == BF_PLANES_FP32)
+        BF_CUDA(launch_fwd32(forward_args(p, f, fp, out, op), s));
+    else
+        BF_CUDA(launch_fwd_tc(forward_args(p, f, fp, out, op),
+                              p->opt.plane_dtype == BF_PLANES_BF16, p->opt.spin_limit,
+                              p->d_status, s));
     BF_CUDA(mark(p, 3, s));
     if (p->timing && p->n_timed < kMaxTimed) ++p->n_timed;
     p->executed = 1;

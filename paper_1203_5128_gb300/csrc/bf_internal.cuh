@@ -86,4 +86,10 @@ void fwd32_tile(int R, int* th, int* tw);
 size_t fwd32_smem(int R, int th, int tw);
 cudaError_t launch_fwd32(const FwdArgs& a, cudaStream_t s);
 
+// K3-tc (FP16 / BF16 planes, tcgen05): 128 x 32 output tiles, R <= max radius.
+int fwd_tc_max_radius();
+void fwd_tc_tile(int* th, int* tw);
+cudaError_t launch_fwd_tc(const FwdArgs& a, bool bf16, long long spin_limit, unsigned* status,
+                          cudaStream_t s);
+
 }  // namespace bf

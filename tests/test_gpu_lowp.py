@@ -1,0 +1,104 @@
+"""GPU parity of the tensor-core forward (FP16 / BF16 planes, FP32
+accumulation in TMEM, FP32 phases and demodulation) against the FP64 oracle
+run with the same (T, N, M).
+
+Bar: the reduced-precision forms must stay within 0.5 gray level (the
+metric's bound) for FP16 planes; BF16 planes (8-bit significand) are
+reported and held to a looser stated bound.  T, N and M are bit-exact as in
+the FP32 tests (computed by the same K1 / K2).
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1203_5128_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"fp16": 0.5, "bf16": 2.0}     # gray levels (8-bit); 16-bit images scale by 257
+
+
+@pytest.fixture(scope="module")
+def bf():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need CUDA"
+    from paper_1203_5128_gb300 import build
+    build.build()
+    import paper_1203_5128_gb300 as m
+    return m
+
+
+def to_dev(a):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).cuda()
+
+
+def run(bf, f, ss, sr, eps, planes, mode="global", rule="alg2", tile=128, vr=255.0, tf=None):
+    import torch
+    H, W = f.shape
+    kw = dict(t_mode=mode, trunc_rule=rule, t_tile=tile, value_range=vr, plane_dtype=planes)
+    if tf is not None:
+        kw["t_fixed"] = tf
+    plan = bf.bf_plan(H, W, ss, sr, eps, **kw)
+    out = bf.bf_execute(plan, to_dev(f))
+    torch.cuda.synchronize()
+    assert bf.bf_get_device_status(plan) == 0
+    p = oracle.resolve(f, ss, sr, eps, t_mode=mode, rule=rule, t_tile=tile, value_range=vr,
+                       t_fixed=tf)
+    T, N, M = bf.bf_get_sets(plan)
+    assert np.array_equal(T, p.T.ravel()) and np.array_equal(N, p.N.ravel().astype(np.int32))
+    assert np.array_equal(M, p.M.ravel().astype(np.int32))
+    return out.cpu().numpy().astype(np.float64), p
+
+
+CASES = [
+    # H, W, sigma_s, sigma_r, eps, mode, rule, tile
+    (256, 256, 3.0, 30.0, 0.0, "fixed", "alg2", 128),
+    (200, 150, 2.0, 15.0, 0.01, "global", "trunc", 128),
+    (300, 170, 4.0, 10.0, 0.01, "global", "alg2", 128),      # Chernoff band
+    (256, 320, 5.0, 20.0, 0.01, "tile", "alg2", 128),        # per-tile T
+    (130, 33, 8.0, 10.0, 0.01, "global", "alg2", 128),       # R = 24, ragged tiles
+    (1, 90, 2.0, 20.0, 0.01, "global", "alg2", 128),
+    (90, 1, 2.0, 20.0, 0.01, "global", "alg2", 128),
+]
+
+
+@pytest.mark.parametrize("planes", ["fp16", "bf16"])
+@pytest.mark.parametrize("case", CASES, ids=lambda c: "%dx%d_s%g_r%g_%s" % (c[0], c[1], c[2], c[3], c[5]))
+def test_lowp_matches_oracle(bf, planes, case):
+    H, W, ss, sr, eps, mode, rule, tile = case
+    f = synth.g8(H, W, seed=H * 7 + W)
+    tf = 255.0 if mode == "fixed" else None
+    out, p = run(bf, f, ss, sr, eps, planes, mode, rule, tile, tf=tf)
+    ref = oracle.shiftable(f, ss, sr, p)
+    err = np.max(np.abs(out - ref))
+    print("%s %s: max-abs %.4f gray levels" % (planes, case, err))
+    assert err <= TOL[planes], "%s max-abs %.3g gray levels" % (planes, err)
+
+
+@pytest.mark.parametrize("planes", ["fp16", "bf16"])
+def test_lowp_16bit_image(bf, planes):
+    """16-bit range (G16): planes are range-normalised, so the bound scales
+    with the range (257 x the 8-bit bound, in 16-bit gray levels)."""
+    f = synth.g16(192, 160, seed=2)
+    out, p = run(bf, f, 4.0, 2000.0, 0.01, planes, "global", "alg2", 128, vr=65535.0)
+    ref = oracle.shiftable(f, 4.0, 2000.0, p)
+    err = np.max(np.abs(out - ref))
+    print("%s 16-bit: max-abs %.3f (16-bit gray levels), N=%d M=%d" % (planes, err, p.N[0, 0],
+                                                                     p.M[0, 0]))
+    assert err <= 257 * TOL[planes]
+
+
+def test_tuned_metric_workload_sampled(bf):
+    """The metric's tuned form at full size (4096^2 G8, sigma_s = 8,
+    sigma_r = 10, Algorithm 2 with eps = 1e-2, FP16 planes): <= 0.5 gray
+    level against the oracle with the same (T, N, M), at sampled pixels."""
+    f = synth.g8(4096, 4096, seed=5)
+    out, p = run(bf, f, 8.0, 10.0, 0.01, "fp16", "global", "alg2", 128)
+    rng = np.random.default_rng(9)
+    ys = np.concatenate([rng.integers(0, 4096, 150), [0, 4095, 0, 4095, 127, 128, 2048]])
+    xs = np.concatenate([rng.integers(0, 4096, 150), [0, 4095, 4095, 0, 31, 32, 2048]])
+    ref = oracle.direct(f, 8.0, 10.0, p, points=(ys, xs))
+    err = np.max(np.abs(out[ys, xs] - ref))
+    print("tuned fp16 4096^2: max-abs %.4f gray levels at %d pixels" % (err, ys.size))
+    assert err <= 0.5
