@@ -1,28 +1,39 @@
 // K3-tc: fused SHIFTABLE-BF forward with FP16 / BF16 planes on the 5th-gen
-// tensor cores (tcgen05, accumulators in TMEM).
+// tensor cores (tcgen05, accumulators in TMEM), warp-specialised and
+// pipelined across the terms of phi_eps.
 //
 // Same method as K3 (Sec. 1.2, eqs. (f1)-(f2) with phi_eps of eq. (approx)):
 // per kept pair, modulate, Gaussian-filter the four planes, demodulate and
-// accumulate num / den.  The difference is step 3, the spatial Gaussian: the
-// separable FIR over a tile is written as two dense products with constant
-// banded Toeplitz matrices, which is exactly the shape tcgen05.mma executes:
+// accumulate num / den.  The spatial Gaussian of a 128 x 32 output tile is
+// two dense products with constant banded matrices, the shape tcgen05.mma
+// executes:
 //
-//   vertical   D1[y, (p, j)] = sum_r Gv[y, r] * P[(p, j), r]      M = 128 rows y
-//   horizontal D2[y, (p, x)] = sum_j V_p[y, j] * Gh[x, j]          (per plane p)
+//   vertical   D1[m, (p, j)] = sum_r Gv[m, r] * P[(p, j), r]     (M = 128)
+//   horizontal D2[m, (p, n)] = sum_j V_p[m, j] * Gh[n, j]        (per plane p)
 //
-// with Gv[y, r] = g(r - y - R), Gh[x, j] = g(j - x - R) (zero off the band),
-// P the four modulated planes of the tile + halo stored K-major (r fastest),
-// and V_p = D1 converted to FP16/BF16 by the threads (TMEM -> registers ->
-// shared memory, K-major with j fastest, so no transpose is needed).  All
-// operands are K-major, no swizzle; accumulation is FP32 in TMEM.  Phases
-// and the demodulation stay FP32 on the CUDA cores.
+// P holds the four modulated planes of the tile + halo (K-major, r fastest);
+// V_p is D1 converted to 16 bits by the threads (TMEM -> registers -> shared,
+// K-major with j fastest: no transpose).  Output rows and columns are taken
+// in reverse order (m = 127 - y, n = 31 - x), which makes Gv[m, r] =
+// g(r + m - 127 - R) and Gh[n, j] = g(j + n - 31 - R) depend on the sum of
+// the indices: every 8 x 8 core matrix of such a Hankel matrix depends only
+// on the sum of its block indices, so one row of distinct core matrices,
+// read with both descriptor strides equal to 128 bytes, stands for the whole
+// matrix (6 KB instead of 50 KB of shared memory).
 //
-// Tile: 128 output rows (the MMA's M) x 32 output columns; radius R <= 24.
-// One CTA per tile, 256 threads: every thread modulates a fixed set of
-// (column, 8-row) items whose centred values stay in registers for the
-// whole launch; thread 0 issues the MMAs; all threads move data out of TMEM.
-// Every wait on the MMA completion barrier is bounded (spin_limit polls);
-// if it runs out the CTA records BF_DEV_TIMEOUT, frees its TMEM and exits.
+// Roles (416 threads, one CTA per SM):
+//   warps 0-3   TMEM lane quarters: D1 -> V (shared), then D2 -> demodulate
+//               into num / den registers (their output row), normalise, store;
+//   warps 4-11  modulate the halo planes of pair k+1 while the tensor core
+//               and warps 0-3 work on pair k;
+//   warp 12     allocates TMEM, issues the MMAs, frees TMEM.
+// Handshakes are mbarriers; every wait is bounded (spin_limit polls) and a
+// wait that runs out sets BF_DEV_TIMEOUT, tells the other roles to stop,
+// lets the tensor core drain (again bounded) and frees TMEM.
+//
+// The planes are 16-bit, so their phases need no more than FP32 single
+// products: theta = (omega c0) * ((f - c0) / c0), with the same rounding at
+// the halo pixel (modulation) and at the output pixel (demodulation).
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 #include <math.h>
@@ -32,29 +43,16 @@
 namespace bf {
 namespace {
 
-constexpr double kTwoPi = 6.283185307179586476925286766559;
-constexpr float k2PiHi = (float)kTwoPi;
-constexpr float k2PiLo = (float)(kTwoPi - (double)(float)kTwoPi);
-constexpr float kInv2Pi = (float)(1.0 / kTwoPi);
-
-constexpr int TH = 128;           // output rows per tile = MMA M
-constexpr int TW = 32;            // output columns per tile
-constexpr int NT = 256;           // threads
-constexpr int kMaxItems = 7;      // modulation items per thread (R <= 24)
-constexpr int kCsStride = 36;     // fp32 words per row of the output cos / sin
+constexpr int TH = 128;          // output rows per tile = MMA M
+constexpr int TW = 32;           // output columns per tile
+constexpr int kEpiWarps = 4;
+constexpr int kModWarps = 8;
+constexpr int NT = (kEpiWarps + kModWarps + 1) * 32;   // 416
+constexpr int kModThreads = kModWarps * 32;
+constexpr int kEpiThreads = kEpiWarps * 32;
+constexpr int kMaxItems = 7;     // modulation items per thread (R <= 24)
 constexpr int kTmemCols = 512;
-
-__device__ __forceinline__ void phase_cs(float v, float om_hi, float om_lo, float& c, float& s)
-{
-    const float p = __fmul_rn(om_hi, v);
-    float e = fmaf(om_hi, v, -p);
-    e = fmaf(om_lo, v, e);
-    const float q = rintf(__fmul_rn(p, kInv2Pi));
-    float r = fmaf(-q, k2PiHi, p);
-    r = fmaf(-q, k2PiLo, r);
-    r = __fadd_rn(r, e);
-    __sincosf(r, &s, &c);
-}
+constexpr int kPnStride = TW + 1;   // fp32 words per row of the output pixels' scaled f
 
 template <bool kBF16>
 __device__ __forceinline__ uint32_t pack2(float a, float b)
@@ -126,31 +124,49 @@ __device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::aft
 __device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 
-__device__ __forceinline__ void mbar_init(uint32_t mbar)
+__device__ __forceinline__ void mbar_init(uint32_t mbar, uint32_t count)
 {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mbar) : "memory");
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(mbar), "r"(count) : "memory");
 }
 
-// Bounded wait for the phase with the given parity; false if it ran out.
-__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity, long long limit)
+__device__ __forceinline__ void mbar_arrive(uint32_t mbar)
 {
-    for (long long i = 0; i < limit; ++i) {
-        uint32_t done;
-        asm volatile(
-            "{\n\t.reg .pred p;\n\t"
-            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-            "selp.u32 %0, 1, 0, p;\n\t}\n"
-            : "=r"(done)
-            : "r"(mbar), "r"(parity)
-            : "memory");
-        if (done) return true;
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(mbar) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try(uint32_t mbar, uint32_t parity)
+{
+    uint32_t done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}\n"
+        : "=r"(done)
+        : "r"(mbar), "r"(parity)
+        : "memory");
+    return done != 0;
+}
+
+// Bounded wait for the phase of the given parity.  Returns false when the
+// CTA is stopping: this wait ran out (it then raises the stop flag) or
+// another role raised it.
+__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity, long long limit,
+                                          volatile int* stop)
+{
+    for (long long i = 0;; ++i) {
+        if (mbar_try(mbar, parity)) return true;
+        if ((i & 63) == 63) {
+            if (*stop) return false;
+            if (i >= limit) {
+                *stop = 1;
+                return false;
+            }
+        }
     }
-    return false;
 }
 
-// n (16 or 32) consecutive 32-bit TMEM columns of this thread's lane; the
-// wait is in the same statement, so no use of v can be scheduled before it.
+// TMEM loads of this thread's lane; the wait is in the same statement, so no
+// use of the outputs can be scheduled before it.
 __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v)
 {
     uint32_t r[16];
@@ -187,12 +203,41 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v)
     for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+// Eight columns from each of four TMEM column ranges (one wait).
+__device__ __forceinline__ void tmem_ld4x8(uint32_t t0, uint32_t t1, uint32_t t2, uint32_t t3,
+                                           float* a, float* b, float* c, float* d)
+{
+    uint32_t r[32];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%32];\n\t"
+        "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%8,%9,%10,%11,%12,%13,%14,%15}, [%33];\n\t"
+        "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%16,%17,%18,%19,%20,%21,%22,%23}, [%34];\n\t"
+        "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%24,%25,%26,%27,%28,%29,%30,%31}, [%35];\n\t"
+        "tcgen05.wait::ld.sync.aligned;"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
+          "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]),
+          "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+          "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]),
+          "=r"(r[31])
+        : "r"(t0), "r"(t1), "r"(t2), "r"(t3)
+        : "memory");
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        a[i] = __uint_as_float(r[i]);
+        b[i] = __uint_as_float(r[8 + i]);
+        c[i] = __uint_as_float(r[16 + i]);
+        d[i] = __uint_as_float(r[24 + i]);
+    }
+}
+
 // ---- geometry -------------------------------------------------------------
 
 struct TcGeo {
     int R, RH, RW, RHp, RWp;
-    uint32_t offA1, offB2, offP, offCS, bytes;   // byte offsets in dynamic smem
-    uint32_t sboA1, sboB2, sboB1, sboA2, planeA2;
+    int nA1, nB2;                                   // Hankel core matrices
+    uint32_t offA1, offB2, offB1, offA2, offPn, offBar, bytes;
+    uint32_t sboB1, sboA2, planeA2;
     __host__ __device__ TcGeo(int R_)
     {
         R = R_;
@@ -200,37 +245,40 @@ struct TcGeo {
         RW = TW + 2 * R;
         RHp = (RH + 15) / 16 * 16;
         RWp = (RW + 15) / 16 * 16;
-        sboA1 = (RHp / 8) * 128;       // A1: 128 rows (y) x RHp (r)
-        sboB2 = (RWp / 8) * 128;       // B2: 32 rows (x) x RWp (j)
-        sboB1 = (RHp / 8) * 128;       // B1: 4 RWp rows (p, j) x RHp (r)
-        sboA2 = (RWp / 8) * 128;       // A2: per plane 128 rows (y) x RWp (j)
+        nA1 = TH / 8 + RHp / 8 - 1;
+        nB2 = TW / 8 + RWp / 8 - 1;
+        sboB1 = (RHp / 8) * 128;       // B1: 4 RWp rows (plane, j) x RHp (r)
+        sboA2 = (RWp / 8) * 128;       // A2: per plane 128 rows (m) x RWp (j)
         planeA2 = TH * RWp * 2;
-        const uint32_t a1 = TH * RHp * 2, b2 = TW * RWp * 2;
-        const uint32_t b1 = 4u * RWp * RHp * 2, a2 = 4u * planeA2;
-        const uint32_t p = b1 > a2 ? b1 : a2;
         offA1 = 0;
-        offB2 = offA1 + a1;
-        offP = offB2 + b2;
-        offCS = offP + p;
-        bytes = offCS + 2u * TH * kCsStride * 4 + 64;   // + barrier and TMEM slot
+        offB2 = offA1 + nA1 * 128;
+        offB1 = offB2 + nB2 * 128;
+        offA2 = offB1 + 4u * RWp * RHp * 2;
+        offPn = offA2 + 4u * planeA2;
+        offBar = offPn + TH * kPnStride * 4;
+        bytes = offBar + 64;
     }
 };
 
-template <bool kBF16>
+// barrier slots (8 bytes each) after the operand buffers
+enum { kBarB1Full = 0, kBarC1, kBarA2Full, kBarC2, kBarD2Free, kNumBars };
+
+template <bool kBF16, int NCH>
 __global__ void __launch_bounds__(NT, 1) k_fwd_tc(FwdArgs a, long long spin_limit,
                                                     unsigned* status)
 {
+    constexpr int RWp = NCH * 16;
     extern __shared__ __align__(1024) unsigned char smem[];
     const TcGeo G(a.R);
     const int R = a.R;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int by = blockIdx.y * TH, bx = blockIdx.x * TW;
     const int gy0 = by - R, gx0 = bx - R;
-    float* cs = reinterpret_cast<float*>(smem + G.offCS);           // cos, then sin
-    uint64_t* mbar_p = reinterpret_cast<uint64_t*>(smem + G.offCS + 2 * TH * kCsStride * 4);
-    uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar_p + 1);
     const uint32_t sbase = smem_u32(smem);
-    const uint32_t mbar = smem_u32(mbar_p);
+    const uint32_t bar0 = sbase + G.offBar;
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(smem + G.offBar + 8 * kNumBars);
+    volatile int* stop = reinterpret_cast<volatile int*>(smem + G.offBar + 8 * kNumBars + 8);
+    auto bar = [&](int i) { return bar0 + 8u * i; };
 
     const int set = a.set_tile ? (by / a.set_tile) * a.sets_x + (bx / a.set_tile) : 0;
     const SetHdr hd = a.hdr[set];
@@ -245,244 +293,234 @@ __global__ void __launch_bounds__(NT, 1) k_fwd_tc(FwdArgs a, long long spin_limi
         return;
     }
 
-    // ---- TMEM, barrier
-    if (warp == 0) {
+    // ---- set-up: TMEM, barriers, constant Hankel operands
+    if (warp == kEpiWarps + kModWarps) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
                      ::"r"(smem_u32(tslot)), "r"(kTmemCols) : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
-    if (tid == 0) mbar_init(mbar);
-
-    // ---- constant Toeplitz operands: A1 = Gv (128 x RHp), B2 = Gh (32 x RWp)
-    for (int i = tid; i < TH * (G.RHp / 8); i += NT) {
-        const int y = i / (G.RHp / 8), k8 = i % (G.RHp / 8);
-        uint32_t w[4];
-#pragma unroll
-        for (int h = 0; h < 4; ++h) {
-            float t2[2];
-#pragma unroll
-            for (int e = 0; e < 2; ++e) {
-                const int t = k8 * 8 + 2 * h + e - y;      // tap index r - y in [0, 2R]
-                t2[e] = (t >= 0 && t <= 2 * R) ? a.taps[t] : 0.f;
-            }
-            w[h] = pack2<kBF16>(t2[0], t2[1]);
-        }
-        const uint32_t off = G.offA1 + (y / 8) * G.sboA1 + k8 * 128 + (y % 8) * 16;
-        *reinterpret_cast<uint4*>(smem + off) = make_uint4(w[0], w[1], w[2], w[3]);
+    if (tid == 0) {
+        mbar_init(bar(kBarB1Full), kModThreads);
+        mbar_init(bar(kBarC1), 1);
+        mbar_init(bar(kBarA2Full), kEpiThreads);
+        mbar_init(bar(kBarC2), 1);
+        mbar_init(bar(kBarD2Free), kEpiThreads);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        *stop = 0;
     }
-    for (int i = tid; i < TW * (G.RWp / 8); i += NT) {
-        const int x = i / (G.RWp / 8), k8 = i % (G.RWp / 8);
-        uint32_t w[4];
+    // Gv (rows reversed): core matrix d holds g(8d + i + e - (TH-1) - R)
+    for (int i = tid; i < G.nA1 * 8; i += NT) {
+        const int d = i / 8, row = i % 8;
+        float v[8];
 #pragma unroll
-        for (int h = 0; h < 4; ++h) {
-            float t2[2];
-#pragma unroll
-            for (int e = 0; e < 2; ++e) {
-                const int t = k8 * 8 + 2 * h + e - x;      // j - x in [0, 2R]
-                t2[e] = (t >= 0 && t <= 2 * R) ? a.taps[t] : 0.f;
-            }
-            w[h] = pack2<kBF16>(t2[0], t2[1]);
+        for (int e = 0; e < 8; ++e) {
+            const int t = 8 * d + row + e - (TH - 1);    // r - y, tap index in [0, 2R]
+            v[e] = (t >= 0 && t <= 2 * R) ? a.taps[t] : 0.f;
         }
-        const uint32_t off = G.offB2 + (x / 8) * G.sboB2 + k8 * 128 + (x % 8) * 16;
-        *reinterpret_cast<uint4*>(smem + off) = make_uint4(w[0], w[1], w[2], w[3]);
+        store_row8<kBF16>(smem + G.offA1 + d * 128 + row * 16, v);
     }
-
-    // ---- my modulation items: (column j, rows rb*8 .. rb*8+7) of the halo
-    // region, j in [0, RWp), rb in [0, RHp/8); values kept in registers
-    const int n_items = G.RWp * (G.RHp / 8);
-    float fv[kMaxItems][8];
-    uint32_t valid[kMaxItems];
+    // Gh (columns reversed): core matrix d holds g(8d + i + e - (TW-1) - R)
+    for (int i = tid; i < G.nB2 * 8; i += NT) {
+        const int d = i / 8, row = i % 8;
+        float v[8];
 #pragma unroll
-    for (int t = 0; t < kMaxItems; ++t) {
-        valid[t] = 0u;
-        const int it = tid + t * NT;
-        const int j = it % G.RWp, rb = it / G.RWp;
-        const int gx = gx0 + j;
-#pragma unroll
-        for (int i = 0; i < 8; ++i) {
-            fv[t][i] = 0.f;
-            const int r = rb * 8 + i, gy = gy0 + r;
-            if (it < n_items && j < G.RW && r < G.RH && gx >= 0 && gx < a.W && gy >= 0 &&
-                gy < a.H) {
-                fv[t][i] = __ldg(a.f + (size_t)gy * a.f_pitch + gx) - c0;
-                valid[t] |= 1u << i;
-            }
+        for (int e = 0; e < 8; ++e) {
+            const int t = 8 * d + row + e - (TW - 1);    // j - x
+            v[e] = (t >= 0 && t <= 2 * R) ? a.taps[t] : 0.f;
         }
+        store_row8<kBF16>(smem + G.offB2 + d * 128 + row * 16, v);
     }
-
-    // ---- epilogue ownership: lane quarter q = warp % 4 (TMEM lanes 32q..),
-    // output row y = 32q + lane, columns x in [16h, 16h + 16), h = warp / 4
-    const int q = warp & 3, hcol = warp >> 2;
-    const int yl = 32 * q + lane;
-    float num[16], den[16];
-#pragma unroll
-    for (int i = 0; i < 16; ++i) num[i] = den[i] = 0.f;
-
+    fence_async_smem();
     fence_before();
     __syncthreads();
     fence_after();
     const uint32_t tbase = *tslot;
-    const uint32_t tD1 = tbase;                     // 4 RWp columns
-    const uint32_t tD2 = tbase + 4 * G.RWp;         // 128 columns
-    const uint32_t tlane = (uint32_t)(32 * q) << 16;
-
-    const uint32_t idesc1 = idesc_f16(TH, 2 * G.RWp, kBF16);   // N = 2 RWp per MMA
-    const uint32_t idesc2 = idesc_f16(TH, TW, kBF16);
+    const uint32_t tD1 = tbase;                  // 4 RWp columns
+    const uint32_t tD2 = tbase + 4 * RWp;        // 4 x 32 columns
     const Pair* pr = a.pairs + (size_t)set * a.cap_pairs;
     const int K = hd.F + hd.z;
-    uint32_t phase = 0;
-    bool failed = false;
 
-    for (int k = 0; k < K && !failed; ++k) {
-        float om_hi = 0.f, om_lo = 0.f, Wk = hd.w0;
-        if (k < hd.F) {
-            const Pair p = pr[k];
-            om_hi = p.om_hi;
-            om_lo = p.om_lo;
-            Wk = p.W;
-        }
-
-        // (1) modulate into B1 (K-major: rows (plane, j), K = r) and the
-        //     FP32 cos / sin of the output pixels
+    if (warp >= kEpiWarps && warp < kEpiWarps + kModWarps) {
+        // ================= modulation warps =================
+        const int mt = tid - kEpiThreads;
+        const int n_items = RWp * (G.RHp / 8);
+        float pn[kMaxItems][8];
+        uint32_t valid[kMaxItems];
 #pragma unroll
         for (int t = 0; t < kMaxItems; ++t) {
-            const int it = tid + t * NT;
-            if (it >= n_items) break;
-            const int j = it % G.RWp, rb = it / G.RWp;
-            float cv[8], sv[8], av[8], bv[8];
+            valid[t] = 0u;
+            const int it = mt + t * kModThreads;
+            const int j = it % RWp, rb = it / RWp;
+            const int gx = gx0 + j;
 #pragma unroll
             for (int i = 0; i < 8; ++i) {
-                float c = 0.f, s = 0.f;
-                if (valid[t] & (1u << i)) phase_cs(fv[t][i], om_hi, om_lo, c, s);
-                const float pn = fv[t][i] * inv_c0;
-                cv[i] = c;
-                sv[i] = s;
-                av[i] = pn * c;
-                bv[i] = pn * s;
-                const int y = rb * 8 + i - R, x = j - R;
-                if (y >= 0 && y < TH && x >= 0 && x < TW) {
-                    cs[y * kCsStride + x] = c;
-                    cs[TH * kCsStride + y * kCsStride + x] = s;
+                pn[t][i] = 0.f;
+                const int r = rb * 8 + i, gy = gy0 + r;
+                if (it < n_items && j < G.RW && r < G.RH && gx >= 0 && gx < a.W && gy >= 0 &&
+                    gy < a.H) {
+                    const float f = __ldg(a.f + (size_t)gy * a.f_pitch + gx);
+                    pn[t][i] = __fmul_rn(__fsub_rn(f, c0), inv_c0);
+                    valid[t] |= 1u << i;
                 }
             }
-            store_row8<kBF16>(smem + G.offP + ((0 * G.RWp + j) / 8) * G.sboB1 + rb * 128 +
-                                  ((0 * G.RWp + j) % 8) * 16, av);
-            store_row8<kBF16>(smem + G.offP + ((1 * G.RWp + j) / 8) * G.sboB1 + rb * 128 +
-                                  ((1 * G.RWp + j) % 8) * 16, bv);
-            store_row8<kBF16>(smem + G.offP + ((2 * G.RWp + j) / 8) * G.sboB1 + rb * 128 +
-                                  ((2 * G.RWp + j) % 8) * 16, cv);
-            store_row8<kBF16>(smem + G.offP + ((3 * G.RWp + j) / 8) * G.sboB1 + rb * 128 +
-                                  ((3 * G.RWp + j) % 8) * 16, sv);
         }
-        fence_async_smem();
-        __syncthreads();
-
-        // (2) vertical pass on the tensor cores: D1 = Gv * P^T
-        if (tid == 0) {
-            fence_after();
-            for (int half = 0; half < 2; ++half) {
-                const uint32_t nb = sbase + G.offP + (uint32_t)(half * 2 * G.RWp / 8) * G.sboB1;
-                for (int ks = 0; ks < G.RHp / 16; ++ks) {
-                    const uint64_t da = sdesc(sbase + G.offA1 + ks * 256, 128, G.sboA1);
-                    const uint64_t db = sdesc(nb + ks * 256, 128, G.sboB1);
-                    mma_f16(tD1 + half * 2 * G.RWp, da, db, idesc1, ks > 0);
-                }
-            }
-            mma_commit(mbar);
-        }
-        bool ok = mbar_wait(mbar, phase, spin_limit);
-        if (__syncthreads_or(!ok)) { failed = true; break; }
-        phase ^= 1u;
-        fence_after();
-
-        // (3) D1 (FP32, TMEM) -> A2 (16-bit, shared, K-major: rows y, K = j)
+        for (int k = 0; k < K; ++k) {
+            const float wc = k < hd.F ? __fmul_rn(pr[k].om_hi, c0) : 0.f;
+            if (k > 0 && !mbar_wait(bar(kBarC1), (k - 1) & 1, spin_limit, stop)) break;
 #pragma unroll
-        for (int pp = 0; pp < 2; ++pp) {
-            const int pl = 2 * hcol + pp;
-            for (int c0c = 0; c0c < G.RWp; c0c += 32) {
-                const bool two = c0c + 16 < G.RWp;
-                float v[32];
-                if (two) tmem_ld32(tD1 + tlane + pl * G.RWp + c0c, v);
-                else tmem_ld16(tD1 + tlane + pl * G.RWp + c0c, v);
-                const uint32_t off = G.offP + pl * G.planeA2 + (yl / 8) * G.sboA2 +
-                                     (c0c / 8) * 128 + (yl % 8) * 16;
-                store_row8<kBF16>(smem + off, v);
-                store_row8<kBF16>(smem + off + 128, v + 8);
-                if (two) {
-                    store_row8<kBF16>(smem + off + 256, v + 16);
-                    store_row8<kBF16>(smem + off + 384, v + 24);
-                }
-            }
-        }
-        fence_async_smem();
-        fence_before();
-        __syncthreads();
-
-        // (4) horizontal pass: D2_p = V_p * Gh^T for the four planes
-        if (tid == 0) {
-            fence_after();
-            for (int pl = 0; pl < 4; ++pl) {
-                for (int ks = 0; ks < G.RWp / 16; ++ks) {
-                    const uint64_t da = sdesc(sbase + G.offP + pl * G.planeA2 + ks * 256, 128,
-                                              G.sboA2);
-                    const uint64_t db = sdesc(sbase + G.offB2 + ks * 256, 128, G.sboB2);
-                    mma_f16(tD2 + pl * TW, da, db, idesc2, ks > 0);
-                }
-            }
-            mma_commit(mbar);
-        }
-        ok = mbar_wait(mbar, phase, spin_limit);
-        if (__syncthreads_or(!ok)) { failed = true; break; }
-        phase ^= 1u;
-        fence_after();
-
-        // (5) demodulate and accumulate (eqs. (f1), (f2)): numerator planes,
-        //     then denominator planes, 32 TMEM columns at a time
-        {
-            const float* crow = cs + yl * kCsStride + 16 * hcol;
-            const float* srow = crow + TH * kCsStride;
+            for (int t = 0; t < kMaxItems; ++t) {
+                const int it = mt + t * kModThreads;
+                if (it >= n_items) break;
+                const int j = it % RWp, rb = it / RWp;
+                float cv[8], sv[8], av[8], bv[8];
 #pragma unroll
-            for (int part = 0; part < 2; ++part) {
-                float va[16], vb[16];
-                tmem_ld16(tD2 + tlane + (2 * part) * TW + 16 * hcol, va);
-                tmem_ld16(tD2 + tlane + (2 * part + 1) * TW + 16 * hcol, vb);
-                float* acc = part == 0 ? num : den;
-#pragma unroll
-                for (int i = 0; i < 16; i += 4) {
-                    const float4 c4 = *reinterpret_cast<const float4*>(crow + i);
-                    const float4 s4 = *reinterpret_cast<const float4*>(srow + i);
-                    acc[i + 0] = fmaf(Wk, fmaf(c4.x, va[i + 0], s4.x * vb[i + 0]), acc[i + 0]);
-                    acc[i + 1] = fmaf(Wk, fmaf(c4.y, va[i + 1], s4.y * vb[i + 1]), acc[i + 1]);
-                    acc[i + 2] = fmaf(Wk, fmaf(c4.z, va[i + 2], s4.z * vb[i + 2]), acc[i + 2]);
-                    acc[i + 3] = fmaf(Wk, fmaf(c4.w, va[i + 3], s4.w * vb[i + 3]), acc[i + 3]);
+                for (int i = 0; i < 8; ++i) {
+                    float s, c;
+                    __sincosf(__fmul_rn(wc, pn[t][i]), &s, &c);
+                    const bool v = (valid[t] >> i) & 1u;
+                    c = v ? c : 0.f;
+                    s = v ? s : 0.f;
+                    cv[i] = c;
+                    sv[i] = s;
+                    av[i] = pn[t][i] * c;
+                    bv[i] = pn[t][i] * s;
                 }
+                unsigned char* b1 = smem + G.offB1 + rb * 128;
+                store_row8<kBF16>(b1 + ((0 * RWp + j) / 8) * G.sboB1 + ((0 * RWp + j) % 8) * 16, av);
+                store_row8<kBF16>(b1 + ((1 * RWp + j) / 8) * G.sboB1 + ((1 * RWp + j) % 8) * 16, bv);
+                store_row8<kBF16>(b1 + ((2 * RWp + j) / 8) * G.sboB1 + ((2 * RWp + j) % 8) * 16, cv);
+                store_row8<kBF16>(b1 + ((3 * RWp + j) / 8) * G.sboB1 + ((3 * RWp + j) % 8) * 16, sv);
+            }
+            fence_async_smem();
+            mbar_arrive(bar(kBarB1Full));
+        }
+    } else if (warp == kEpiWarps + kModWarps) {
+        // ================= MMA issue (one thread) =================
+        if (lane == 0) {
+            const uint32_t idesc1 = idesc_f16(TH, 2 * RWp, kBF16);
+            const uint32_t idesc2 = idesc_f16(TH, TW, kBF16);
+            int issued1 = 0, issued2 = 0;
+            for (int k = 0; k < K; ++k) {
+                if (!mbar_wait(bar(kBarB1Full), k & 1, spin_limit, stop)) break;
+                fence_after();
+                for (int half = 0; half < 2; ++half) {
+                    const uint32_t nb = sbase + G.offB1 + (uint32_t)(half * 2 * RWp / 8) * G.sboB1;
+                    for (int ks = 0; ks < G.RHp / 16; ++ks) {
+                        const uint64_t da = sdesc(sbase + G.offA1 + ks * 256, 128, 128);
+                        const uint64_t db = sdesc(nb + ks * 256, 128, G.sboB1);
+                        mma_f16(tD1 + half * 2 * RWp, da, db, idesc1, ks > 0);
+                    }
+                }
+                mma_commit(bar(kBarC1));
+                ++issued1;
+                if (!mbar_wait(bar(kBarA2Full), k & 1, spin_limit, stop)) break;
+                if (k > 0 && !mbar_wait(bar(kBarD2Free), (k - 1) & 1, spin_limit, stop)) break;
+                fence_after();
+                for (int pl = 0; pl < 4; ++pl) {
+#pragma unroll
+                    for (int ks = 0; ks < NCH; ++ks) {
+                        const uint64_t da = sdesc(sbase + G.offA2 + pl * G.planeA2 + ks * 256, 128,
+                                                  G.sboA2);
+                        const uint64_t db = sdesc(sbase + G.offB2 + ks * 256, 128, 128);
+                        mma_f16(tD2 + pl * TW, da, db, idesc2, ks > 0);
+                    }
+                }
+                mma_commit(bar(kBarC2));
+                ++issued2;
+            }
+            if (*stop) {
+                // let every committed MMA finish before TMEM is freed (bounded)
+                volatile int never = 0;
+                if (issued1) mbar_wait(bar(kBarC1), (issued1 - 1) & 1, spin_limit, &never);
+                if (issued2) mbar_wait(bar(kBarC2), (issued2 - 1) & 1, spin_limit, &never);
             }
         }
-        fence_before();
-        __syncthreads();
-    }
-
-    if (failed) {
-        if (tid == 0) atomicOr(status, kDevTimeout);
-        // give the tensor core one more bounded chance to drain before freeing TMEM
-        mbar_wait(mbar, phase, spin_limit);
+        __syncwarp();
     } else {
-        // ---- normalise and write (den guard with the FP32 clipped Gaussian mass)
-        const int gy = by + yl;
-        if (gy < a.H) {
+        // ================= epilogue warps (TMEM lanes 32 q ..) =================
+        const int q = warp;
+        const int m = 32 * q + lane;              // MMA row = TMEM lane
+        const int y = TH - 1 - m;                 // output row of this thread
+        const int gy = by + y;
+        const uint32_t tl = (uint32_t)(32 * q) << 16;
+        // centred, scaled f of my outputs, in shared memory (row m, padded)
+        float* pno = reinterpret_cast<float*>(smem + G.offPn) + m * kPnStride;
+#pragma unroll
+        for (int x = 0; x < TW; ++x) {
+            const int gx = bx + x;
+            pno[x] = (gy < a.H && gx < a.W)
+                         ? __fmul_rn(__fsub_rn(__ldg(a.f + (size_t)gy * a.f_pitch + gx), c0), inv_c0)
+                         : 0.f;
+        }
+        float num[TW], den[TW];
+#pragma unroll
+        for (int x = 0; x < TW; ++x) num[x] = den[x] = 0.f;
+        bool ok = true;
+        for (int k = 0; k < K && ok; ++k) {
+            float wc = 0.f, Wk = hd.w0;
+            if (k < hd.F) {
+                const Pair p = pr[k];
+                wc = __fmul_rn(p.om_hi, c0);
+                Wk = p.W;
+            }
+            // D1 ready: convert my row of each plane to 16 bits (A2, K-major)
+            if (!mbar_wait(bar(kBarC1), k & 1, spin_limit, stop)) { ok = false; break; }
+            fence_after();
+            unsigned char* a2row = smem + G.offA2 + (m / 8) * G.sboA2 + (m % 8) * 16;
+#pragma unroll
+            for (int pl = 0; pl < 4; ++pl) {
+#pragma unroll
+                for (int c = 0; c < NCH; c += 2) {
+                    float v[32];
+                    if (c + 1 < NCH) tmem_ld32(tD1 + tl + pl * RWp + 16 * c, v);
+                    else tmem_ld16(tD1 + tl + pl * RWp + 16 * c, v);
+                    unsigned char* dst = a2row + pl * G.planeA2 + (2 * c) * 128;
+                    store_row8<kBF16>(dst, v);
+                    store_row8<kBF16>(dst + 128, v + 8);
+                    if (c + 1 < NCH) {
+                        store_row8<kBF16>(dst + 256, v + 16);
+                        store_row8<kBF16>(dst + 384, v + 24);
+                    }
+                }
+            }
+            fence_async_smem();
+            fence_before();
+            mbar_arrive(bar(kBarA2Full));
+            // D2 ready: demodulate (eqs. (f1), (f2)); TMEM column n is x = 31 - n
+            if (!mbar_wait(bar(kBarC2), k & 1, spin_limit, stop)) { ok = false; break; }
+            fence_after();
+#pragma unroll
+            for (int cb = 0; cb < TW / 8; ++cb) {
+                float fa[8], fb[8], fc[8], fd[8];
+                tmem_ld4x8(tD2 + tl + 0 * TW + 8 * cb, tD2 + tl + 1 * TW + 8 * cb,
+                           tD2 + tl + 2 * TW + 8 * cb, tD2 + tl + 3 * TW + 8 * cb, fa, fb, fc, fd);
+#pragma unroll
+                for (int e = 0; e < 8; ++e) {
+                    const int x = TW - 1 - (8 * cb + e);
+                    float s, c;
+                    __sincosf(__fmul_rn(wc, pno[x]), &s, &c);
+                    num[x] = fmaf(Wk, fmaf(c, fa[e], s * fb[e]), num[x]);
+                    den[x] = fmaf(Wk, fmaf(c, fc[e], s * fd[e]), den[x]);
+                }
+            }
+            fence_before();
+            mbar_arrive(bar(kBarD2Free));
+        }
+        if (ok && gy < a.H) {
+            // normalise with the guard (FP32 clipped Gaussian mass) and store
             float rmass = 0.f;
             for (int t = -R; t <= R; ++t)
                 if (gy + t >= 0 && gy + t < a.H) rmass += a.taps[t + R];
 #pragma unroll
-            for (int i = 0; i < 16; ++i) {
-                const int gx = bx + 16 * hcol + i;
+            for (int x = 0; x < TW; ++x) {
+                const int gx = bx + x;
                 if (gx >= a.W) continue;
                 float cmass = 0.f;
                 for (int t = -R; t <= R; ++t)
                     if (gx + t >= 0 && gx + t < a.W) cmass += a.taps[t + R];
                 float v;
-                if (den[i] > kGuard * rmass * cmass) {
-                    v = __fdiv_rn(num[i], den[i]) * c0 + c0;
+                if (den[x] > kGuard * rmass * cmass) {
+                    v = __fdiv_rn(num[x], den[x]) * c0 + c0;
                 } else {
                     v = a.f[(size_t)gy * a.f_pitch + gx];
                     atomicAdd(a.n_guarded, 1ull);
@@ -491,31 +529,45 @@ __global__ void __launch_bounds__(NT, 1) k_fwd_tc(FwdArgs a, long long spin_limi
             }
         }
     }
+
     fence_before();
     __syncthreads();
-    if (warp == 0) {
+    if (tid == 0 && *stop) atomicOr(status, kDevTimeout);
+    if (warp == kEpiWarps + kModWarps) {
         fence_after();
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;"
                      ::"r"(tbase), "r"(kTmemCols) : "memory");
     }
 }
 
-template <bool kBF16>
+template <bool kBF16, int NCH>
 cudaError_t launch_t(const FwdArgs& a, long long spin, unsigned* status, cudaStream_t s)
 {
     const TcGeo G(a.R);
-    cudaError_t e = cudaFuncSetAttribute(k_fwd_tc<kBF16>,
+    cudaError_t e = cudaFuncSetAttribute(k_fwd_tc<kBF16, NCH>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G.bytes);
     if (e != cudaSuccess) return e;
     dim3 grid((a.W + TW - 1) / TW, (a.H + TH - 1) / TH);
-    k_fwd_tc<kBF16><<<grid, NT, G.bytes, s>>>(a, spin, status);
+    k_fwd_tc<kBF16, NCH><<<grid, NT, G.bytes, s>>>(a, spin, status);
     return cudaGetLastError();
+}
+
+template <bool kBF16>
+cudaError_t launch_nch(const FwdArgs& a, long long spin, unsigned* status, cudaStream_t s)
+{
+    switch (TcGeo(a.R).RWp / 16) {
+    case 2: return launch_t<kBF16, 2>(a, spin, status, s);
+    case 3: return launch_t<kBF16, 3>(a, spin, status, s);
+    case 4: return launch_t<kBF16, 4>(a, spin, status, s);
+    case 5: return launch_t<kBF16, 5>(a, spin, status, s);
+    }
+    return cudaErrorInvalidValue;
 }
 
 }  // namespace
 
-// Largest R the tensor-core kernel takes (shared memory, TMEM columns and
-// the per-thread item count all fit).
+// Largest R the tensor-core kernel takes: shared memory, TMEM columns, the
+// per-thread item count and the N of one vertical MMA all fit.
 int fwd_tc_max_radius()
 {
     int best = -1;
@@ -523,7 +575,7 @@ int fwd_tc_max_radius()
         const TcGeo G(R);
         const int items = G.RWp * (G.RHp / 8);
         if (G.bytes <= 227 * 1024 && 4 * G.RWp + 4 * TW <= kTmemCols &&
-            items <= kMaxItems * NT && 2 * G.RWp <= 256)
+            items <= kMaxItems * kModThreads && 2 * G.RWp <= 256 && G.RWp / 16 <= 5)
             best = R;
         else
             break;
@@ -541,7 +593,7 @@ cudaError_t launch_fwd_tc(const FwdArgs& a, bool bf16, long long spin, unsigned*
                           cudaStream_t s)
 {
     if (a.R > fwd_tc_max_radius()) return cudaErrorInvalidValue;
-    return bf16 ? launch_t<true>(a, spin, status, s) : launch_t<false>(a, spin, status, s);
+    return bf16 ? launch_nch<true>(a, spin, status, s) : launch_nch<false>(a, spin, status, s);
 }
 
 }  // namespace bf
