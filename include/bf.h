@@ -21,9 +21,10 @@
  *     without synchronising, unless the comment says otherwise.  Results are
  *     valid once the stream has reached the work.
  *   - A plan owns its device workspace (parameter tables, T words, status
- *     word), allocated in bf_plan and freed in bf_destroy.  bf_execute and
- *     bf_backward allocate nothing.  One plan must not be used on two
- *     streams at the same time.
+ *     word), allocated in bf_plan and freed in bf_destroy.  bf_execute
+ *     allocates nothing; bf_execute_host and bf_backward allocate their own
+ *     scratch on their first call on a plan.  One plan must not be used on
+ *     two streams at the same time.
  *   - Errors are returned as bf_status codes, never as exceptions.  Argument
  *     errors are detected on the host before anything is enqueued.
  *     Data-dependent failures (order above the plan's cap, a bounded wait
@@ -125,7 +126,12 @@ bf_status bf_execute_host(bf_plan_t plan, const float *f_host, float *out_host,
  * (and the denominator guard) held at the values the last bf_execute of this
  * plan produced on device (not in the paper; derived from eqs. (f1)-(f2)).
  * f_dev must be the image of that bf_execute.  All three images share
- * `pitch`.  Returns BF_ERR_NO_FORWARD if the plan has not been executed. */
+ * `pitch`.  The gradient is that of the FP32-plane filter whatever the
+ * plan's plane_dtype: a forward pass with FP32 planes recomputes out and the
+ * denominator, then the adjoint kernel runs.  The first call on a plan
+ * allocates that pass's scratch (two H x W float images), later calls reuse
+ * it.  Returns BF_ERR_NO_FORWARD if the plan has not been executed, and
+ * BF_ERR_NOT_SUPPORTED if R is too large for the adjoint's tiles. */
 bf_status bf_backward(bf_plan_t plan, const float *f_dev, const float *grad_out_dev,
                       float *grad_in_dev, size_t pitch, void *stream);
 

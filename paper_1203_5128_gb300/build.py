@@ -19,8 +19,8 @@ LIB = os.path.join(OUT, "libbf.so")
 INCLUDE = os.path.join(ROOT, "include")
 
 SOURCES = ["bf_api.cu", "bf_range.cu", "bf_params.cu", "bf_fwd32.cu", "bf_fwd_tc.cu",
-           "bf_noalloc.cu"]
-HEADERS = ["bf_internal.cuh"]
+           "bf_bwd32.cu", "bf_noalloc.cu"]
+HEADERS = ["bf_internal.cuh", "bf_fir32.cuh"]
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE, "-I", CSRC]

@@ -519,8 +519,51 @@ bf_status bf_execute_batch(int n, const bf_plan_t* plans, const float* const* f,
 }  // extern "C"
 
 namespace bf {
-cudaError_t launch_backward(bf_plan_s*, const float*, const float*, float*, size_t, cudaStream_t)
+
+// Backward: a forward pass with FP32 planes on the parameters the last
+// bf_execute left on device (writing out and den to plan scratch), then the
+// adjoint kernel.  The scratch (two H x W images and a counter) is allocated
+// by the first backward of the plan.
+cudaError_t launch_backward(bf_plan_s* p, const float* f, const float* gout, float* gin,
+                            size_t pitch, cudaStream_t s)
 {
-    return cudaErrorNotSupported;
+    int th = 0, tw = 0;
+    bwd32_tile(p->R, &th, &tw);
+    if (!th) return cudaErrorNotSupported;
+    const size_t hw = (size_t)p->H * p->W;
+    if (!p->d_bwd) {
+        cudaError_t e = cudaMalloc(&p->d_bwd, sizeof(float) * (2 * hw + 4));
+        if (e != cudaSuccess) return cudaErrorMemoryAllocation;
+    }
+    float* s_out = p->d_bwd;
+    float* s_den = p->d_bwd + hw;
+    unsigned long long* s_cnt =
+        reinterpret_cast<unsigned long long*>(p->d_bwd + 2 * hw + ((2 * hw) & 1));
+    FwdArgs fa = forward_args(p, f, pitch, s_out, p->W);
+    fa.den_out = s_den;
+    fa.den_pitch = p->W;
+    fa.n_guarded = s_cnt;
+    cudaError_t e = launch_fwd32(fa, s);
+    if (e != cudaSuccess) return e;
+    BwdArgs ba;
+    ba.f = f;
+    ba.u = gout;
+    ba.grad = gin;
+    ba.pitch = pitch;
+    ba.out = s_out;
+    ba.den = s_den;
+    ba.spitch = p->W;
+    ba.H = p->H;
+    ba.W = p->W;
+    ba.R = p->R;
+    ba.taps = p->d_taps;
+    ba.hdr = p->d_hdr;
+    ba.pairs = p->d_pairs;
+    ba.cap_pairs = p->cap_pairs;
+    ba.set_tile = fa.set_tile;
+    ba.sets_x = p->sets_x;
+    ba.c0 = fa.c0;
+    return launch_bwd32(ba, s);
 }
+
 }  // namespace bf

@@ -20,62 +20,13 @@
 //   * a pixel whose den <= 1e-6 (g * 1_Omega) keeps f (the paper is silent).
 #include <math.h>
 
-#include "bf_internal.cuh"
+#include "bf_fir32.cuh"
 
 namespace bf {
 namespace {
 
-constexpr double kTwoPi = 6.283185307179586476925286766559;
-constexpr float k2PiHi = (float)kTwoPi;
-constexpr float k2PiLo = (float)(kTwoPi - (double)(float)kTwoPi);
-constexpr float kInv2Pi = (float)(1.0 / kTwoPi);
-
-// cos and sin of (om_hi + om_lo) * v.
-__device__ __forceinline__ void phase_cs(float v, float om_hi, float om_lo, float& c, float& s)
-{
-    const float p = __fmul_rn(om_hi, v);
-    float e = fmaf(om_hi, v, -p);           // exact rounding error of p
-    e = fmaf(om_lo, v, e);                  // + tail of omega
-    const float q = rintf(__fmul_rn(p, kInv2Pi));
-    float r = fmaf(-q, k2PiHi, p);
-    r = fmaf(-q, k2PiLo, r);
-    r = __fadd_rn(r, e);
-    __sincosf(r, &s, &c);
-}
-
-// Element j (0..7, a compile-time constant after unrolling) of the pair (a, b).
-__device__ __forceinline__ float pick8(const float4& a, const float4& b, int j)
-{
-    switch (j) {
-    case 0: return a.x;
-    case 1: return a.y;
-    case 2: return a.z;
-    case 3: return a.w;
-    case 4: return b.x;
-    case 5: return b.y;
-    case 6: return b.z;
-    default: return b.w;
-    }
-}
-
-// Shared-memory geometry for a tile of TH x TW outputs and radius R.
-struct Geo {
-    int R, nch, RH, RW, RWp, RHp, ngz;
-    __host__ __device__ Geo(int R_, int TH, int TW)
-    {
-        R = R_;
-        nch = (2 * R + 15) / 8;                 // 8-wide steps covering 2R+8 inputs
-        RH = TH + 2 * R;
-        RW = TW + 2 * R;
-        RWp = TW - 8 + 8 * nch + 4;             // +4 words: rows 16 B aligned, banks staggered
-        RHp = TH - 8 + 8 * nch;
-        ngz = 8 * nch + 16;
-    }
-    __host__ __device__ size_t floats(int TW) const
-    {
-        return 3 * (size_t)RH * RWp + 4 * (size_t)RHp * TW + (size_t)ngz;
-    }
-};
+using fir32::Geo;
+using fir32::phase_cs;
 
 template <int TH, int TW>
 __global__ void __launch_bounds__(TH * TW / 8, 1) k_fwd32(FwdArgs a)
@@ -170,76 +121,13 @@ __global__ void __launch_bounds__(TH * TW / 8, 1) k_fwd32(FwdArgs a)
         __syncthreads();
 
         // (2) rows: item (r, cb) -> 8 outputs of row r, columns cb*8 .. cb*8+7
-        for (int it = tid; it < G.RH * (TW / 8); it += NT) {
-            const int r = it / (TW / 8), cb = it - r * (TW / 8);
-            const float* fr = fsm + r * G.RWp + cb * 8;
-            const float* cr = csm + r * G.RWp + cb * 8;
-            const float* sr = ssm + r * G.RWp + cb * 8;
-            float acc[4][8];
-#pragma unroll
-            for (int q = 0; q < 4; ++q)
-#pragma unroll
-                for (int i = 0; i < 8; ++i) acc[q][i] = 0.f;
-            for (int ch = 0; ch < G.nch; ++ch) {
-                const int a0 = ch * 8;
-                float g[15];
-#pragma unroll
-                for (int d = 0; d < 15; ++d) g[d] = gz[a0 + d + 1];   // tap a0 + d - 7
-                const float4 c0 = *(const float4*)(cr + a0), c1 = *(const float4*)(cr + a0 + 4);
-                const float4 s0 = *(const float4*)(sr + a0), s1 = *(const float4*)(sr + a0 + 4);
-                const float4 f0 = *(const float4*)(fr + a0), f1 = *(const float4*)(fr + a0 + 4);
-#pragma unroll
-                for (int j = 0; j < 8; ++j) {
-                    const float cj = pick8(c0, c1, j), sj = pick8(s0, s1, j);
-                    const float fj = pick8(f0, f1, j);
-                    const float A = fj * cj, B = fj * sj;
-#pragma unroll
-                    for (int i = 0; i < 8; ++i) {
-                        const float w = g[j - i + 7];
-                        acc[0][i] = fmaf(w, A, acc[0][i]);
-                        acc[1][i] = fmaf(w, B, acc[1][i]);
-                        acc[2][i] = fmaf(w, cj, acc[2][i]);
-                        acc[3][i] = fmaf(w, sj, acc[3][i]);
-                    }
-                }
-            }
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                float* hp = hsm + q * hplane + (size_t)r * TW + cb * 8;
-                *(float4*)hp = make_float4(acc[q][0], acc[q][1], acc[q][2], acc[q][3]);
-                *(float4*)(hp + 4) = make_float4(acc[q][4], acc[q][5], acc[q][6], acc[q][7]);
-            }
-        }
+        fir32::row_pass<TW, true>(G, fsm, nullptr, csm, ssm, gz, hsm, tid, NT);
         __syncthreads();
 
         // (3) columns of my item, then demodulate into num / den
         {
             float acc[4][8];
-#pragma unroll
-            for (int q = 0; q < 4; ++q)
-#pragma unroll
-                for (int i = 0; i < 8; ++i) acc[q][i] = 0.f;
-            const float* h0 = hsm + (size_t)(rb * 8) * TW + o;
-            for (int ch = 0; ch < G.nch; ++ch) {
-                const int a0 = ch * 8;
-                float g[15];
-#pragma unroll
-                for (int d = 0; d < 15; ++d) g[d] = gz[a0 + d + 1];
-#pragma unroll
-                for (int j = 0; j < 8; ++j) {
-                    const float* hj = h0 + (size_t)(a0 + j) * TW;
-                    const float hA = hj[0], hB = hj[hplane], hC = hj[2 * hplane],
-                                hD = hj[3 * hplane];
-#pragma unroll
-                    for (int i = 0; i < 8; ++i) {
-                        const float w = g[j - i + 7];
-                        acc[0][i] = fmaf(w, hA, acc[0][i]);
-                        acc[1][i] = fmaf(w, hB, acc[1][i]);
-                        acc[2][i] = fmaf(w, hC, acc[2][i]);
-                        acc[3][i] = fmaf(w, hD, acc[3][i]);
-                    }
-                }
-            }
+            fir32::col_pass<TW>(G, hsm, gz, o, rb, acc);
 #pragma unroll
             for (int i = 0; i < 8; ++i) {
                 const int ry = rb * 8 + i + R;
@@ -277,7 +165,7 @@ template <int TH, int TW>
 cudaError_t launch_tile(const FwdArgs& a, cudaStream_t s)
 {
     const Geo G(a.R, TH, TW);
-    const size_t smem = G.floats(TW) * sizeof(float);
+    const size_t smem = G.floats(TW, 3) * sizeof(float);
     cudaError_t e = cudaFuncSetAttribute(k_fwd32<TH, TW>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
@@ -292,7 +180,7 @@ constexpr size_t kSmemLimit = 227 * 1024;
 
 size_t fwd32_smem(int R, int th, int tw)
 {
-    return Geo(R, th, tw).floats(tw) * sizeof(float);
+    return Geo(R, th, tw).floats(tw, 3) * sizeof(float);
 }
 
 void fwd32_tile(int R, int* th, int* tw)

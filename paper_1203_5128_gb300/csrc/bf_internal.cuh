@@ -86,6 +86,27 @@ void fwd32_tile(int R, int* th, int* tw);
 size_t fwd32_smem(int R, int th, int tw);
 cudaError_t launch_fwd32(const FwdArgs& a, cudaStream_t s);
 
+// K5 (adjoint, FP32 planes, FIR): needs the forward's out and den images.
+struct BwdArgs {
+    const float* f;
+    const float* u;         // dL/d out
+    float* grad;            // dL/d f
+    size_t pitch;           // of f, u, grad
+    const float* out;       // forward output (scratch)
+    const float* den;       // forward denominator (scratch)
+    size_t spitch;          // of out, den
+    int H, W, R;
+    const float* taps;
+    const SetHdr* hdr;
+    const Pair* pairs;
+    int cap_pairs;
+    int set_tile;
+    int sets_x;
+    float c0;
+};
+void bwd32_tile(int R, int* th, int* tw);
+cudaError_t launch_bwd32(const BwdArgs& a, cudaStream_t s);
+
 // K3-tc (FP16 / BF16 planes, tcgen05): 128 x 32 output tiles, R <= max radius.
 int fwd_tc_max_radius();
 void fwd_tc_tile(int* th, int* tw);

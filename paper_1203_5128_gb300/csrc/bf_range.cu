@@ -1,20 +1,24 @@
 // K1: windowed max / min filter and the dynamic range T.
 //
 // Sec. 2 of the paper: T = max_x max_{y in window} |f(x-y) - f(x)| (eq.
-// (bound)); Prop. 2.1 removes the modulus, Prop. MAX-FILTER and the Appendix
-// give the van Herk / Gil-Werman running maxima: split a line into
-// partitions of length Wn = 2R+1, take prefix maxima l and suffix maxima r
-// inside each partition, and the windowed max at i is max(r[i], l[i+2R]) in
-// coordinates padded by R.  Algorithm 1 applies it to rows, then to the
-// columns of the row result.
+// (bound)); Prop. 2.1 removes the modulus (for the image-wide T the max
+// filter alone suffices: max_x (M(x) - f(x)) = max_x (f(x) - m(x))), Prop.
+// MAX-FILTER and the Appendix give the van Herk / Gil-Werman running maxima:
+// split a line into partitions of length Wn = 2R+1, take suffix maxima r and
+// prefix maxima l inside each partition, and the windowed max of the window
+// starting at i is max(r[i], l[i+2R]).  Algorithm 1 applies it to rows, then
+// to the columns of the row result.
 //
-// GB300 form: one CTA per 32x32 block of outputs.  The block plus its R halo
-// is staged in shared memory once (coalesced), every (line, partition) pair
-// is one thread running the two running extrema over its partition, and only
-// the entries the combine step reads are kept (r on [0,32), l on
-// [2R, 2R+32)), so the line buffers are 32 wide whatever R is.  Max and min
-// run in the same pass (padding -inf for the max, +inf for the min).  The
-// block's largest local range max(M - f, f - m) goes to its T word with an
+// GB300 form: one CTA per 64 x 64 block of outputs.  The block plus its R
+// halo is staged in shared memory once (coalesced).  Each (line, partition)
+// is one thread running the partition's suffix (then prefix) maxima
+// sequentially -- 3 max operations per point as in the Appendix -- with the
+// 32 lanes of a warp on 32 consecutive lines, so every step is one
+// conflict-free shared load per lane and the loops carry no branches.  Only
+// the entries the combine reads are kept: suffix maxima on [0, 64) are
+// written first, then the prefix maxima on [2R, 2R+64) are folded in.
+// Per-tile T needs max and min; the image-wide T needs only the max (Prop.
+// 2.1).  The block's largest local range goes to its T word with an
 // atomicMax on the float's bit pattern (valid: the values are >= 0).
 #include <math.h>
 
@@ -23,7 +27,8 @@
 namespace bf {
 namespace {
 
-constexpr int kT = 32;       // output block side
+constexpr int kT = 64;          // output block side
+constexpr int kTp = kT + 1;     // padded row stride of the 64-wide buffers
 constexpr int kThreads = 256;
 
 __device__ __forceinline__ float min_operand(float v)
@@ -32,106 +37,123 @@ __device__ __forceinline__ float min_operand(float v)
     return v == -INFINITY ? INFINITY : v;
 }
 
-template <bool kImages>
+// Suffix maxima of smax[q0..q1) (and minima of smin[q0..q1)), stride `st`
+// between entries, written to dmax / dmin [q * dst_st] for q < lim.
+template <bool kMin>
+__device__ __forceinline__ void suffix_part(const float* smax, const float* smin, int st, int q0,
+                                            int q1, int lim, float* dmax, float* dmin, int dst_st)
+{
+    float hi = -INFINITY, lo = INFINITY;
+    int q = q1 - 1;
+    const int qs = min(q1, lim);          // entries below qs are stored
+#pragma unroll 4
+    for (; q >= qs; --q) {
+        hi = fmaxf(hi, smax[q * st]);
+        if (kMin) lo = fminf(lo, min_operand(smin[q * st]));
+    }
+#pragma unroll 4
+    for (; q >= q0; --q) {
+        hi = fmaxf(hi, smax[q * st]);
+        dmax[q * dst_st] = hi;
+        if (kMin) {
+            lo = fminf(lo, min_operand(smin[q * st]));
+            dmin[q * dst_st] = lo;
+        }
+    }
+}
+
+// Prefix maxima of smax[q0..qe) (and minima of smin), folded into
+// dmax / dmin [(q - off) * dst_st] for q >= off: the combine
+// max(r[i], l[i + 2R]) of the Appendix.
+template <bool kMin>
+__device__ __forceinline__ void prefix_part(const float* smax, const float* smin, int st, int q0,
+                                            int qe, int off, float* dmax, float* dmin, int dst_st)
+{
+    float hi = -INFINITY, lo = INFINITY;
+    int q = q0;
+    const int qs = max(q0, off);
+#pragma unroll 4
+    for (; q < qs; ++q) {
+        hi = fmaxf(hi, smax[q * st]);
+        if (kMin) lo = fminf(lo, min_operand(smin[q * st]));
+    }
+#pragma unroll 4
+    for (; q < qe; ++q) {
+        hi = fmaxf(hi, smax[q * st]);
+        float* dm = dmax + (q - off) * dst_st;
+        *dm = fmaxf(*dm, hi);
+        if (kMin) {
+            lo = fminf(lo, min_operand(smin[q * st]));
+            float* dn = dmin + (q - off) * dst_st;
+            *dn = fminf(*dn, lo);
+        }
+    }
+}
+
+template <bool kMin, bool kImages>
 __global__ void __launch_bounds__(kThreads)
 k_local_range(const float* __restrict__ f, size_t pitch, int H, int W, int R, int set_tile,
               int sets_x, unsigned* __restrict__ Tbits, float* __restrict__ Mx,
               float* __restrict__ mn)
 {
     extern __shared__ float sm[];
-    const int L = kT + 2 * R;       // region side
-    const int Ls = L + 1;           // padded row stride of the region
+    const int L = kT + 2 * R;       // region side (even)
+    const int Ls = L + 1;           // odd row stride: lanes on consecutive rows hit distinct banks
     const int Wn = 2 * R + 1;       // window = partition length
     const int P = (L + Wn - 1) / Wn;
     float* reg = sm;                // L x Ls, -inf outside the image
-    float* rmax = reg + L * Ls;     // L x 32: row pass, suffix part then result
-    float* rmin = rmax + L * kT;
-    float* lmax = rmin + L * kT;    // L x 32: row pass, prefix part
-    float* lmin = lmax + L * kT;
-    float* cRmax = lmin + L * kT;   // 32 x 32 each: column pass
-    float* cRmin = cRmax + kT * kT;
-    float* cLmax = cRmin + kT * kT;
-    float* cLmin = cLmax + kT * kT;
+    float* rmax = reg + L * Ls;     // L x kTp: row pass result
+    float* rmin = rmax + L * kTp;
+    float* cmax = rmin + (kMin ? L * kTp : 0);   // kT x kTp: column pass result
+    float* cmin = cmax + kT * kTp;
     __shared__ float red[kThreads / 32];
 
     const int by = blockIdx.y * kT, bx = blockIdx.x * kT;
     const int gy0 = by - R, gx0 = bx - R;
-    for (int i = threadIdx.x; i < L * L; i += kThreads) {
-        const int r = i / L, c = i - r * L;
-        const int gy = gy0 + r, gx = gx0 + c;
-        reg[r * Ls + c] = (gy >= 0 && gy < H && gx >= 0 && gx < W)
-                              ? __ldg(f + (size_t)gy * pitch + gx) : -INFINITY;
+    for (int r = threadIdx.x / 32; r < L; r += kThreads / 32) {
+        const int gy = gy0 + r;
+        const bool rin = gy >= 0 && gy < H;
+        for (int c = threadIdx.x % 32; c < L; c += 32) {
+            const int gx = gx0 + c;
+            reg[r * Ls + c] = (rin && gx >= 0 && gx < W) ? __ldg(f + (size_t)gy * pitch + gx)
+                                                         : -INFINITY;
+        }
     }
     __syncthreads();
 
-    // ---- rows: running extrema per (row, partition)
-    for (int it = threadIdx.x; it < L * P; it += kThreads) {
-        const int r = it / P, p = it - r * P;
+    // ---- rows: suffix parts (partitions meeting [0, kT)), then prefix parts
+    //      (partitions meeting [2R, 2R + kT)); lane = row
+    const int pr_hi = (kT - 1) / Wn;              // last partition meeting [0, kT)
+    const int pl_lo = (2 * R) / Wn, pl_hi = (2 * R + kT - 1) / Wn;
+    for (int it = threadIdx.x; it < L * (pr_hi + 1); it += kThreads) {
+        const int p = it / L, r = it - p * L;
         const int q0 = p * Wn, q1 = min(q0 + Wn, L);
-        const float* row = reg + r * Ls;
-        if (q1 > 2 * R && q0 < 2 * R + kT) {       // prefix maxima, kept on [2R, 2R+32)
-            float hi = -INFINITY, lo = INFINITY;
-            const int qe = min(q1, 2 * R + kT);
-            for (int q = q0; q < qe; ++q) {
-                const float v = row[q];
-                hi = fmaxf(hi, v);
-                lo = fminf(lo, min_operand(v));
-                if (q >= 2 * R) {
-                    lmax[r * kT + (q - 2 * R)] = hi;
-                    lmin[r * kT + (q - 2 * R)] = lo;
-                }
-            }
-        }
-        if (q0 < kT) {                             // suffix maxima, kept on [0, 32)
-            float hi = -INFINITY, lo = INFINITY;
-            for (int q = q1 - 1; q >= q0; --q) {
-                const float v = row[q];
-                hi = fmaxf(hi, v);
-                lo = fminf(lo, min_operand(v));
-                if (q < kT) {
-                    rmax[r * kT + q] = hi;
-                    rmin[r * kT + q] = lo;
-                }
-            }
-        }
+        suffix_part<kMin>(reg + r * Ls, reg + r * Ls, 1, q0, q1, kT, rmax + r * kTp,
+                          rmin + r * kTp, 1);
     }
     __syncthreads();
-    for (int i = threadIdx.x; i < L * kT; i += kThreads) {   // combine
-        rmax[i] = fmaxf(rmax[i], lmax[i]);
-        const float a = rmin[i], b = lmin[i];
-        rmin[i] = fminf(a, b);
+    for (int it = threadIdx.x; it < L * (pl_hi - pl_lo + 1); it += kThreads) {
+        const int p = pl_lo + it / L, r = it % L;
+        const int q0 = p * Wn, qe = min(min(q0 + Wn, L), 2 * R + kT);
+        prefix_part<kMin>(reg + r * Ls, reg + r * Ls, 1, q0, qe, 2 * R, rmax + r * kTp,
+                          rmin + r * kTp, 1);
     }
     __syncthreads();
 
-    // ---- columns of the row result: running extrema per (column, partition)
-    for (int it = threadIdx.x; it < kT * P; it += kThreads) {
-        const int c = it % kT, p = it / kT;
+    // ---- columns of the row result; lane = column
+    for (int it = threadIdx.x; it < kT * (pr_hi + 1); it += kThreads) {
+        const int p = it / kT, c = it % kT;
         const int q0 = p * Wn, q1 = min(q0 + Wn, L);
-        if (q1 > 2 * R && q0 < 2 * R + kT) {
-            float hi = -INFINITY, lo = INFINITY;
-            const int qe = min(q1, 2 * R + kT);
-            for (int q = q0; q < qe; ++q) {
-                hi = fmaxf(hi, rmax[q * kT + c]);
-                lo = fminf(lo, rmin[q * kT + c]);
-                if (q >= 2 * R) {
-                    cLmax[(q - 2 * R) * kT + c] = hi;
-                    cLmin[(q - 2 * R) * kT + c] = lo;
-                }
-            }
-        }
-        if (q0 < kT) {
-            float hi = -INFINITY, lo = INFINITY;
-            for (int q = q1 - 1; q >= q0; --q) {
-                hi = fmaxf(hi, rmax[q * kT + c]);
-                lo = fminf(lo, rmin[q * kT + c]);
-                if (q < kT) {
-                    cRmax[q * kT + c] = hi;
-                    cRmin[q * kT + c] = lo;
-                }
-            }
-        }
+        suffix_part<kMin>(rmax + c, rmin + c, kTp, q0, q1, kT, cmax + c, cmin + c, kTp);
     }
     __syncthreads();
+    for (int it = threadIdx.x; it < kT * (pl_hi - pl_lo + 1); it += kThreads) {
+        const int p = pl_lo + it / kT, c = it % kT;
+        const int q0 = p * Wn, qe = min(min(q0 + Wn, L), 2 * R + kT);
+        prefix_part<kMin>(rmax + c, rmin + c, kTp, q0, qe, 2 * R, cmax + c, cmin + c, kTp);
+    }
+    __syncthreads();
+    (void)P;
 
     // ---- local range and its block maximum
     float best = 0.0f;
@@ -139,14 +161,14 @@ k_local_range(const float* __restrict__ f, size_t pitch, int H, int W, int R, in
         const int oy = i / kT, ox = i - oy * kT;
         const int gy = by + oy, gx = bx + ox;
         if (gy >= H || gx >= W) continue;
-        const float M = fmaxf(cRmax[i], cLmax[i]);
-        const float m = fminf(cRmin[i], cLmin[i]);
+        const float M = cmax[oy * kTp + ox];
         const float v = reg[(oy + R) * Ls + (ox + R)];
         if (kImages) {
             Mx[(size_t)gy * pitch + gx] = M;
-            mn[(size_t)gy * pitch + gx] = m;
+            mn[(size_t)gy * pitch + gx] = cmin[oy * kTp + ox];
         } else {
-            best = fmaxf(best, fmaxf(M - v, v - m));
+            best = fmaxf(best, M - v);
+            if (kMin) best = fmaxf(best, v - cmin[oy * kTp + ox]);
         }
     }
     if (!kImages) {
@@ -162,23 +184,24 @@ k_local_range(const float* __restrict__ f, size_t pitch, int H, int W, int R, in
     }
 }
 
-size_t range_smem(int R)
+size_t range_smem(int R, bool with_min)
 {
     const size_t L = kT + 2 * (size_t)R;
-    return sizeof(float) * (L * (L + 1) + 4 * L * kT + 4 * kT * kT);
+    const size_t lines = with_min ? 2 : 1;
+    return sizeof(float) * (L * (L + 1) + lines * (L * kTp + kT * kTp));
 }
 
-template <bool kImages>
+template <bool kMin, bool kImages>
 cudaError_t launch(const float* f, size_t pitch, int H, int W, int R, int set_tile, int sets_x,
                    unsigned* Tbits, float* Mx, float* mn, cudaStream_t s)
 {
-    const size_t smem = range_smem(R);
-    cudaError_t e = cudaFuncSetAttribute(k_local_range<kImages>,
+    const size_t smem = range_smem(R, kMin);
+    cudaError_t e = cudaFuncSetAttribute(k_local_range<kMin, kImages>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     dim3 grid((W + kT - 1) / kT, (H + kT - 1) / kT);
-    k_local_range<kImages><<<grid, kThreads, smem, s>>>(f, pitch, H, W, R, set_tile, sets_x,
-                                                        Tbits, Mx, mn);
+    k_local_range<kMin, kImages><<<grid, kThreads, smem, s>>>(f, pitch, H, W, R, set_tile, sets_x,
+                                                              Tbits, Mx, mn);
     return cudaGetLastError();
 }
 
@@ -187,20 +210,23 @@ cudaError_t launch(const float* f, size_t pitch, int H, int W, int R, int set_ti
 int range_max_radius()
 {
     int R = 0;
-    while (range_smem(R + 1) <= 226 * 1024) ++R;   // static reduction buffer rides on top
+    while (range_smem(R + 1, true) <= 226 * 1024) ++R;   // static reduction buffer rides on top
     return R;
 }
 
 cudaError_t launch_local_range(const float* f, size_t pitch, int H, int W, int R, int set_tile,
                                int sets_x, unsigned* Tbits, cudaStream_t s)
 {
-    return launch<false>(f, pitch, H, W, R, set_tile, sets_x, Tbits, nullptr, nullptr, s);
+    // per-tile T needs the min filter too; the image-wide T does not (Prop. 2.1)
+    if (set_tile)
+        return launch<true, false>(f, pitch, H, W, R, set_tile, sets_x, Tbits, nullptr, nullptr, s);
+    return launch<false, false>(f, pitch, H, W, R, 0, 1, Tbits, nullptr, nullptr, s);
 }
 
 cudaError_t launch_maxmin(const float* f, size_t pitch, int H, int W, int R, float* Mx, float* mn,
                           cudaStream_t s)
 {
-    return launch<true>(f, pitch, H, W, R, 0, 1, nullptr, Mx, mn, s);
+    return launch<true, true>(f, pitch, H, W, R, 0, 1, nullptr, Mx, mn, s);
 }
 
 }  // namespace bf
