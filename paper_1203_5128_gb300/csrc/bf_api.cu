@@ -21,31 +21,7 @@ cudaError_t launch_backward(bf_plan_s* p, const float* f, const float* gout, flo
                             size_t pitch, cudaStream_t s);
 }
 
-struct bf_plan_s {
-    int H, W, R;
-    double sigma_s, sigma_r, eps;
-    bf_options opt;
-    int device;
-    int n_sets, sets_x, sets_y, set_tile;
-    int n_cap, cap_pairs;
-    float c0;
-    int th, tw;
-    unsigned* d_T;
-    SetHdr* d_hdr;
-    Pair* d_pairs;
-    float* d_taps;
-    double* d_logfact;
-    unsigned* d_status;
-    unsigned long long* d_nguard;
-    float* d_hin;
-    float* d_hout;
-    float* d_bwd;            // backward scratch (out, den), allocated on first use
-    int executed;
-    cudaStream_t last;
-    int timing;              // record events around the kernels
-    int n_timed;
-    cudaEvent_t* ev;         // 4 per recorded execute
-};
+
 
 namespace {
 
@@ -113,6 +89,8 @@ ParamsArgs params_args(bf_plan_s* p)
 }  // namespace
 
 namespace bf {
+
+ParamsArgs plan_params_args(bf_plan_s* p) { return params_args(p); }
 
 FwdArgs forward_args(bf_plan_s* p, const float* f, size_t fp, float* out, size_t op)
 {
@@ -465,6 +443,7 @@ void bf_destroy(bf_plan_t p)
     if (!p) return;
     cudaSetDevice(p->device);
     cudaStreamSynchronize(p->last);
+    batch_forget(p);
     free_plan(p);
 }
 
@@ -509,12 +488,7 @@ bf_status bf_maxmin(const float* f, int H, int W, size_t pitch, int R, float* Mx
     return cuda_status(launch_maxmin(f, pitch, H, W, R, Mx, mn, (cudaStream_t)stream));
 }
 
-bf_status bf_execute_batch(int n, const bf_plan_t* plans, const float* const* f,
-                           float* const* out, void* stream)
-{
-    (void)n; (void)plans; (void)f; (void)out; (void)stream;
-    return BF_ERR_NOT_SUPPORTED;
-}
+
 
 }  // extern "C"
 

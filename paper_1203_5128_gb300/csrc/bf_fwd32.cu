@@ -28,12 +28,12 @@ namespace {
 using fir32::Geo;
 using fir32::phase_cs;
 
+// One output tile with origin (by, bx): the whole block takes part.
 template <int TH, int TW>
-__global__ void __launch_bounds__(TH * TW / 8, 1) k_fwd32(FwdArgs a)
+__device__ __forceinline__ void fwd32_body(const FwdArgs& a, int by, int bx, float* sm)
 {
     constexpr int NT = TH * TW / 8;
     constexpr int NW = NT / 32;
-    extern __shared__ __align__(16) float sm[];
     const Geo G(a.R, TH, TW);
     const int R = a.R;
     float* fsm = sm;                              // RH x RWp  centred f, 0 outside
@@ -44,7 +44,6 @@ __global__ void __launch_bounds__(TH * TW / 8, 1) k_fwd32(FwdArgs a)
     const size_t hplane = (size_t)G.RHp * TW;
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int by = blockIdx.y * TH, bx = blockIdx.x * TW;
     const int gy0 = by - R, gx0 = bx - R;
 
     const int set = a.set_tile ? (by / a.set_tile) * a.sets_x + (bx / a.set_tile) : 0;
@@ -162,6 +161,34 @@ __global__ void __launch_bounds__(TH * TW / 8, 1) k_fwd32(FwdArgs a)
 }
 
 template <int TH, int TW>
+__global__ void __launch_bounds__(TH * TW / 8, 1) k_fwd32(FwdArgs a)
+{
+    extern __shared__ __align__(16) float sm[];
+    fwd32_body<TH, TW>(a, blockIdx.y * TH, blockIdx.x * TW, sm);
+}
+
+// Persistent form: CTAs take (image, tile) items from a queue (atomic head)
+// until it is empty; items are ordered by the caller (costly first).
+template <int TH, int TW>
+__global__ void __launch_bounds__(TH * TW / 8, 1)
+k_fwd32_persistent(const FwdArgs* __restrict__ imgs, const int4* __restrict__ items, int n_items,
+                   unsigned* __restrict__ head)
+{
+    extern __shared__ __align__(16) float sm[];
+    __shared__ int s_item;
+    for (;;) {
+        __syncthreads();                       // the previous item is done with shared memory
+        if (threadIdx.x == 0) s_item = (int)atomicAdd(head, 1u);
+        __syncthreads();
+        const int i = s_item;
+        if (i >= n_items) break;
+        const int4 it = items[i];              // (image, tile row origin, tile column origin, -)
+        const FwdArgs a = imgs[it.x];
+        fwd32_body<TH, TW>(a, it.y, it.z, sm);
+    }
+}
+
+template <int TH, int TW>
 cudaError_t launch_tile(const FwdArgs& a, cudaStream_t s)
 {
     const Geo G(a.R, TH, TW);
@@ -193,6 +220,48 @@ void fwd32_tile(int R, int* th, int* tw)
             return;
         }
     *th = *tw = 0;
+}
+
+int fwd32_persistent_ctas_per_sm(int th, int tw, int max_R)
+{
+    const size_t smem = fwd32_smem(max_R, th, tw);
+    int n = 0;
+    cudaError_t e = cudaErrorInvalidValue;
+#define BF_OCC(TH_, TW_)                                                                  \
+    if (th == TH_ && tw == TW_) {                                                         \
+        e = cudaFuncSetAttribute(k_fwd32_persistent<TH_, TW_>,                            \
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); \
+        if (e == cudaSuccess)                                                             \
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(                            \
+                &n, k_fwd32_persistent<TH_, TW_>, TH_ * TW_ / 8, smem);                   \
+    }
+    BF_OCC(64, 32)
+    BF_OCC(32, 32)
+    BF_OCC(16, 16)
+#undef BF_OCC
+    return e == cudaSuccess ? n : 0;
+}
+
+cudaError_t launch_fwd32_persistent(int th, int tw, int max_R, const FwdArgs* imgs,
+                                   const int4* items, int n_items, unsigned* head, int n_ctas,
+                                   cudaStream_t s)
+{
+    const size_t smem = fwd32_smem(max_R, th, tw);
+    cudaError_t e = cudaErrorInvalidValue;
+#define BF_PERSIST(TH_, TW_)                                                               \
+    if (th == TH_ && tw == TW_) {                                                          \
+        e = cudaFuncSetAttribute(k_fwd32_persistent<TH_, TW_>,                             \
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);  \
+        if (e != cudaSuccess) return e;                                                    \
+        k_fwd32_persistent<TH_, TW_><<<n_ctas, TH_ * TW_ / 8, smem, s>>>(imgs, items,      \
+                                                                           n_items, head); \
+        return cudaGetLastError();                                                         \
+    }
+    BF_PERSIST(64, 32)
+    BF_PERSIST(32, 32)
+    BF_PERSIST(16, 16)
+#undef BF_PERSIST
+    return e;
 }
 
 cudaError_t launch_fwd32(const FwdArgs& a, cudaStream_t s)

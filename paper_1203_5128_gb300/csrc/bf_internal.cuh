@@ -7,6 +7,38 @@
 #include "bf.h"
 
 namespace bf {
+struct SetHdr;
+struct Pair;
+}
+
+// A plan: the sizes, options and device workspace of one image shape.
+struct bf_plan_s {
+    int H, W, R;
+    double sigma_s, sigma_r, eps;
+    bf_options opt;
+    int device;
+    int n_sets, sets_x, sets_y, set_tile;
+    int n_cap, cap_pairs;
+    float c0;
+    int th, tw;
+    unsigned* d_T;
+    bf::SetHdr* d_hdr;
+    bf::Pair* d_pairs;
+    float* d_taps;
+    double* d_logfact;
+    unsigned* d_status;
+    unsigned long long* d_nguard;
+    float* d_hin;
+    float* d_hout;
+    float* d_bwd;            // backward scratch (out, den), allocated on first use
+    int executed;
+    cudaStream_t last;
+    int timing;              // record events around the kernels
+    int n_timed;
+    cudaEvent_t* ev;         // 4 per recorded execute
+};
+
+namespace bf {
 
 // One parameter set (Algorithm 2, steps 3-5) as the forward kernels read it.
 // F folded frequency pairs (n and N-n, weight 2 w_n) follow in the pair
@@ -106,6 +138,27 @@ struct BwdArgs {
 };
 void bwd32_tile(int R, int* th, int* tw);
 cudaError_t launch_bwd32(const BwdArgs& a, cudaStream_t s);
+
+// ---- batched path (bf_execute_batch) ----------------------------------------
+struct RangeImg {
+    const float* f;
+    size_t pitch;
+    int H, W, R, set_tile, sets_x;
+    unsigned* Tbits;
+};
+int range_tile();
+size_t range_smem_bytes(int R);
+cudaError_t launch_local_range_batch(const RangeImg* imgs, const int4* items, int n_items,
+                                     int max_R, int n_ctas, cudaStream_t s);
+cudaError_t launch_params_batch(const ParamsArgs* imgs, const int* block_img, const int* block_set,
+                                int n_blocks, cudaStream_t s);
+cudaError_t launch_fwd32_persistent(int th, int tw, int max_R, const FwdArgs* imgs,
+                                   const int4* items, int n_items, unsigned* head, int n_ctas,
+                                   cudaStream_t s);
+int fwd32_persistent_ctas_per_sm(int th, int tw, int max_R);
+FwdArgs forward_args(bf_plan_s* p, const float* f, size_t fp, float* out, size_t op);
+ParamsArgs plan_params_args(bf_plan_s* p);
+void batch_forget(bf_plan_s* p);
 
 // K3-tc (FP16 / BF16 planes, tcgen05): 128 x 32 output tiles, R <= max radius.
 int fwd_tc_max_radius();

@@ -32,11 +32,11 @@ __device__ double log_weight(const ParamsArgs& a, int N, int n)
     return c - a.logfact[n] - a.logfact[N - n];
 }
 
-__global__ void __launch_bounds__(kThreads) k_params(ParamsArgs a)
+// One block computes set `set` of `a` (all threads of the block take part).
+__device__ void params_body(const ParamsArgs& a, int set)
 {
     __shared__ double tail[kMaxTail / 2 + 2];
     __shared__ int sN, sM;
-    const int set = blockIdx.x;
     const double T = (double)a.T[set];
 
     if (threadIdx.x == 0) {
@@ -122,12 +122,30 @@ __global__ void __launch_bounds__(kThreads) k_params(ParamsArgs a)
     }
 }
 
+__global__ void __launch_bounds__(kThreads) k_params(ParamsArgs a) { params_body(a, blockIdx.x); }
+
+// Batched: block b computes set block_set[b] of image block_img[b].
+__global__ void __launch_bounds__(kThreads)
+k_params_batch(const ParamsArgs* __restrict__ imgs, const int* __restrict__ block_img,
+               const int* __restrict__ block_set)
+{
+    const ParamsArgs a = imgs[block_img[blockIdx.x]];
+    params_body(a, block_set[blockIdx.x]);
+}
+
 }  // namespace
 
 cudaError_t launch_params(const ParamsArgs& a, cudaStream_t s)
 {
     if (a.n_cap > kMaxTail) return cudaErrorInvalidValue;
     k_params<<<a.n_sets, kThreads, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_params_batch(const ParamsArgs* imgs, const int* block_img,
+                                const int* block_set, int n_blocks, cudaStream_t s)
+{
+    k_params_batch<<<n_blocks, kThreads, 0, s>>>(imgs, block_img, block_set);
     return cudaGetLastError();
 }
 

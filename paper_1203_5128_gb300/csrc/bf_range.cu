@@ -90,13 +90,14 @@ __device__ __forceinline__ void prefix_part(const float* smax, const float* smin
     }
 }
 
+// One 64 x 64 output block with origin (by, bx): the whole block takes part.
 template <bool kMin, bool kImages>
-__global__ void __launch_bounds__(kThreads)
-k_local_range(const float* __restrict__ f, size_t pitch, int H, int W, int R, int set_tile,
-              int sets_x, unsigned* __restrict__ Tbits, float* __restrict__ Mx,
-              float* __restrict__ mn)
+__device__ __forceinline__ void range_body(const float* __restrict__ f, size_t pitch, int H, int W,
+                                           int R, int set_tile, int sets_x,
+                                           unsigned* __restrict__ Tbits, float* __restrict__ Mx,
+                                           float* __restrict__ mn, int by, int bx, float* sm,
+                                           float* red)
 {
-    extern __shared__ float sm[];
     const int L = kT + 2 * R;       // region side (even)
     const int Ls = L + 1;           // odd row stride: lanes on consecutive rows hit distinct banks
     const int Wn = 2 * R + 1;       // window = partition length
@@ -106,9 +107,7 @@ k_local_range(const float* __restrict__ f, size_t pitch, int H, int W, int R, in
     float* rmin = rmax + L * kTp;
     float* cmax = rmin + (kMin ? L * kTp : 0);   // kT x kTp: column pass result
     float* cmin = cmax + kT * kTp;
-    __shared__ float red[kThreads / 32];
 
-    const int by = blockIdx.y * kT, bx = blockIdx.x * kT;
     const int gy0 = by - R, gx0 = bx - R;
     for (int r = threadIdx.x / 32; r < L; r += kThreads / 32) {
         const int gy = gy0 + r;
@@ -184,6 +183,35 @@ k_local_range(const float* __restrict__ f, size_t pitch, int H, int W, int R, in
     }
 }
 
+template <bool kMin, bool kImages>
+__global__ void __launch_bounds__(kThreads)
+k_local_range(const float* __restrict__ f, size_t pitch, int H, int W, int R, int set_tile,
+              int sets_x, unsigned* __restrict__ Tbits, float* __restrict__ Mx,
+              float* __restrict__ mn)
+{
+    extern __shared__ float sm[];
+    __shared__ float red[kThreads / 32];
+    range_body<kMin, kImages>(f, pitch, H, W, R, set_tile, sets_x, Tbits, Mx, mn,
+                              blockIdx.y * kT, blockIdx.x * kT, sm, red);
+}
+
+// Batched: CTAs stride over (image, block row, block column) items.  Max and
+// min are both computed, which leaves the image-wide T unchanged (Prop. 2.1:
+// max (M - f) and max (f - m) over the image are equal).
+__global__ void __launch_bounds__(kThreads)
+k_local_range_batch(const RangeImg* __restrict__ imgs, const int4* __restrict__ items, int n_items)
+{
+    extern __shared__ float sm[];
+    __shared__ float red[kThreads / 32];
+    for (int i = blockIdx.x; i < n_items; i += gridDim.x) {
+        const int4 it = items[i];
+        const RangeImg g = imgs[it.x];
+        __syncthreads();
+        range_body<true, false>(g.f, g.pitch, g.H, g.W, g.R, g.set_tile, g.sets_x, g.Tbits,
+                                nullptr, nullptr, it.y, it.z, sm, red);
+    }
+}
+
 size_t range_smem(int R, bool with_min)
 {
     const size_t L = kT + 2 * (size_t)R;
@@ -206,6 +234,21 @@ cudaError_t launch(const float* f, size_t pitch, int H, int W, int R, int set_ti
 }
 
 }  // namespace
+
+int range_tile() { return kT; }
+
+size_t range_smem_bytes(int R) { return range_smem(R, true); }
+
+cudaError_t launch_local_range_batch(const RangeImg* imgs, const int4* items, int n_items,
+                                     int max_R, int n_ctas, cudaStream_t s)
+{
+    const size_t smem = range_smem(max_R, true);
+    cudaError_t e = cudaFuncSetAttribute(k_local_range_batch,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k_local_range_batch<<<n_ctas, kThreads, smem, s>>>(imgs, items, n_items);
+    return cudaGetLastError();
+}
 
 int range_max_radius()
 {
