@@ -403,10 +403,13 @@ __global__ void __launch_bounds__(NT, 1) k_fwd_tc(FwdArgs a, long long spin_limi
             for (int k = 0; k < K; ++k) {
                 if (!mbar_wait(bar(kBarB1Full), k & 1, spin_limit, stop)) break;
                 fence_after();
-                for (int half = 0; half < 2; ++half) {
-                    const uint32_t nb = sbase + G.offB1 + (uint32_t)(half * 2 * RWp / 8) * G.sboB1;
-                    for (int ks = 0; ks < G.RHp / 16; ++ks) {
-                        const uint64_t da = sdesc(sbase + G.offA1 + ks * 256, 128, 128);
+                // consecutive MMAs go to different accumulators, so that no
+                // MMA waits on the previous one's accumulation
+                for (int ks = 0; ks < G.RHp / 16; ++ks) {
+                    const uint64_t da = sdesc(sbase + G.offA1 + ks * 256, 128, 128);
+                    for (int half = 0; half < 2; ++half) {
+                        const uint32_t nb =
+                            sbase + G.offB1 + (uint32_t)(half * 2 * RWp / 8) * G.sboB1;
                         const uint64_t db = sdesc(nb + ks * 256, 128, G.sboB1);
                         mma_f16(tD1 + half * 2 * RWp, da, db, idesc1, ks > 0);
                     }
@@ -416,12 +419,12 @@ __global__ void __launch_bounds__(NT, 1) k_fwd_tc(FwdArgs a, long long spin_limi
                 if (!mbar_wait(bar(kBarA2Full), k & 1, spin_limit, stop)) break;
                 if (k > 0 && !mbar_wait(bar(kBarD2Free), (k - 1) & 1, spin_limit, stop)) break;
                 fence_after();
-                for (int pl = 0; pl < 4; ++pl) {
 #pragma unroll
-                    for (int ks = 0; ks < NCH; ++ks) {
+                for (int ks = 0; ks < NCH; ++ks) {
+                    const uint64_t db = sdesc(sbase + G.offB2 + ks * 256, 128, 128);
+                    for (int pl = 0; pl < 4; ++pl) {
                         const uint64_t da = sdesc(sbase + G.offA2 + pl * G.planeA2 + ks * 256, 128,
                                                   G.sboA2);
-                        const uint64_t db = sdesc(sbase + G.offB2 + ks * 256, 128, 128);
                         mma_f16(tD2 + pl * TW, da, db, idesc2, ks > 0);
                     }
                 }
