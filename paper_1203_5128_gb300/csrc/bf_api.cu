@@ -221,6 +221,10 @@ bf_status bf_plan(int H, int W, double sigma_s, double sigma_r, double eps, cons
     int th = 0, tw = 0;
     if (o.plane_dtype == BF_PLANES_FP32) {
         fwd32_tile(R, &th, &tw);
+        if (fwd32t_ok(R, o.t_mode == BF_T_TILE ? o.t_tile : 0)) {
+            th = 128;
+            tw = 32;
+        }
     } else if (R <= fwd_tc_max_radius()) {
         fwd_tc_tile(&th, &tw);
     }

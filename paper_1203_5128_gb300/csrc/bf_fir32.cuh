@@ -164,3 +164,135 @@ __device__ __forceinline__ void col_pass(const Geo& G, const float* hsm, const f
 
 }  // namespace fir32
 }  // namespace bf
+
+namespace bf {
+namespace fir32 {
+
+// ---- tall-tile variant: two row-filtered planes at a time, exact taps ------
+//
+// The radius is padded to Rp = 4 ceil(R/4) (taps beyond R are zero and add
+// exact zeros), so that 2 Rp is a multiple of 8: the first 8-input step of
+// an 8-output block then only meets taps j - i >= 0 (lower triangle) and the
+// last one only taps j - i <= 0 (upper triangle), and the FIR executes
+// exactly 2 Rp + 1 multiply-adds per output.  The row-filtered planes are
+// stored with the 16-byte quads of each row permuted by (row & 7), which
+// spreads the vector stores of a warp over all 32 banks.
+
+struct Geo2 {
+    int R, Rp, nch, RH, RW, RWp, RHp, ngz;
+    __host__ __device__ Geo2(int R_, int TH, int TW)
+    {
+        R = R_;
+        Rp = (R + 3) / 4 * 4;
+        nch = Rp / 4 + 1;                       // (2 Rp + 8) / 8 input steps
+        RH = TH + 2 * Rp;
+        RW = TW + 2 * Rp;
+        RWp = TW - 8 + 8 * nch + 4;             // = RW + 4: rows 16 B aligned, banks staggered
+        RHp = TH - 8 + 8 * nch;                 // = RH
+        ngz = 8 * nch + 16;
+    }
+    __host__ __device__ size_t floats(int TW) const
+    {
+        return 3 * (size_t)RH * RWp + 2 * (size_t)RHp * TW + (size_t)ngz;
+    }
+};
+
+// word offset of element (row r, column x) of a swizzled row-filtered plane
+template <int TW>
+__device__ __forceinline__ int hsw(int r, int x)
+{
+    return r * TW + ((((x >> 2) ^ (r & 7)) & (TW / 4 - 1)) << 2) + (x & 3);
+}
+
+// One 8x8 step of an 8-output FIR block: acc[i] += g[j - i + 7] * v[j] for
+// the (j, i) allowed by kPart (0 full, 1 lower triangle j >= i, 2 upper j <= i).
+template <int kPart>
+__device__ __forceinline__ void fir_step(float (&acc)[8], const float (&g)[15], const float (&v)[8])
+{
+#pragma unroll
+    for (int j = 0; j < 8; ++j)
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            if (kPart == 1 && j < i) continue;
+            if (kPart == 2 && j > i) continue;
+            acc[i] = fmaf(g[j - i + 7], v[j], acc[i]);
+        }
+}
+
+// Row pass for one plane per item: plane value m * cs (m = m1s, or 1 when
+// m1s is null), items (halo row r, 8-column block cb, plane p of the pair
+// (p = 0 uses cos, p = 1 sin)); output to hsm plane p (swizzled rows).
+template <int TW>
+__device__ __forceinline__ void row_pass2(const Geo2& G, const float* m1s, const float* csm,
+                                          const float* ssm, const float* gz, float* hsm, int tid,
+                                          int nthreads)
+{
+    const size_t hplane = (size_t)G.RHp * TW;
+    for (int it = tid; it < G.RH * (TW / 8) * 2; it += nthreads) {
+        const int p = it & 1, rc = it >> 1;
+        const int r = rc / (TW / 8), cb = rc - r * (TW / 8);
+        const float* src = (p ? ssm : csm) + r * G.RWp + cb * 8;
+        const float* mr = m1s ? m1s + r * G.RWp + cb * 8 : nullptr;
+        float acc[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) acc[i] = 0.f;
+        for (int ch = 0; ch < G.nch; ++ch) {
+            const int a0 = ch * 8;
+            float g[15];
+#pragma unroll
+            for (int d = 0; d < 15; ++d) g[d] = gz[a0 + d + 1];   // tap a0 + d - 7
+            const float4 v0 = *(const float4*)(src + a0), v1 = *(const float4*)(src + a0 + 4);
+            float v[8] = {v0.x, v0.y, v0.z, v0.w, v1.x, v1.y, v1.z, v1.w};
+            if (mr) {
+                const float4 f0 = *(const float4*)(mr + a0), f1 = *(const float4*)(mr + a0 + 4);
+                v[0] *= f0.x; v[1] *= f0.y; v[2] *= f0.z; v[3] *= f0.w;
+                v[4] *= f1.x; v[5] *= f1.y; v[6] *= f1.z; v[7] *= f1.w;
+            }
+            if (ch == 0) fir_step<1>(acc, g, v);
+            else if (ch == G.nch - 1) fir_step<2>(acc, g, v);
+            else fir_step<0>(acc, g, v);
+        }
+        float* hp = hsm + p * hplane;
+        *(float4*)(hp + hsw<TW>(r, cb * 8)) = make_float4(acc[0], acc[1], acc[2], acc[3]);
+        *(float4*)(hp + hsw<TW>(r, cb * 8 + 4)) = make_float4(acc[4], acc[5], acc[6], acc[7]);
+    }
+}
+
+// Column pass of two planes for one item: column o, output rows rb*8 .. rb*8+7.
+template <int TW>
+__device__ __forceinline__ void col_pass2(const Geo2& G, const float* hsm, const float* gz, int o,
+                                          int rb, float (&acc)[2][8])
+{
+    const size_t hplane = (size_t)G.RHp * TW;
+#pragma unroll
+    for (int q = 0; q < 2; ++q)
+#pragma unroll
+        for (int i = 0; i < 8; ++i) acc[q][i] = 0.f;
+    for (int ch = 0; ch < G.nch; ++ch) {
+        const int a0 = ch * 8;
+        float g[15];
+#pragma unroll
+        for (int d = 0; d < 15; ++d) g[d] = gz[a0 + d + 1];
+        float v0[8], v1[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            const int r = rb * 8 + a0 + j;
+            const int w = hsw<TW>(r, o);
+            v0[j] = hsm[w];
+            v1[j] = hsm[hplane + w];
+        }
+        if (ch == 0) {
+            fir_step<1>(acc[0], g, v0);
+            fir_step<1>(acc[1], g, v1);
+        } else if (ch == G.nch - 1) {
+            fir_step<2>(acc[0], g, v0);
+            fir_step<2>(acc[1], g, v1);
+        } else {
+            fir_step<0>(acc[0], g, v0);
+            fir_step<0>(acc[1], g, v1);
+        }
+    }
+}
+
+}  // namespace fir32
+}  // namespace bf

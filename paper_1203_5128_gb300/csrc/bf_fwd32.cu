@@ -160,6 +160,132 @@ __device__ __forceinline__ void fwd32_body(const FwdArgs& a, int by, int bx, flo
     }
 }
 
+// Tall-tile form (128 x 32 outputs, 512 threads): row-filtered planes two at
+// a time in a swizzled buffer, exact taps (see Geo2).  Same arithmetic per
+// output as fwd32_body: the nonzero taps are summed in the same order and
+// the skipped ones would have added exact zeros.
+template <int TH, int TW>
+__device__ __forceinline__ void fwd32t_body(const FwdArgs& a, int by, int bx, float* sm)
+{
+    constexpr int NT = TH * TW / 8;
+    constexpr int NW = NT / 32;
+    const fir32::Geo2 G(a.R, TH, TW);
+    const int R = a.R, Rp = G.Rp;
+    float* fsm = sm;                              // RH x RWp  centred f, 0 outside
+    float* csm = fsm + (size_t)G.RH * G.RWp;      // RH x RWp  cos
+    float* ssm = csm + (size_t)G.RH * G.RWp;      // RH x RWp  sin
+    float* hsm = ssm + (size_t)G.RH * G.RWp;      // 2 x RHp x TW  row-filtered planes
+    float* gz = hsm + 2 * (size_t)G.RHp * TW;     // gz[t + 8] = g(t - Rp), 0 outside |t - Rp| <= R
+
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int gy0 = by - Rp, gx0 = bx - Rp;
+    const int set = a.set_tile ? (by / a.set_tile) * a.sets_x + (bx / a.set_tile) : 0;
+    const SetHdr hd = a.hdr[set];
+    const int o = tid % TW, rb = tid / TW;
+    const int gx = bx + o;
+
+    if (hd.F < 0) {          // order above the cap: pass the image through
+        for (int i = 0; i < 8; ++i) {
+            const int gy = by + rb * 8 + i;
+            if (gy < a.H && gx < a.W)
+                a.out[(size_t)gy * a.out_pitch + gx] = a.f[(size_t)gy * a.f_pitch + gx];
+        }
+        return;
+    }
+    for (int r = warp; r < G.RH; r += NW) {
+        const int gy = gy0 + r;
+        const bool rin = gy >= 0 && gy < a.H;
+        for (int col = lane; col < G.RWp; col += 32) {
+            const int x = gx0 + col;
+            float v = 0.f;
+            if (rin && col < G.RW && x >= 0 && x < a.W)
+                v = __ldg(a.f + (size_t)gy * a.f_pitch + x) - a.c0;
+            fsm[r * G.RWp + col] = v;
+        }
+    }
+    for (int i = tid; i < G.ngz; i += NT) {
+        const int k = i - 8 - Rp;
+        gz[i] = (k >= -R && k <= R) ? a.taps[k + R] : 0.f;
+    }
+    float cmass = 0.f;
+    for (int t = -R; t <= R; ++t)
+        if (gx + t >= 0 && gx + t < a.W) cmass += a.taps[t + R];
+    float num[8], den[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) num[i] = den[i] = 0.f;
+    __syncthreads();
+
+    const Pair* pr = a.pairs + (size_t)set * a.cap_pairs;
+    const int K = hd.F + hd.z;
+    for (int k = 0; k < K; ++k) {
+        float om_hi = 0.f, om_lo = 0.f, Wk = hd.w0;
+        if (k < hd.F) {
+            const Pair p = pr[k];
+            om_hi = p.om_hi;
+            om_lo = p.om_lo;
+            Wk = p.W;
+        }
+        for (int r = warp; r < G.RH; r += NW) {
+            const int gy = gy0 + r;
+            const bool rin = gy >= 0 && gy < a.H;
+            for (int col = lane; col < G.RWp; col += 32) {
+                const int x = gx0 + col;
+                float c = 0.f, s = 0.f;
+                if (rin && col < G.RW && x >= 0 && x < a.W)
+                    phase_cs(fsm[r * G.RWp + col], om_hi, om_lo, c, s);
+                csm[r * G.RWp + col] = c;
+                ssm[r * G.RWp + col] = s;
+            }
+        }
+        __syncthreads();
+        // numerator planes f' c, f' s
+        fir32::row_pass2<TW>(G, fsm, csm, ssm, gz, hsm, tid, NT);
+        __syncthreads();
+        float nab[2][8];
+        fir32::col_pass2<TW>(G, hsm, gz, o, rb, nab);
+        __syncthreads();
+        // denominator planes c, s
+        fir32::row_pass2<TW>(G, nullptr, csm, ssm, gz, hsm, tid, NT);
+        __syncthreads();
+        float dcd[2][8];
+        fir32::col_pass2<TW>(G, hsm, gz, o, rb, dcd);
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            const int ry = rb * 8 + i + Rp;
+            const float c = csm[ry * G.RWp + o + Rp], s = ssm[ry * G.RWp + o + Rp];
+            num[i] = fmaf(Wk, fmaf(c, nab[0][i], s * nab[1][i]), num[i]);
+            den[i] = fmaf(Wk, fmaf(c, dcd[0][i], s * dcd[1][i]), den[i]);
+        }
+        __syncthreads();
+    }
+    if (gx < a.W) {
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            const int gy = by + rb * 8 + i;
+            if (gy >= a.H) continue;
+            float rmass = 0.f;
+            for (int t = -R; t <= R; ++t)
+                if (gy + t >= 0 && gy + t < a.H) rmass += a.taps[t + R];
+            float v;
+            if (den[i] > kGuard * rmass * cmass) {
+                v = __fdiv_rn(num[i], den[i]) + a.c0;
+            } else {
+                v = a.f[(size_t)gy * a.f_pitch + gx];
+                atomicAdd(a.n_guarded, 1ull);
+            }
+            a.out[(size_t)gy * a.out_pitch + gx] = v;
+            if (a.den_out) a.den_out[(size_t)gy * a.den_pitch + gx] = den[i];
+        }
+    }
+}
+
+template <int TH, int TW>
+__global__ void __launch_bounds__(TH * TW / 8, 1) k_fwd32t(FwdArgs a)
+{
+    extern __shared__ __align__(16) float sm[];
+    fwd32t_body<TH, TW>(a, blockIdx.y * TH, blockIdx.x * TW, sm);
+}
+
 template <int TH, int TW>
 __global__ void __launch_bounds__(TH * TW / 8, 1) k_fwd32(FwdArgs a)
 {
@@ -264,8 +390,26 @@ cudaError_t launch_fwd32_persistent(int th, int tw, int max_R, const FwdArgs* im
     return e;
 }
 
+size_t fwd32t_smem(int R) { return fir32::Geo2(R, 128, 32).floats(32) * sizeof(float); }
+
+// The 128 x 32 tall tile serves a launch when its shared memory fits and its
+// tiles nest inside the T-tiles.
+bool fwd32t_ok(int R, int set_tile)
+{
+    return fwd32t_smem(R) <= kSmemLimit && (set_tile == 0 || set_tile % 128 == 0);
+}
+
 cudaError_t launch_fwd32(const FwdArgs& a, cudaStream_t s)
 {
+    if (fwd32t_ok(a.R, a.set_tile)) {
+        const size_t smem = fwd32t_smem(a.R);
+        cudaError_t e = cudaFuncSetAttribute(k_fwd32t<128, 32>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        dim3 grid((a.W + 31) / 32, (a.H + 127) / 128);
+        k_fwd32t<128, 32><<<grid, 512, smem, s>>>(a);
+        return cudaGetLastError();
+    }
     int th, tw;
     fwd32_tile(a.R, &th, &tw);
     if (th == 64 && tw == 32) return launch_tile<64, 32>(a, s);
