@@ -53,6 +53,7 @@ void free_plan(bf_plan_s* p)
     cudaFree(p->d_hdr);
     cudaFree(p->d_pairs);
     cudaFree(p->d_taps);
+    free(p->h_taps);
     cudaFree(p->d_logfact);
     cudaFree(p->d_status);
     cudaFree(p->d_nguard);
@@ -112,6 +113,7 @@ FwdArgs forward_args(bf_plan_s* p, const float* f, size_t fp, float* out, size_t
     a.n_guarded = p->d_nguard;
     a.den_out = nullptr;
     a.den_pitch = 0;
+    a.h_taps = p->h_taps;
     return a;
 }
 
@@ -293,7 +295,7 @@ bf_status bf_plan(int H, int W, double sigma_s, double sigma_r, double eps, cons
           cudaSuccess;
     ok &= cudaMemset(p->d_status, 0, sizeof(unsigned)) == cudaSuccess;
     ok &= cudaMemset(p->d_nguard, 0, sizeof(unsigned long long)) == cudaSuccess;
-    free(taps);
+    p->h_taps = taps;      // kept: the tall FP32 kernel takes the taps as a parameter
     free(lf);
     if (o.t_mode == BF_T_FIXED) {
         float T = o.t_fixed;

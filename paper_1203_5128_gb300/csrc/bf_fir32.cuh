@@ -191,9 +191,14 @@ struct Geo2 {
         RHp = TH - 8 + 8 * nch;                 // = RH
         ngz = 8 * nch + 16;
     }
+    // the sin array and the second row-filtered plane start 4 words (16 B)
+    // past a bank-aligned offset, so that the two arrays a quarter-warp
+    // reads or writes together fall on different banks
+    __host__ __device__ size_t region() const { return (size_t)RH * RWp; }
+    __host__ __device__ size_t hplane(int TW) const { return (size_t)RHp * TW + 4; }
     __host__ __device__ size_t floats(int TW) const
     {
-        return 3 * (size_t)RH * RWp + 2 * (size_t)RHp * TW + (size_t)ngz;
+        return 3 * region() + 4 + 2 * hplane(TW) + (size_t)ngz;
     }
 };
 
@@ -227,7 +232,7 @@ __device__ __forceinline__ void row_pass2(const Geo2& G, const float* m1s, const
                                           const float* ssm, const float* gz, float* hsm, int tid,
                                           int nthreads)
 {
-    const size_t hplane = (size_t)G.RHp * TW;
+    const size_t hplane = G.hplane(TW);
     for (int it = tid; it < G.RH * (TW / 8) * 2; it += nthreads) {
         const int p = it & 1, rc = it >> 1;
         const int r = rc / (TW / 8), cb = rc - r * (TW / 8);
@@ -263,7 +268,7 @@ template <int TW>
 __device__ __forceinline__ void col_pass2(const Geo2& G, const float* hsm, const float* gz, int o,
                                           int rb, float (&acc)[2][8])
 {
-    const size_t hplane = (size_t)G.RHp * TW;
+    const size_t hplane = G.hplane(TW);
 #pragma unroll
     for (int q = 0; q < 2; ++q)
 #pragma unroll
@@ -285,6 +290,102 @@ __device__ __forceinline__ void col_pass2(const Geo2& G, const float* hsm, const
             fir_step<1>(acc[0], g, v0);
             fir_step<1>(acc[1], g, v1);
         } else if (ch == G.nch - 1) {
+            fir_step<2>(acc[0], g, v0);
+            fir_step<2>(acc[1], g, v1);
+        } else {
+            fir_step<0>(acc[0], g, v0);
+            fir_step<0>(acc[1], g, v1);
+        }
+    }
+}
+
+}  // namespace fir32
+}  // namespace bf
+
+namespace bf {
+namespace fir32 {
+
+// ---- compile-time tap count: taps as kernel parameters ---------------------
+//
+// With NCH (the number of 8-input steps, Rp / 4 + 1) a template parameter the
+// FIR loops unroll completely and every tap index is a constant, so the taps
+// are read from the kernel's parameter bank as FFMA operands instead of being
+// loaded from shared memory.  R >= 1 makes NCH >= 2, so the first and last
+// steps are distinct.
+
+constexpr int kTapsMaxRp = 24;    // the tall tile's largest padded radius
+struct Taps {
+    float g[8 * (kTapsMaxRp / 4 + 1) + 16];   // g[t + 8] = g(t - Rp), 0 outside |t - Rp| <= R
+};
+
+template <int TW, int NCH>
+__device__ __forceinline__ void row_pass2c(const Geo2& G, const Taps& tp, const float* m1s,
+                                           const float* csm, const float* ssm, float* hsm,
+                                           int tid, int nthreads)
+{
+    const size_t hplane = G.hplane(TW);
+    for (int it = tid; it < G.RH * (TW / 8) * 2; it += nthreads) {
+        const int p = it & 1, rc = it >> 1;
+        const int r = rc / (TW / 8), cb = rc - r * (TW / 8);
+        const float* src = (p ? ssm : csm) + r * G.RWp + cb * 8;
+        const float* mr = m1s ? m1s + r * G.RWp + cb * 8 : nullptr;
+        float acc[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) acc[i] = 0.f;
+#pragma unroll
+        for (int ch = 0; ch < NCH; ++ch) {
+            const int a0 = ch * 8;
+            float g[15];
+#pragma unroll
+            for (int d = 0; d < 15; ++d) g[d] = tp.g[a0 + d + 1];
+            const float4 v0 = *(const float4*)(src + a0), v1 = *(const float4*)(src + a0 + 4);
+            float v[8] = {v0.x, v0.y, v0.z, v0.w, v1.x, v1.y, v1.z, v1.w};
+            if (mr) {
+                const float4 f0 = *(const float4*)(mr + a0), f1 = *(const float4*)(mr + a0 + 4);
+                v[0] *= f0.x; v[1] *= f0.y; v[2] *= f0.z; v[3] *= f0.w;
+                v[4] *= f1.x; v[5] *= f1.y; v[6] *= f1.z; v[7] *= f1.w;
+            }
+            if (ch == 0) {
+                fir_step<1>(acc, g, v);
+            } else if (ch == NCH - 1) {
+                fir_step<2>(acc, g, v);
+            } else {
+                fir_step<0>(acc, g, v);
+            }
+        }
+        float* hp = hsm + p * hplane;
+        *(float4*)(hp + hsw<TW>(r, cb * 8)) = make_float4(acc[0], acc[1], acc[2], acc[3]);
+        *(float4*)(hp + hsw<TW>(r, cb * 8 + 4)) = make_float4(acc[4], acc[5], acc[6], acc[7]);
+    }
+}
+
+template <int TW, int NCH>
+__device__ __forceinline__ void col_pass2c(const Geo2& G, const Taps& tp, const float* hsm, int o,
+                                           int rb, float (&acc)[2][8])
+{
+    const size_t hplane = G.hplane(TW);
+#pragma unroll
+    for (int q = 0; q < 2; ++q)
+#pragma unroll
+        for (int i = 0; i < 8; ++i) acc[q][i] = 0.f;
+#pragma unroll
+    for (int ch = 0; ch < NCH; ++ch) {
+        const int a0 = ch * 8;
+        float g[15];
+#pragma unroll
+        for (int d = 0; d < 15; ++d) g[d] = tp.g[a0 + d + 1];
+        float v0[8], v1[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            const int r = rb * 8 + a0 + j;
+            const int w = hsw<TW>(r, o);
+            v0[j] = hsm[w];
+            v1[j] = hsm[hplane + w];
+        }
+        if (ch == 0) {
+            fir_step<1>(acc[0], g, v0);
+            fir_step<1>(acc[1], g, v1);
+        } else if (ch == NCH - 1) {
             fir_step<2>(acc[0], g, v0);
             fir_step<2>(acc[1], g, v1);
         } else {

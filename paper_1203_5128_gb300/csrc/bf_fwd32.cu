@@ -164,18 +164,23 @@ __device__ __forceinline__ void fwd32_body(const FwdArgs& a, int by, int bx, flo
 // a time in a swizzled buffer, exact taps (see Geo2).  Same arithmetic per
 // output as fwd32_body: the nonzero taps are summed in the same order and
 // the skipped ones would have added exact zeros.
-template <int TH, int TW>
-__device__ __forceinline__ void fwd32t_body(const FwdArgs& a, int by, int bx, float* sm)
+//
+// NCH = Rp / 4 + 1 is a template parameter and the taps arrive as a kernel
+// parameter (tp.g[t + 8] = g(t - Rp)), so the fully unrolled FIR takes every
+// tap from the constant bank; the taps are the plan's FP32 taps, the same
+// words the shared-memory form reads.
+template <int TH, int TW, int NCH>
+__device__ __forceinline__ void fwd32t_body(const FwdArgs& a, const fir32::Taps& tp, int by,
+                                            int bx, float* sm)
 {
     constexpr int NT = TH * TW / 8;
     constexpr int NW = NT / 32;
     const fir32::Geo2 G(a.R, TH, TW);
     const int R = a.R, Rp = G.Rp;
     float* fsm = sm;                              // RH x RWp  centred f, 0 outside
-    float* csm = fsm + (size_t)G.RH * G.RWp;      // RH x RWp  cos
-    float* ssm = csm + (size_t)G.RH * G.RWp;      // RH x RWp  sin
-    float* hsm = ssm + (size_t)G.RH * G.RWp;      // 2 x RHp x TW  row-filtered planes
-    float* gz = hsm + 2 * (size_t)G.RHp * TW;     // gz[t + 8] = g(t - Rp), 0 outside |t - Rp| <= R
+    float* csm = fsm + G.region();                // RH x RWp  cos
+    float* ssm = csm + G.region() + 4;            // RH x RWp  sin (bank-staggered)
+    float* hsm = ssm + G.region();                // 2 planes of RHp x TW (+4), row-filtered
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int gy0 = by - Rp, gx0 = bx - Rp;
@@ -203,13 +208,9 @@ __device__ __forceinline__ void fwd32t_body(const FwdArgs& a, int by, int bx, fl
             fsm[r * G.RWp + col] = v;
         }
     }
-    for (int i = tid; i < G.ngz; i += NT) {
-        const int k = i - 8 - Rp;
-        gz[i] = (k >= -R && k <= R) ? a.taps[k + R] : 0.f;
-    }
     float cmass = 0.f;
     for (int t = -R; t <= R; ++t)
-        if (gx + t >= 0 && gx + t < a.W) cmass += a.taps[t + R];
+        if (gx + t >= 0 && gx + t < a.W) cmass += tp.g[t + Rp + 8];
     float num[8], den[8];
 #pragma unroll
     for (int i = 0; i < 8; ++i) num[i] = den[i] = 0.f;
@@ -239,16 +240,16 @@ __device__ __forceinline__ void fwd32t_body(const FwdArgs& a, int by, int bx, fl
         }
         __syncthreads();
         // numerator planes f' c, f' s
-        fir32::row_pass2<TW>(G, fsm, csm, ssm, gz, hsm, tid, NT);
+        fir32::row_pass2c<TW, NCH>(G, tp, fsm, csm, ssm, hsm, tid, NT);
         __syncthreads();
         float nab[2][8];
-        fir32::col_pass2<TW>(G, hsm, gz, o, rb, nab);
+        fir32::col_pass2c<TW, NCH>(G, tp, hsm, o, rb, nab);
         __syncthreads();
         // denominator planes c, s
-        fir32::row_pass2<TW>(G, nullptr, csm, ssm, gz, hsm, tid, NT);
+        fir32::row_pass2c<TW, NCH>(G, tp, nullptr, csm, ssm, hsm, tid, NT);
         __syncthreads();
         float dcd[2][8];
-        fir32::col_pass2<TW>(G, hsm, gz, o, rb, dcd);
+        fir32::col_pass2c<TW, NCH>(G, tp, hsm, o, rb, dcd);
 #pragma unroll
         for (int i = 0; i < 8; ++i) {
             const int ry = rb * 8 + i + Rp;
@@ -265,7 +266,7 @@ __device__ __forceinline__ void fwd32t_body(const FwdArgs& a, int by, int bx, fl
             if (gy >= a.H) continue;
             float rmass = 0.f;
             for (int t = -R; t <= R; ++t)
-                if (gy + t >= 0 && gy + t < a.H) rmass += a.taps[t + R];
+                if (gy + t >= 0 && gy + t < a.H) rmass += tp.g[t + Rp + 8];
             float v;
             if (den[i] > kGuard * rmass * cmass) {
                 v = __fdiv_rn(num[i], den[i]) + a.c0;
@@ -279,11 +280,23 @@ __device__ __forceinline__ void fwd32t_body(const FwdArgs& a, int by, int bx, fl
     }
 }
 
-template <int TH, int TW>
-__global__ void __launch_bounds__(TH * TW / 8, 1) k_fwd32t(FwdArgs a)
+template <int TH, int TW, int NCH>
+__global__ void __launch_bounds__(TH * TW / 8, 1)
+k_fwd32t(FwdArgs a, const __grid_constant__ fir32::Taps tp)
 {
     extern __shared__ __align__(16) float sm[];
-    fwd32t_body<TH, TW>(a, blockIdx.y * TH, blockIdx.x * TW, sm);
+    fwd32t_body<TH, TW, NCH>(a, tp, blockIdx.y * TH, blockIdx.x * TW, sm);
+}
+
+template <int NCH>
+cudaError_t launch_tall(const FwdArgs& a, const fir32::Taps& tp, size_t smem, cudaStream_t s)
+{
+    cudaError_t e = cudaFuncSetAttribute(k_fwd32t<128, 32, NCH>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    dim3 grid((a.W + 31) / 32, (a.H + 127) / 128);
+    k_fwd32t<128, 32, NCH><<<grid, 512, smem, s>>>(a, tp);
+    return cudaGetLastError();
 }
 
 template <int TH, int TW>
@@ -392,23 +405,34 @@ cudaError_t launch_fwd32_persistent(int th, int tw, int max_R, const FwdArgs* im
 
 size_t fwd32t_smem(int R) { return fir32::Geo2(R, 128, 32).floats(32) * sizeof(float); }
 
-// The 128 x 32 tall tile serves a launch when its shared memory fits and its
-// tiles nest inside the T-tiles.
+// The 128 x 32 tall tile serves a launch when its padded radius has a
+// compiled tap count, its shared memory fits and its tiles nest inside the
+// T-tiles.
 bool fwd32t_ok(int R, int set_tile)
 {
-    return fwd32t_smem(R) <= kSmemLimit && (set_tile == 0 || set_tile % 128 == 0);
+    return R >= 1 && (R + 3) / 4 * 4 <= fir32::kTapsMaxRp && fwd32t_smem(R) <= kSmemLimit &&
+           (set_tile == 0 || set_tile % 128 == 0);
 }
 
 cudaError_t launch_fwd32(const FwdArgs& a, cudaStream_t s)
 {
-    if (fwd32t_ok(a.R, a.set_tile)) {
+    if (a.h_taps && fwd32t_ok(a.R, a.set_tile)) {
+        const fir32::Geo2 G(a.R, 128, 32);
+        fir32::Taps tp;
+        for (int i = 0; i < (int)(sizeof(tp.g) / sizeof(float)); ++i) {
+            const int k = i - 8 - G.Rp;
+            tp.g[i] = (k >= -a.R && k <= a.R) ? a.h_taps[k + a.R] : 0.f;
+        }
         const size_t smem = fwd32t_smem(a.R);
-        cudaError_t e = cudaFuncSetAttribute(k_fwd32t<128, 32>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        dim3 grid((a.W + 31) / 32, (a.H + 127) / 128);
-        k_fwd32t<128, 32><<<grid, 512, smem, s>>>(a);
-        return cudaGetLastError();
+        switch (G.nch) {
+            case 2: return launch_tall<2>(a, tp, smem, s);
+            case 3: return launch_tall<3>(a, tp, smem, s);
+            case 4: return launch_tall<4>(a, tp, smem, s);
+            case 5: return launch_tall<5>(a, tp, smem, s);
+            case 6: return launch_tall<6>(a, tp, smem, s);
+            case 7: return launch_tall<7>(a, tp, smem, s);
+            default: break;
+        }
     }
     int th, tw;
     fwd32_tile(a.R, &th, &tw);

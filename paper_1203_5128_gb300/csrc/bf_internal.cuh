@@ -25,6 +25,7 @@ struct bf_plan_s {
     bf::SetHdr* d_hdr;
     bf::Pair* d_pairs;
     float* d_taps;
+    float* h_taps;          // host copy of the 2R+1 taps
     double* d_logfact;
     unsigned* d_status;
     unsigned long long* d_nguard;
@@ -112,6 +113,7 @@ struct FwdArgs {
     unsigned long long* n_guarded;
     float* den_out;         // optional: den per pixel (backward)
     size_t den_pitch;
+    const float* h_taps;    // host copy of taps (null: shared-memory taps only)
 };
 // Output tile of the FP32 kernel for a given R (0 if unsupported).
 void fwd32_tile(int R, int* th, int* tw);

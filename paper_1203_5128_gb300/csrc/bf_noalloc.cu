@@ -158,6 +158,11 @@ extern "C" bf_status bf_execute_noalloc(const float* f, size_t f_pitch, float* o
     fa.n_guarded = &s->n_guarded;
     fa.den_out = nullptr;
     fa.den_pitch = 0;
+    // the same taps on the host, for the kernels that take them as a parameter
+    float h_taps[2 * kNoAllocMaxR + 1];
+    for (int k = -R; k <= R; ++k)
+        h_taps[k + R] = (float)exp(-(double)k * (double)k / (2.0 * sigma_s * sigma_s));
+    fa.h_taps = h_taps;
     if (launch_fwd32(fa, st) != cudaSuccess) return BF_ERR_CUDA;
     return BF_OK;
 }
