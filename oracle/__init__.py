@@ -17,8 +17,10 @@ strings the steps together in the order of Algorithm 2:
 
 Parity status: every function here is pinned by ``tests/test_oracle_pins.py``
 (closed forms, invariants, brute force, exact rational arithmetic and the
-values the paper prints) except the Young-van Vliet mode, which has no
-printed value to compare against ("parity unpinned" for that mode only).
+values the paper prints).  The Young-van Vliet mode (``spatial="yvv"``) is
+pinned by ``tests/test_oracle_yvv.py`` against the recursion's closed-form
+frequency response, brute-force convolution with its impulse response and
+the direct form; the paper prints no value for it.
 """
 from __future__ import annotations
 
@@ -79,6 +81,11 @@ def _load():
         "orc_direct_points": (L, [P, I, I, P, I, P, P, D, I, P, P, I, P, P, P]),
         "orc_grad_shiftable_block": (None, [P, I, I, P, I, I, I, D, I, I, I, I, P, P, P]),
         "orc_grad_direct_points": (None, [P, I, I, P, I, I, I, D, P, P, P, P, I, P]),
+        "orc_yvv_coeffs": (None, [D, P]),
+        "orc_yvv_margin": (I, [D]),
+        "orc_yvv_2d": (None, [P, P, I, I, D, I]),
+        "orc_yvv_impulse": (None, [D, I, P]),
+        "orc_shiftable_yvv": (L, [P, I, I, D, I, I, D, P, P, P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -257,13 +264,55 @@ def _blocks(p: Params, H: int, W: int):
             yield a, b, y0, min(H, y0 + p.tile_h), x0, min(W, x0 + p.tile_w)
 
 
+# ---------------------------------------------------------------- recursive filter
+
+def yvv_coeffs(sigma: float) -> np.ndarray:
+    """[B, b1/b0, b2/b0, b3/b0] of the Young-van Vliet recursion."""
+    c = np.empty(4)
+    _load().orc_yvv_coeffs(float(sigma), _p(c))
+    return c
+
+
+def yvv_margin(sigma: float) -> int:
+    return _load().orc_yvv_margin(float(sigma))
+
+
+def yvv_2d(img, sigma: float, margin: int = -1) -> np.ndarray:
+    """Rows, then columns, of the recursion on the zero-extended image."""
+    img = _f64(img)
+    out = np.empty_like(img)
+    _load().orc_yvv_2d(_p(img), _p(out), img.shape[0], img.shape[1], float(sigma), int(margin))
+    return out
+
+
+def yvv_impulse(sigma: float, half: int) -> np.ndarray:
+    """h[d + half], d = -half..half."""
+    h = np.empty(2 * half + 1)
+    _load().orc_yvv_impulse(float(sigma), int(half), _p(h))
+    return h
+
+
 # ---------------------------------------------------------------- filters
 
-def shiftable(f, sigma_s: float, sigma_r: float, params: Params, *, return_parts=False):
+def shiftable(f, sigma_s: float, sigma_r: float, params: Params, *, return_parts=False,
+              spatial: str = "fir"):
     """SHIFTABLE-BF (Sec. 1.2) with phi_eps per T-tile.  Returns out (and
-    num, den, number of guarded pixels when return_parts)."""
+    num, den, number of guarded pixels when return_parts).  ``spatial``
+    "yvv" filters the planes with the Young-van Vliet recursion instead of
+    the truncated Gaussian (single kernel only)."""
     f = _f64(f)
     H, W = f.shape
+    if spatial == "yvv":
+        assert params.T.size == 1, "the recursive mode takes one (N, M)"
+        out, num, den = np.empty_like(f), np.empty_like(f), np.empty_like(f)
+        nfb = _load().orc_shiftable_yvv(_p(f), H, W, float(sigma_s), int(params.N[0, 0]),
+                                        int(params.M[0, 0]), float(sigma_r),
+                                        _p(out), _p(num), _p(den))
+        if return_parts:
+            return out, num, den, nfb
+        return out
+    if spatial != "fir":
+        raise ValueError(spatial)
     g = taps(sigma_s, params.R)
     out = np.empty_like(f)
     num = np.empty_like(f)
@@ -285,10 +334,13 @@ def _tile_of(params: Params, ys, xs):
 
 
 def direct(f, sigma_s: float, sigma_r: float, params: Params | None = None, *,
-           points=None, gauss: bool = False, return_parts=False):
+           points=None, gauss: bool = False, return_parts=False, spatial: str = "fir"):
     """Direct sum of eq. (BF) at the given points (all pixels if None), with
     the range kernel phi_eps of each point's T-tile, or the Gaussian itself
-    when ``gauss``.  Returns values in the order of ``points`` (or an image)."""
+    when ``gauss``.  Returns values in the order of ``points`` (or an image).
+    ``spatial`` "yvv" weighs neighbours by the product of the recursion's
+    one-dimensional impulse responses over the whole image instead of the
+    truncated Gaussian."""
     f = _f64(f)
     H, W = f.shape
     if points is None:
@@ -298,8 +350,14 @@ def direct(f, sigma_s: float, sigma_r: float, params: Params | None = None, *,
         ys, xs = np.asarray(points[0]), np.asarray(points[1])
     ys = np.ascontiguousarray(ys, dtype=np.int32)
     xs = np.ascontiguousarray(xs, dtype=np.int32)
-    R = radius(sigma_s) if params is None else params.R
-    g = taps(sigma_s, R)
+    if spatial == "yvv":
+        R = max(H, W)
+        g = yvv_impulse(sigma_s, R)
+    elif spatial == "fir":
+        R = radius(sigma_s) if params is None else params.R
+        g = taps(sigma_s, R)
+    else:
+        raise ValueError(spatial)
     if gauss:
         Ns = np.ones(ys.size, np.int32)
         Ms = np.zeros(ys.size, np.int32)

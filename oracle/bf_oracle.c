@@ -23,7 +23,9 @@
  *   - M: eq. (trunc) literally, eq. (Chernoff) floored, or the sigma_r bands
  *     of Algorithm 2;
  *   - denominator guard: where den <= 1e-6 * (g * 1_Omega)(x) the output is
- *     f(x) (the paper is silent; phi_eps may dip to -eps on its tails).
+ *     f(x) (the paper is silent; phi_eps may dip to -eps on its tails);
+ *   - recursive mode: the Young-van Vliet recursion applied to the image
+ *     extended by zeros without limit (a margin beyond double precision).
  */
 #include <math.h>
 #include <stdlib.h>
@@ -349,6 +351,149 @@ long orc_shiftable_block(const double *f, int H, int W, const double *g, int R,
             if (den_out) den_out[(size_t)y * W + x] = den[k];
         }
     free(P); free(Hp); free(num); free(den); free(lw);
+    return nfb;
+}
+
+/* ------------------------------------------------------------------ */
+/* Recursive Gaussian (Young and van Vliet, Signal Processing 44, 1995) */
+/* as the "recursive O(1)" spatial filter that Sec. 1.2 allows in place */
+/* of the truncated Gaussian.  The recursion is the published method;   */
+/* the paper itself names no particular recursive filter.               */
+/* ------------------------------------------------------------------ */
+
+/* Coefficients of the third-order recursion for scale sigma (>= 0.5):
+ *   q  = 0.98711 sigma - 0.96330                   for sigma >= 2.5,
+ *   q  = 3.97156 - 4.14554 sqrt(1 - 0.26891 sigma) for 0.5 <= sigma < 2.5,
+ *   b0 = 1.57825 + 2.44413 q + 1.4281 q^2 + 0.422205 q^3,
+ *   b1 = 2.44413 q + 2.85619 q^2 + 1.26661 q^3,
+ *   b2 = -(1.4281 q^2 + 1.26661 q^3),
+ *   b3 = 0.422205 q^3,
+ *   B  = 1 - (b1 + b2 + b3) / b0  (unit gain at zero frequency).
+ * c[0] = B and c[k] = bk / b0 for k = 1, 2, 3. */
+void orc_yvv_coeffs(double sigma, double *c)
+{
+    double q;
+    if (sigma >= 2.5) q = 0.98711 * sigma - 0.96330;
+    else q = 3.97156 - 4.14554 * sqrt(1.0 - 0.26891 * sigma);
+    const double q2 = q * q, q3 = q2 * q;
+    const double b0 = 1.57825 + 2.44413 * q + 1.4281 * q2 + 0.422205 * q3;
+    const double b1 = 2.44413 * q + 2.85619 * q2 + 1.26661 * q3;
+    const double b2 = -(1.4281 * q2 + 1.26661 * q3);
+    const double b3 = 0.422205 * q3;
+    c[0] = 1.0 - (b1 + b2 + b3) / b0;
+    c[1] = b1 / b0;
+    c[2] = b2 / b0;
+    c[3] = b3 / b0;
+}
+
+/* Length of the zero extension that stands for an infinite one: the
+ * recursion's impulse response decays like |pole|^d with 1 - |pole| of
+ * order 1/sigma, so 60 sigma + 64 samples leave a tail far below double
+ * precision for every sigma (the tests check that doubling it changes
+ * nothing). */
+int orc_yvv_margin(double sigma) { return (int)ceil(60.0 * sigma) + 64; }
+
+/* The filter on one line of n samples x[0], x[stride], ... (in place),
+ * the line extended by zeros on both sides:
+ *   causal      w[i] = B x[i] + c1 w[i-1] + c2 w[i-2] + c3 w[i-3],
+ *               zero state before i = 0, run on through L zeros past the end;
+ *   anti-causal y[i] = B w[i] + c1 y[i+1] + c2 y[i+2] + c3 y[i+3],
+ *               zero state after i = n - 1 + L, run back to i = 0.
+ * (Zeros before the line leave the causal state at zero, so only the right
+ * extension needs samples.)  w holds n + L doubles of scratch. */
+static void yvv_line(double *x, int n, long stride, const double *c, int L, double *w)
+{
+    const double B = c[0];
+    double w1 = 0.0, w2 = 0.0, w3 = 0.0;
+    for (int i = 0; i < n + L; ++i) {
+        const double xi = i < n ? x[(long)i * stride] : 0.0;
+        const double wi = B * xi + c[1] * w1 + c[2] * w2 + c[3] * w3;
+        w[i] = wi;
+        w3 = w2; w2 = w1; w1 = wi;
+    }
+    double y1 = 0.0, y2 = 0.0, y3 = 0.0;
+    for (int i = n + L - 1; i >= 0; --i) {
+        const double yi = B * w[i] + c[1] * y1 + c[2] * y2 + c[3] * y3;
+        if (i < n) x[(long)i * stride] = yi;
+        y3 = y2; y2 = y1; y1 = yi;
+    }
+}
+
+/* Two-dimensional filter: every row, then every column, of the H x W image
+ * in (margin L; L < 0 takes orc_yvv_margin(sigma)), written to out. */
+void orc_yvv_2d(const double *in, double *out, int H, int W, double sigma, int L)
+{
+    double c[4];
+    orc_yvv_coeffs(sigma, c);
+    if (L < 0) L = orc_yvv_margin(sigma);
+    if (out != in) memcpy(out, in, sizeof(double) * (size_t)H * W);
+    #pragma omp parallel
+    {
+        double *w = (double *)malloc(sizeof(double) * (size_t)((H > W ? H : W) + L));
+        #pragma omp for schedule(static)
+        for (int i = 0; i < H; ++i) yvv_line(out + (size_t)i * W, W, 1, c, L, w);
+        #pragma omp for schedule(static)
+        for (int j = 0; j < W; ++j) yvv_line(out + j, H, W, c, L, w);
+        free(w);
+    }
+}
+
+/* Impulse response h[d + half], d = -half..half: the filtered line of
+ * 2 half + 1 samples with a unit sample in the middle. */
+void orc_yvv_impulse(double sigma, int half, double *h)
+{
+    double c[4];
+    orc_yvv_coeffs(sigma, c);
+    const int n = 2 * half + 1, L = orc_yvv_margin(sigma);
+    double *w = (double *)malloc(sizeof(double) * (size_t)(n + L));
+    for (int i = 0; i < n; ++i) h[i] = 0.0;
+    h[half] = 1.0;
+    yvv_line(h, n, 1, c, L, w);
+    free(w);
+}
+
+/* SHIFTABLE-BF with the recursive filter in step 2, one kernel (N, M) for
+ * the whole image (every output depends on every pixel, so blocks do not
+ * apply).  For each kept n (no folding): planes f c, f s, c, s over the
+ * image; each filtered by orc_yvv_2d; num += w_n (c Fc + s Fs),
+ * den += w_n (c Gc + s Gs).  Guard: den <= 1e-6 Y(1_Omega)(x) -> f(x),
+ * Y(1_Omega) being the same filter applied to the indicator of the image.
+ * Returns the number of guarded pixels. */
+long orc_shiftable_yvv(const double *f, int H, int W, double sigma_s, int N, int M,
+                       double sigma_r, double *out, double *num_out, double *den_out)
+{
+    const size_t n_px = (size_t)H * W;
+    double *P = (double *)malloc(sizeof(double) * 4 * n_px);
+    double *num = (double *)calloc(n_px, sizeof(double));
+    double *den = (double *)calloc(n_px, sizeof(double));
+    double *mass = (double *)malloc(sizeof(double) * n_px);
+    double *lw = (double *)malloc(sizeof(double) * (size_t)(N + 1));
+    orc_log_weights(N, lw);
+    const double scale = sqrt((double)N) * sigma_r;
+    for (int n = M; n <= N - M; ++n) {
+        const double wn = exp(lw[n]);
+        const double om = (double)(2 * n - N) / scale;
+        for (size_t k = 0; k < n_px; ++k) {
+            const double v = f[k], c = cos(om * v), s = sin(om * v);
+            P[k] = v * c; P[n_px + k] = v * s; P[2 * n_px + k] = c; P[3 * n_px + k] = s;
+        }
+        for (int q = 0; q < 4; ++q) orc_yvv_2d(P + q * n_px, P + q * n_px, H, W, sigma_s, -1);
+        for (size_t k = 0; k < n_px; ++k) {
+            const double v = f[k], c = cos(om * v), s = sin(om * v);
+            num[k] += wn * (c * P[k] + s * P[n_px + k]);
+            den[k] += wn * (c * P[2 * n_px + k] + s * P[3 * n_px + k]);
+        }
+    }
+    for (size_t k = 0; k < n_px; ++k) mass[k] = 1.0;
+    orc_yvv_2d(mass, mass, H, W, sigma_s, -1);
+    long nfb = 0;
+    for (size_t k = 0; k < n_px; ++k) {
+        if (den[k] > 1e-6 * mass[k]) out[k] = num[k] / den[k];
+        else { out[k] = f[k]; ++nfb; }
+        if (num_out) num_out[k] = num[k];
+        if (den_out) den_out[k] = den[k];
+    }
+    free(P); free(num); free(den); free(mass); free(lw);
     return nfb;
 }
 
