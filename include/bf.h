@@ -70,7 +70,19 @@ enum {
     BF_RULE_CHERNOFF = 2 /* eq. (Chernoff), floored                           */
 };
 
-/* Spatial filter of the modulated planes (step 3 of SHIFTABLE-BF). */
+/* Spatial filter of the modulated planes (step 2 of SHIFTABLE-BF, Sec. 1.2).
+ * FIR: the Gaussian truncated to the (2R+1)^2 window, clipped at the image
+ * border.  YVV: the "recursive O(1)" filter that Sec. 1.2 admits, here the
+ * third-order recursion of Young and van Vliet (1995), causal plus
+ * anti-causal per row then per column, on the image extended by zeros
+ * without limit; it approximates the Gaussian of scale sigma_s (a few per
+ * cent) at a cost per pixel independent of sigma_s.  YVV needs sigma_s >=
+ * 0.5, FP32 planes and t_mode FIXED or GLOBAL (else BF_ERR_NOT_SUPPORTED);
+ * its plan holds H x W x C x 16 B of row-filtered planes (C = 8, 16 or 32
+ * terms per pass, from the cap on N) and 8 B per pixel of num/den.
+ * bf_backward and bf_execute_batch take FIR plans only.  AUTO = FIR: the two
+ * filters give different results, so the library never swaps one for the
+ * other. */
 enum { BF_FILTER_AUTO = 0, BF_FILTER_FIR = 1, BF_FILTER_YVV = 2 };
 
 /* Storage / multiply type of the modulated planes. */

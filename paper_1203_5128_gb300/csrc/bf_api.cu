@@ -59,6 +59,9 @@ void free_plan(bf_plan_s* p)
     cudaFree(p->d_nguard);
     cudaFree(p->d_hin);
     cudaFree(p->d_hout);
+    cudaFree(p->d_yvv_P);
+    cudaFree(p->d_yvv_nd);
+    cudaFree(p->d_yvv_mass);
     cudaFree(p->d_bwd);
     if (p->ev) {
         for (int i = 0; i < 4 * kMaxTimed; ++i)
@@ -92,6 +95,27 @@ ParamsArgs params_args(bf_plan_s* p)
 namespace bf {
 
 ParamsArgs plan_params_args(bf_plan_s* p) { return params_args(p); }
+
+YvvArgs yvv_args(bf_plan_s* p, const float* f, size_t fp, float* out, size_t op)
+{
+    YvvArgs a;
+    a.f = f;
+    a.f_pitch = fp;
+    a.out = out;
+    a.out_pitch = op;
+    a.H = p->H;
+    a.W = p->W;
+    a.c0 = p->c0;
+    a.hdr = p->d_hdr;
+    a.pairs = p->d_pairs;
+    a.P = p->d_yvv_P;
+    a.nd = p->d_yvv_nd;
+    a.mass_y = p->d_yvv_mass;
+    a.mass_x = p->d_yvv_mass + p->H;
+    a.n_guarded = p->d_nguard;
+    yvv_design(p->sigma_s, &a.coef, nullptr);
+    return a;
+}
 
 FwdArgs forward_args(bf_plan_s* p, const float* f, size_t fp, float* out, size_t op)
 {
@@ -206,8 +230,14 @@ bf_status bf_plan(int H, int W, double sigma_s, double sigma_r, double eps, cons
     for (int i = 0; i < 8; ++i)
         if (o.reserved[i]) return BF_ERR_INVALID_ARG;
     if (o.filter == BF_FILTER_AUTO) o.filter = BF_FILTER_FIR;
-    if (o.filter != BF_FILTER_FIR) return BF_ERR_NOT_SUPPORTED;
+    if (o.filter != BF_FILTER_FIR && o.filter != BF_FILTER_YVV) return BF_ERR_INVALID_ARG;
     if (o.plane_dtype < BF_PLANES_FP32 || o.plane_dtype > BF_PLANES_FP16) return BF_ERR_INVALID_ARG;
+    // the recursive filter: FP32 planes, one parameter set per image (every
+    // output depends on the whole image), and the recursion's range of scales
+    YvvCoef yc;
+    if (o.filter == BF_FILTER_YVV &&
+        (o.plane_dtype != BF_PLANES_FP32 || o.t_mode == BF_T_TILE || !yvv_design(sigma_s, &yc, nullptr)))
+        return BF_ERR_NOT_SUPPORTED;
     if (o.t_mode == BF_T_TILE && (o.t_tile < 64 || o.t_tile % 64)) return BF_ERR_INVALID_ARG;
     // the 16-bit planes run on the tensor cores with 128 x 32 output tiles,
     // which must nest inside the T-tiles
@@ -221,7 +251,9 @@ bf_status bf_plan(int H, int W, double sigma_s, double sigma_r, double eps, cons
     const int R = (int)Rr;
     if (o.t_mode != BF_T_FIXED && R > range_max_radius()) return BF_ERR_NOT_SUPPORTED;
     int th = 0, tw = 0;
-    if (o.plane_dtype == BF_PLANES_FP32) {
+    if (o.filter == BF_FILTER_YVV) {
+        th = tw = 1;                      // whole lines, no output tiles
+    } else if (o.plane_dtype == BF_PLANES_FP32) {
         fwd32_tile(R, &th, &tw);
         if (fwd32t_ok(R, o.t_mode == BF_T_TILE ? o.t_tile : 0)) {
             th = 128;
@@ -301,6 +333,31 @@ bf_status bf_plan(int H, int W, double sigma_s, double sigma_r, double eps, cons
         float T = o.t_fixed;
         ok &= cudaMemcpy(p->d_T, &T, sizeof(float), cudaMemcpyHostToDevice) == cudaSuccess;
     }
+    if (ok && o.filter == BF_FILTER_YVV) {
+        // terms per pass from the cap (pairs + zero frequency); workspace:
+        // row-filtered planes [H][W][C] x 16 B, (num, den) [H][W], masses
+        const int cap_terms = p->cap_pairs + 1;
+        p->yvv_C = yvv_terms_per_pass(cap_terms);
+        p->yvv_passes = (cap_terms + p->yvv_C - 1) / p->yvv_C;
+        const size_t npx = (size_t)H * W;
+        if (cudaMalloc(&p->d_yvv_P, npx * p->yvv_C * sizeof(float4)) != cudaSuccess ||
+            cudaMalloc(&p->d_yvv_nd, npx * sizeof(float2)) != cudaSuccess ||
+            cudaMalloc(&p->d_yvv_mass, sizeof(float) * ((size_t)H + W)) != cudaSuccess) {
+            cudaGetLastError();
+            free_plan(p);
+            return BF_ERR_ALLOC;
+        }
+        float* m = (float*)malloc(sizeof(float) * ((size_t)H + W));
+        if (!m) {
+            free_plan(p);
+            return BF_ERR_ALLOC;
+        }
+        yvv_line_mass(sigma_s, H, m);
+        yvv_line_mass(sigma_s, W, m + H);
+        ok &= cudaMemcpy(p->d_yvv_mass, m, sizeof(float) * ((size_t)H + W),
+                         cudaMemcpyHostToDevice) == cudaSuccess;
+        free(m);
+    }
     if (!ok) {
         free_plan(p);
         return BF_ERR_CUDA;
@@ -317,7 +374,9 @@ bf_status bf_execute(bf_plan_t p, const float* f, size_t fp, float* out, size_t 
     cudaStream_t s = (cudaStream_t)stream;
     BF_CUDA(cudaSetDevice(p->device));
     BF_CUDA(enqueue_params(p, f, fp, s));
-    if (p->opt.plane_dtype == BF_PLANES_FP32)
+    if (p->opt.filter == BF_FILTER_YVV)
+        BF_CUDA(launch_yvv(yvv_args(p, f, fp, out, op), p->yvv_C, p->yvv_passes, s));
+    else if (p->opt.plane_dtype == BF_PLANES_FP32)
         BF_CUDA(launch_fwd32(forward_args(p, f, fp, out, op), s));
     else
         BF_CUDA(launch_fwd_tc(forward_args(p, f, fp, out, op),
@@ -353,6 +412,7 @@ bf_status bf_backward(bf_plan_t p, const float* f, const float* gout, float* gin
 {
     if (!p || !f || !gout || !gin) return BF_ERR_INVALID_ARG;
     if (pitch < (size_t)p->W) return BF_ERR_INVALID_ARG;
+    if (p->opt.filter == BF_FILTER_YVV) return BF_ERR_NOT_SUPPORTED;
     if (!p->executed) return BF_ERR_NO_FORWARD;
     cudaStream_t s = (cudaStream_t)stream;
     BF_CUDA(cudaSetDevice(p->device));

@@ -34,6 +34,10 @@ struct bf_plan_s {
     float* d_bwd;            // backward scratch (out, den), allocated on first use
     int executed;
     cudaStream_t last;
+    int yvv_C, yvv_passes;   // recursive filter: terms per pass, passes
+    float4* d_yvv_P;         // recursive filter: row-filtered planes [H][W][C]
+    float2* d_yvv_nd;        // recursive filter: (num, den) per pixel
+    float* d_yvv_mass;       // recursive filter: mass_y[H] then mass_x[W]
     int timing;              // record events around the kernels
     int n_timed;
     cudaEvent_t* ev;         // 4 per recorded execute
@@ -140,6 +144,38 @@ struct BwdArgs {
     float c0;
 };
 void bwd32_tile(int R, int* th, int* tw);
+
+// K3-yvv (recursive spatial filter): first-order sections of the Young-van
+// Vliet recursion's poles, as FP32 (p0 real pole, p1 = Pr + i Pi; causal
+// output C0 u0 + Cr Re u1 - Ci Im u1, anti-causal output D0 v0 + Dr Re v1 -
+// Di Im v1).
+struct YvvCoef {
+    float P0, Pr, Pi;
+    float C0, Cr, Ci;
+    float D0, Dr, Di;
+};
+struct YvvArgs {
+    const float* f;
+    size_t f_pitch;
+    float* out;
+    size_t out_pitch;
+    int H, W;
+    float c0;
+    const SetHdr* hdr;
+    const Pair* pairs;
+    float4* P;              // [H][W][C] row-filtered planes
+    float2* nd;             // [H][W] (num, den)
+    const float* mass_y;    // [H]
+    const float* mass_x;    // [W]
+    unsigned long long* n_guarded;
+    YvvCoef coef;
+};
+// Plan-time design (false when sigma < 0.5, outside the recursion's range);
+// poles_c (may be null) receives p0, Re p1, Im p1, c0, Re c1, Im c1.
+bool yvv_design(double sigma, YvvCoef* out, double* poles_c);
+void yvv_line_mass(double sigma, int n, float* mass);
+int yvv_terms_per_pass(int n_terms_cap);
+cudaError_t launch_yvv(const YvvArgs& a, int C, int n_passes, cudaStream_t s);
 cudaError_t launch_bwd32(const BwdArgs& a, cudaStream_t s);
 
 // ---- batched path (bf_execute_batch) ----------------------------------------
