@@ -35,6 +35,7 @@ H = W = 4096
 SIGMA_S, SIGMA_R, EPS, SEED = 8.0, 10.0, 0.01, 5
 TUNED = dict(t_mode="global", trunc_rule="alg2", plane_dtype="fp16", filter="fir")
 TUNED_FP32 = dict(t_mode="global", trunc_rule="alg2", plane_dtype="fp32", filter="fir")
+TUNED_YVV = dict(t_mode="global", trunc_rule="alg2", plane_dtype="fp32", filter="yvv")
 PLAIN = dict(t_mode="fixed", t_fixed=255.0, trunc_rule="alg2", plane_dtype="fp32", filter="fir")
 SM_COUNT_NOMINAL = 152
 FP32_LANES_PER_SM = 128
@@ -186,7 +187,8 @@ def workload_config():
                         "Algorithm 2 (exact T, eps=1e-2), FP16 planes on tcgen05 vs plain "
                         "(T=255, eps=0, FP32 planes)",
             "H": H, "W": W, "sigma_s": SIGMA_S, "sigma_r": SIGMA_R, "eps": EPS,
-            "seed": SEED, "tuned": TUNED, "tuned_fp32": TUNED_FP32, "plain": PLAIN,
+            "seed": SEED, "tuned": TUNED, "tuned_fp32": TUNED_FP32, "tuned_yvv": TUNED_YVV,
+            "plain": PLAIN,
             "l2": "flushed (256 MB write) before every timed step, outside the timed interval"}
 
 
@@ -200,6 +202,17 @@ def fp32_instr_per_px(N, M, R):
     z = 1 if N % 2 == 0 else 0
     taps = 2 * R + 1
     return F * (8 * taps + 7) + z * (4 * taps + 2) + 3
+
+
+def yvv_instr_per_px(N, M):
+    """Algorithmic FP32 instructions per output pixel of the recursive
+    filter: per plane a third-order recursion each way along rows and along
+    columns (4 instructions per step, 16 per plane-pixel); per pair 4 planes,
+    2 plane products, 4 demodulation FMAs and 1 weight (71); per zero term
+    2 planes + 2 (34); plus 3 for the normalisation."""
+    F = (N - M) - N // 2
+    z = 1 if N % 2 == 0 else 0
+    return F * 71 + z * 34 + 3
 
 
 def fir_flops_per_px(N, M, R):
@@ -292,6 +305,70 @@ def main():
     t32_ms = max_over_ranks(t32_ms)
     t32_value = world * px * s32 / (t32_ms * 1e3)
 
+    # ---- the same Algorithm 2 with the recursive (Young-van Vliet) filter
+    tyv = bf.bf_plan(H, W, SIGMA_S, SIGMA_R, EPS, **TUNED_YVV)
+    bf.bf_execute(tyv, f, out)
+    torch.cuda.synchronize()
+    info_yv = bf.bf_get_info(tyv)
+    yv_ms, yv_kms, yv_cnt = timed(tyv, s32, 1)
+    yv_ms = max_over_ranks(yv_ms)
+    yv_value = world * px * s32 / (yv_ms * 1e3)
+
+    # ---- batched: 64 images of uneven sizes, each with its own sigma_s and
+    # sigma_r, one bf_execute_batch (graph: batched K1, K2, persistent K4)
+    # against 64 bf_execute calls
+    specs = synth.batch_specs(64, seed=3)
+    b_plans = [bf.bf_plan(bh, bw, bss, bsr, EPS) for bh, bw, bss, bsr in specs]
+    b_fs = [torch.from_numpy(synth.g8(bh, bw, seed=3000 + k)).cuda()
+            for k, (bh, bw, _, _) in enumerate(specs)]
+    b_outs = [torch.empty_like(t) for t in b_fs]
+    b_px = sum(bh * bw for bh, bw, _, _ in specs)
+    bf.bf_execute_batch(b_plans, b_fs, b_outs)          # capture + tile autotune
+    for bp, bfi, bo in zip(b_plans, b_fs, b_outs):
+        bf.bf_execute(bp, bfi, bo)
+    barrier()
+    b_steps = max(1, min(args.plain_steps, args.steps))
+
+    def time_region(fn, n):
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+               for _ in range(n)]
+        for a_, b_ in evs:
+            flush.zero_()
+            a_.record(stream)
+            fn()
+            b_.record(stream)
+        barrier()
+        return sum(a_.elapsed_time(b_) for a_, b_ in evs) / n
+
+    bg_ms = max_over_ranks(time_region(lambda: bf.bf_execute_batch(b_plans, b_fs, b_outs), b_steps))
+
+    def separate():
+        for bp, bfi, bo in zip(b_plans, b_fs, b_outs):
+            bf.bf_execute(bp, bfi, bo)
+
+    bs_ms = max_over_ranks(time_region(separate, b_steps))
+    for bp in b_plans:
+        bp.close()
+    del b_fs, b_outs
+
+    # ---- differentiation: 16 x 512 x 512, sigma_s = 4, sigma_r = 25, eps = 1e-2,
+    # forward + hand-written adjoint of L = sum(w * out) per image
+    d_plan = bf.bf_plan(512, 512, 4.0, 25.0, 0.01)
+    d_fs = [torch.from_numpy(synth.g8(512, 512, seed=700 + i)).cuda() for i in range(16)]
+    d_w = torch.from_numpy(synth.weights_normal((512, 512), seed=4)).cuda()
+    d_out = torch.empty_like(d_fs[0])
+    d_grad = torch.empty_like(d_fs[0])
+
+    def fwd_bwd():
+        for fi in d_fs:
+            bf.bf_execute(d_plan, fi, d_out)
+            bf.bf_backward(d_plan, fi, d_w, d_grad)
+
+    fwd_bwd()
+    barrier()
+    d_ms = max_over_ranks(time_region(fwd_bwd, b_steps))
+    d_plan.close()
+
     # ---- plain FP32 (context for the metric's ratio)
     plain = bf.bf_plan(H, W, SIGMA_S, SIGMA_R, 0.0, **PLAIN)
     bf.bf_execute(plain, f, out)
@@ -346,6 +423,14 @@ def main():
               "kernel": "k_fwd32 (FP32 planes, SIMT FIR)", "launch_ms": k32_ms,
               "peak_source": "%d SMs x %d FP32 lanes x %.0f MHz (%s sm_max_mhz)" % (
                   sms, FP32_LANES_PER_SM, mhz, pk_kind)}
+    kyv_ms = yv_kms[2] / max(yv_cnt, 1)
+    iyv = yvv_instr_per_px(info_yv.N, info_yv.M) * px
+    roofyv = {"bound": "alu", "achieved": iyv / (kyv_ms * 1e-3) / 1e12, "peak": peak_tinst,
+              "unit": "Tinstr/s (FP32)", "frac": iyv / (kyv_ms * 1e-3) / 1e12 / peak_tinst,
+              "kernel": "k_yvv_rows + k_yvv_cols + k_yvv_final (recursive filter, FP32)",
+              "launch_ms": kyv_ms,
+              "peak_source": "%d SMs x %d FP32 lanes x %.0f MHz (%s sm_max_mhz)" % (
+                  sms, FP32_LANES_PER_SM, mhz, pk_kind)}
     p_k3 = p_kms[2] / max(p_cnt, 1)
     p_instr = fp32_instr_per_px(info_p.N, info_p.M, info_p.R) * px
 
@@ -373,7 +458,21 @@ def main():
                   "K": info_p.K, "forward_ms": p_k3,
                   "fp32_frac": p_instr / (p_k3 * 1e-3) / 1e12 / peak_tinst},
         "tuned_fp32": {"value": t32_value, "ms_per_step": t32_ms / s32, "roofline": roof32},
+        "tuned_yvv": {"value": yv_value, "ms_per_step": yv_ms / s32, "roofline": roofyv,
+                      "note": "Young-van Vliet recursion in place of the FIR: approximates "
+                              "the Gaussian; parity is against the oracle's recursive mode"},
         "speedup_vs_plain": value / plain_value,
+        "batch": {"images": len(specs), "pixels": b_px,
+                  "workload": "64 G8 images, sides U[128,2048], sigma_s U[2,16], sigma_r "
+                              "U[10,60], eps=1e-2, exact T, FP32 planes",
+                  "graph": {"value": world * b_px / (bg_ms * 1e3), "unit": "Mpixel/s",
+                            "ms": bg_ms},
+                  "separate_calls": {"value": world * b_px / (bs_ms * 1e3), "unit": "Mpixel/s",
+                                     "ms": bs_ms}},
+        "backward": {"workload": "16 x 512x512 G8, sigma_s=4, sigma_r=25, eps=1e-2, exact T; "
+                                "forward + adjoint of L = sum(w * out), w ~ N(0,1)",
+                     "value": world * 16 * 512 * 512 / (d_ms * 1e3), "unit": "Mpixel/s",
+                     "ms": d_ms},
     }
     print(json.dumps(line), flush=True)
     if dist is not None:

@@ -78,8 +78,9 @@ enum {
  * without limit; it approximates the Gaussian of scale sigma_s (a few per
  * cent) at a cost per pixel independent of sigma_s.  YVV needs sigma_s >=
  * 0.5, FP32 planes and t_mode FIXED or GLOBAL (else BF_ERR_NOT_SUPPORTED);
- * its plan holds H x W x C x 16 B of row-filtered planes (C = 8, 16 or 32
- * terms per pass, from the cap on N) and 8 B per pixel of num/den.
+ * its plan holds 512 B per pixel of row-filtered planes (32 terms at a
+ * time), 24 B per pixel of row states and 8 B per pixel per pass group of
+ * num/den partials (2 or 4 groups): about 9.1 GB at 4096 x 4096.
  * bf_backward and bf_execute_batch take FIR plans only.  AUTO = FIR: the two
  * filters give different results, so the library never swaps one for the
  * other. */

@@ -60,6 +60,7 @@ void free_plan(bf_plan_s* p)
     cudaFree(p->d_hin);
     cudaFree(p->d_hout);
     cudaFree(p->d_yvv_P);
+    cudaFree(p->d_yvv_S);
     cudaFree(p->d_yvv_nd);
     cudaFree(p->d_yvv_mass);
     cudaFree(p->d_bwd);
@@ -108,7 +109,10 @@ YvvArgs yvv_args(bf_plan_s* p, const float* f, size_t fp, float* out, size_t op)
     a.c0 = p->c0;
     a.hdr = p->d_hdr;
     a.pairs = p->d_pairs;
+    a.G = p->yvv_G;
+    a.n_nd = p->yvv_G;
     a.P = p->d_yvv_P;
+    a.S = p->d_yvv_S;
     a.nd = p->d_yvv_nd;
     a.mass_y = p->d_yvv_mass;
     a.mass_x = p->d_yvv_mass + p->H;
@@ -338,10 +342,13 @@ bf_status bf_plan(int H, int W, double sigma_s, double sigma_r, double eps, cons
         // row-filtered planes [H][W][C] x 16 B, (num, den) [H][W], masses
         const int cap_terms = p->cap_pairs + 1;
         p->yvv_C = yvv_terms_per_pass(cap_terms);
+        p->yvv_G = 32 / p->yvv_C;
         p->yvv_passes = (cap_terms + p->yvv_C - 1) / p->yvv_C;
         const size_t npx = (size_t)H * W;
-        if (cudaMalloc(&p->d_yvv_P, npx * p->yvv_C * sizeof(float4)) != cudaSuccess ||
-            cudaMalloc(&p->d_yvv_nd, npx * sizeof(float2)) != cudaSuccess ||
+        const size_t nst = (size_t)H * ((W + 7) / 8) * 3 * 32;
+        if (cudaMalloc(&p->d_yvv_P, npx * 32 * sizeof(float4)) != cudaSuccess ||
+            cudaMalloc(&p->d_yvv_S, nst * sizeof(float4)) != cudaSuccess ||
+            cudaMalloc(&p->d_yvv_nd, npx * p->yvv_G * sizeof(float2)) != cudaSuccess ||
             cudaMalloc(&p->d_yvv_mass, sizeof(float) * ((size_t)H + W)) != cudaSuccess) {
             cudaGetLastError();
             free_plan(p);

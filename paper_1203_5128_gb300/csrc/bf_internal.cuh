@@ -34,9 +34,11 @@ struct bf_plan_s {
     float* d_bwd;            // backward scratch (out, den), allocated on first use
     int executed;
     cudaStream_t last;
-    int yvv_C, yvv_passes;   // recursive filter: terms per pass, passes
-    float4* d_yvv_P;         // recursive filter: row-filtered planes [H][W][C]
-    float2* d_yvv_nd;        // recursive filter: (num, den) per pixel
+    int yvv_C, yvv_passes;   // recursive filter: terms per pass (8 or 16), passes
+    int yvv_G;               // recursive filter: passes per launch (32 / C)
+    float4* d_yvv_P;         // recursive filter: row-filtered planes [H][W][32]
+    float4* d_yvv_S;         // recursive filter: row states [H][ceil(W/8)][3][32]
+    float2* d_yvv_nd;        // recursive filter: (num, den) partials [G][H][W]
     float* d_yvv_mass;       // recursive filter: mass_y[H] then mass_x[W]
     int timing;              // record events around the kernels
     int n_timed;
@@ -163,8 +165,11 @@ struct YvvArgs {
     float c0;
     const SetHdr* hdr;
     const Pair* pairs;
-    float4* P;              // [H][W][C] row-filtered planes
-    float2* nd;             // [H][W] (num, den)
+    int G;                  // pass groups per launch (G * C = 32 term columns)
+    int n_nd;               // (num, den) partials summed by the final kernel
+    float4* P;              // [H][W][G * C] row-filtered planes
+    float4* S;              // [H][ceil(W/8)][3][G * C] anti-causal row states
+    float2* nd;             // [G][H][W] (num, den) partials
     const float* mass_y;    // [H]
     const float* mass_x;    // [W]
     unsigned long long* n_guarded;

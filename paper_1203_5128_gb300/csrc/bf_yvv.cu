@@ -23,13 +23,12 @@
 // column pass never materialises its output: the down sweep adds the causal
 // part's contribution to num and den, the up sweep the anti-causal part's.
 //
-// Kernels, per pass of C terms (C in {8, 16, 32}; lanes = 32 / C lines x C
+// Kernels, per pass of C terms (C in {8, 16}; lanes = 32 / C lines x C
 // terms, term k = pass * C + lane % C, the zero frequency as term F with
 // omega = 0 and weight w0):
 //   k_yvv_rows  one warp per 32 / C rows: planes f'c, f's, c, s of each term
-//               (f' = f - value_range / 2), causal sweep writing the row-
-//               filtered planes to P[y][x][term][4], anti-causal sweep adding
-//               into them;
+//               (f' = f - value_range / 2), filtered along the row and written
+//               once to P[y][x][term][4] (two sweeps, see below);
 //   k_yvv_cols  one warp per 32 / C columns: down and up sweeps over P,
 //               demodulation with the term's cos, sin at the output pixel, a
 //               shuffle sum over the C terms, accumulated into (num, den);
@@ -37,7 +36,10 @@
 //               against 1e-6 times the filter of the image's indicator
 //               (separable: mass_y[y] mass_x[x]).
 // The number of passes follows the plan's cap on N (the host never reads
-// the device's N); passes beyond the set's terms return at once.
+// the device's N); passes beyond the set's terms return at once.  Each
+// launch runs G = 32 / C passes side by side (grid.y); pass group g keeps
+// its own (num, den) partial, and the final kernel adds the G partials in
+// group order, so the result does not depend on scheduling.
 #include <complex>
 #include <math.h>
 
@@ -99,11 +101,24 @@ __device__ __forceinline__ void planes_at(float v, float om_hi, float om_lo, flo
     in[3] = s;
 }
 
+// Row kernel in two sweeps so that each row-filtered sample is written once:
+//   A (right to left): the anti-causal states only; the state entering each
+//     chunk of kRowChunk samples from the right, v[x0 + kRowChunk], is saved
+//     (12 floats per term; the last chunk's is zero);
+//   B (left to right, chunk by chunk): the chunk's planes in registers, the
+//     anti-causal part from the saved state (right to left within the chunk),
+//     then the causal part, and y+ + y- stored once.
+constexpr int kRowChunk = 8;
+
 template <int C>
 __global__ void __launch_bounds__(32 * kWarpsPerCta)
-k_yvv_rows(YvvArgs a, int pass)
+k_yvv_rows(YvvArgs a, int launch)
 {
     constexpr int LPW = 32 / C;                    // lines per warp
+    constexpr int B = kRowChunk;
+    const int GC = a.G * C;                        // term columns per launch
+    const int g = blockIdx.y;                      // pass group of this CTA
+    const int pass = launch * a.G + g;
     const int lane = threadIdx.x & 31;
     const int slot = lane % C;
     const int y = (blockIdx.x * kWarpsPerCta + (threadIdx.x >> 5)) * LPW + lane / C;
@@ -115,51 +130,96 @@ k_yvv_rows(YvvArgs a, int pass)
     float om_hi, om_lo, Wk;
     term_of(a, hd, k, om_hi, om_lo, Wk);
     const YvvCoef cf = a.coef;
-    const float* frow = a.f + (size_t)y * a.f_pitch;
-    float4* P = a.P + (size_t)y * a.W * C + slot;  // (y, x, slot) at P[x * C]
     const int W = a.W;
+    const int nch = (W + B - 1) / B;
+    const int col = g * C + slot;
+    const float* frow = a.f + (size_t)y * a.f_pitch;
+    float4* P = a.P + (size_t)y * W * GC + col;            // (y, x, col) at P[x * GC]
+    float4* S = a.S + (size_t)y * nch * 3 * GC + col;      // (y, chunk, t, col) at S[(j * 3 + t) * GC]
 
+    // sweep A: anti-causal states at the chunk boundaries (the next chunk's
+    // f is fetched while this one is processed)
     Sec st[4];
 #pragma unroll
     for (int q = 0; q < 4; ++q) st[q] = Sec{0.f, 0.f, 0.f};
-    // causal sweep: write y+
-#pragma unroll 4
-    for (int x = 0; x < W; ++x) {
-        float in[4];
-        planes_at(__ldg(frow + x) - a.c0, om_hi, om_lo, in);
-        float o[4];
+    float fn[B];
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            sec_update(st[q], in[q], cf);
-            o[q] = sec_causal_out(st[q], cf);
-        }
-        if (act) P[(size_t)x * C] = make_float4(o[0], o[1], o[2], o[3]);
+    for (int i = 0; i < B; ++i) {
+        const int x = (nch - 1) * B + i;
+        fn[i] = x < W ? __ldg(frow + x) : 0.f;
     }
-    // anti-causal sweep: add y-, in chunks whose loads are issued together
+    for (int j = nch - 1; j >= 0; --j) {
+        if (act) {
+            float4* d = S + (size_t)j * 3 * GC;
+            d[0] = make_float4(st[0].a, st[0].re, st[0].im, st[1].a);
+            d[GC] = make_float4(st[1].re, st[1].im, st[2].a, st[2].re);
+            d[2 * GC] = make_float4(st[2].im, st[3].a, st[3].re, st[3].im);
+        }
+        const int x0 = j * B;
+        float fv[B];
 #pragma unroll
-    for (int q = 0; q < 4; ++q) st[q] = Sec{0.f, 0.f, 0.f};
-    constexpr int kChunk = 8;
-    for (int x1 = W - 1; x1 >= 0; x1 -= kChunk) {
-        float4 cur[kChunk];
-#pragma unroll
-        for (int j = 0; j < kChunk; ++j) {
-            const int x = x1 - j;
-            cur[j] = (act && x >= 0) ? P[(size_t)x * C] : make_float4(0.f, 0.f, 0.f, 0.f);
+        for (int i = 0; i < B; ++i) {
+            fv[i] = fn[i];
+            fn[i] = j > 0 ? __ldg(frow + x0 - B + i) : 0.f;
         }
 #pragma unroll
-        for (int j = 0; j < kChunk; ++j) {
-            const int x = x1 - j;
-            if (x < 0) break;
-            float4 t = cur[j];
-            t.x += sec_anti_out(st[0], cf);
-            t.y += sec_anti_out(st[1], cf);
-            t.z += sec_anti_out(st[2], cf);
-            t.w += sec_anti_out(st[3], cf);
-            if (act) P[(size_t)x * C] = t;
+        for (int i = B - 1; i >= 0; --i) {
+            if (x0 + i >= W) continue;
             float in[4];
-            planes_at(__ldg(frow + x) - a.c0, om_hi, om_lo, in);
+            planes_at(fv[i] - a.c0, om_hi, om_lo, in);
 #pragma unroll
             for (int q = 0; q < 4; ++q) sec_update(st[q], in[q], cf);
+        }
+    }
+    // sweep B: both parts per chunk, one store per sample (the next chunk's
+    // saved state and f are fetched while this one is processed)
+    Sec cs[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) cs[q] = Sec{0.f, 0.f, 0.f};
+    const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+    float4 n0 = act ? S[0] : z4, n1 = act ? S[GC] : z4, n2 = act ? S[2 * GC] : z4;
+#pragma unroll
+    for (int i = 0; i < B; ++i) fn[i] = i < W ? __ldg(frow + i) : 0.f;
+    for (int j = 0; j < nch; ++j) {
+        const int x0 = j * B;
+        Sec vs[4];
+        vs[0] = Sec{n0.x, n0.y, n0.z};
+        vs[1] = Sec{n0.w, n1.x, n1.y};
+        vs[2] = Sec{n1.z, n1.w, n2.x};
+        vs[3] = Sec{n2.y, n2.z, n2.w};
+        float fv[B];
+#pragma unroll
+        for (int i = 0; i < B; ++i) fv[i] = fn[i];
+        if (j + 1 < nch) {
+            const float4* d = S + (size_t)(j + 1) * 3 * GC;
+            n0 = act ? d[0] : z4;
+            n1 = act ? d[GC] : z4;
+            n2 = act ? d[2 * GC] : z4;
+#pragma unroll
+            for (int i = 0; i < B; ++i) fn[i] = x0 + B + i < W ? __ldg(frow + x0 + B + i) : 0.f;
+        }
+        float in[B][4], ym[B][4];
+#pragma unroll
+        for (int i = 0; i < B; ++i) planes_at(x0 + i < W ? fv[i] - a.c0 : 0.f, om_hi, om_lo, in[i]);
+#pragma unroll
+        for (int i = B - 1; i >= 0; --i) {
+            if (x0 + i >= W) continue;            // past the row: the state stays v[W] = 0
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                ym[i][q] = sec_anti_out(vs[q], cf);
+                sec_update(vs[q], in[i][q], cf);
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < B; ++i) {
+            if (x0 + i >= W) break;
+            float o[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                sec_update(cs[q], in[i][q], cf);
+                o[q] = sec_causal_out(cs[q], cf) + ym[i][q];
+            }
+            if (act) P[(size_t)(x0 + i) * GC] = make_float4(o[0], o[1], o[2], o[3]);
         }
     }
 }
@@ -174,19 +234,67 @@ __device__ __forceinline__ void reduce_terms(float& nu, float& de)
     }
 }
 
+// cp.async of 16, 8 or 4 bytes into shared memory, zero-filled when !pred
+// (nothing is read then; src must still be a valid address).
+__device__ __forceinline__ void cp_async16(void* dst, const void* src, bool pred)
+{
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;"
+                 ::"r"((uint32_t)__cvta_generic_to_shared(dst)), "l"(src), "r"(pred ? 16 : 0)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async8(void* dst, const void* src, bool pred)
+{
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;"
+                 ::"r"((uint32_t)__cvta_generic_to_shared(dst)), "l"(src), "r"(pred ? 8 : 0)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async4(void* dst, const void* src, bool pred)
+{
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;"
+                 ::"r"((uint32_t)__cvta_generic_to_shared(dst)), "l"(src), "r"(pred ? 4 : 0)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
+
+constexpr int kColChunk = 8;      // rows per chunk of the column sweeps
+
+// Shared memory of one warp of the column kernel: two stages of a chunk
+// (planes of 32 lanes, f and the (num, den) partials of the warp's columns).
+struct ColStage {
+    float4 P[kColChunk][32];
+    float f[4][kColChunk];
+    float2 nd[4][kColChunk];
+};
+
 template <int C>
 __global__ void __launch_bounds__(32 * kWarpsPerCta)
-k_yvv_cols(YvvArgs a, int pass)
+k_yvv_cols(YvvArgs a, int launch)
 {
     constexpr int LPW = 32 / C;
+    constexpr int B = kColChunk;
+    __shared__ ColStage stage_sm[kWarpsPerCta][2];
+    const int GC = a.G * C;
+    const int g = blockIdx.y;
+    const int pass = launch * a.G + g;
     const int lane = threadIdx.x & 31;
     const int slot = lane % C;
-    const int x = (blockIdx.x * kWarpsPerCta + (threadIdx.x >> 5)) * LPW + lane / C;
+    const int wl = threadIdx.x >> 5;
+    const int x0w = (blockIdx.x * kWarpsPerCta + wl) * LPW;     // first column of the warp
+    const int x = x0w + lane / C;
     const SetHdr hd = a.hdr[0];
     const int nterms = hd.F < 0 ? 0 : hd.F + hd.z;
-    if (pass * C >= nterms) return;               // uniform over the grid
+    if (pass * C >= nterms) {                     // uniform over the CTA
+        // a group without terms in the first launch still owns a partial
+        // that the final kernel sums: zero it
+        if (launch == 0 && x < a.W && slot == 0) {
+            float2* ND = a.nd + (size_t)g * a.H * a.W + x;
+            for (int y = 0; y < a.H; ++y) ND[(size_t)y * a.W] = make_float2(0.f, 0.f);
+        }
+        return;
+    }
     // lanes past the last column stay for the shuffles
-    if ((blockIdx.x * kWarpsPerCta + (threadIdx.x >> 5)) * LPW >= a.W) return;  // whole warp out
+    if (x0w >= a.W) return;                       // whole warp out
     const bool xin = x < a.W;
     const int k = pass * C + slot;
     const bool act = xin && k < nterms;
@@ -196,81 +304,118 @@ k_yvv_cols(YvvArgs a, int pass)
     const YvvCoef cf = a.coef;
     const int H = a.H, W = a.W;
     const int xc = xin ? x : 0;
-    const float4* P = a.P + (size_t)xc * C + slot;   // (y, x, slot) at P[y * W * C]
-    const size_t pstride = (size_t)W * C;
-    const float* fcol = a.f + xc;
-    float2* ND = a.nd + xc;
+    const float4* P = a.P + (size_t)xc * GC + g * C + slot;   // (y, x, col) at P[y * W * GC]
+    const size_t pstride = (size_t)W * GC;
+    float2* ND = a.nd + (size_t)g * H * W + xc;     // this group's partial (num, den)
     const bool writer = xin && slot == 0;
-    const bool first = pass == 0;
-    constexpr int kChunk = 8;
+    const bool first = launch == 0;
+    ColStage* stg = stage_sm[wl];
+    // the (row j, column sub) of f and (num, den) this lane fetches for a chunk
+    const int fj = lane % B, fsub = lane / B;
+    const int fx = x0w + fsub;
+    const bool fcol_ok = fsub < LPW && fx < W;
+    const float* fsrc = a.f + (fcol_ok ? fx : 0);
+    float2* ndsrc = a.nd + (size_t)g * H * W + (fcol_ok ? fx : 0);
+
+    // chunk c of a sweep covers rows y(c, j) = down ? cB + j : H - 1 - (cB + j)
+    auto fetch = [&](int c, bool down, bool need_nd) {
+        ColStage& st = stg[c & 1];
+#pragma unroll
+        for (int jj = 0; jj < B; ++jj) {
+            const int r = c * B + jj;
+            const int y = down ? r : H - 1 - r;
+            const bool ok = act && r < H;
+            cp_async16(&st.P[jj][lane], ok ? (const void*)(P + (size_t)y * pstride) : (const void*)a.P, ok);
+        }
+        {
+            const int r = c * B + fj;
+            const int y = down ? r : H - 1 - r;
+            const bool ok = fcol_ok && r < H;
+            if (fsub < 4) {
+                cp_async4(&st.f[fsub][fj], ok ? (const void*)(fsrc + (size_t)y * a.f_pitch) : (const void*)a.f, ok);
+                cp_async8(&st.nd[fsub][fj], (ok && need_nd) ? (const void*)(ndsrc + (size_t)y * W) : (const void*)a.nd,
+                          ok && need_nd);
+            }
+        }
+        cp_async_commit();
+    };
+    const int nchunk = (H + B - 1) / B;
+    const int sub = lane / C;
 
     Sec st[4];
 #pragma unroll
     for (int q = 0; q < 4; ++q) st[q] = Sec{0.f, 0.f, 0.f};
     // down sweep: causal part
-    for (int y0 = 0; y0 < H; y0 += kChunk) {
-        float4 cur[kChunk];
+    fetch(0, true, !first);
+    for (int c = 0; c < nchunk; ++c) {
+        if (c + 1 < nchunk) fetch(c + 1, true, !first);
+        else cp_async_commit();                   // empty group keeps the count
+        cp_async_wait1();
+        __syncwarp();
+        const ColStage& sc = stg[c & 1];
+        float2 acc[B];
 #pragma unroll
-        for (int j = 0; j < kChunk; ++j) {
-            const int y = y0 + j;
-            cur[j] = (act && y < H) ? P[(size_t)y * pstride] : make_float4(0.f, 0.f, 0.f, 0.f);
-        }
-#pragma unroll
-        for (int j = 0; j < kChunk; ++j) {
-            const int y = y0 + j;
-            if (y >= H) break;
-            sec_update(st[0], cur[j].x, cf);
-            sec_update(st[1], cur[j].y, cf);
-            sec_update(st[2], cur[j].z, cf);
-            sec_update(st[3], cur[j].w, cf);
-            float c, s;
-            fir32::phase_cs(__ldg(fcol + (size_t)y * a.f_pitch) - a.c0, om_hi, om_lo, c, s);
-            float nu = Wk * fmaf(c, sec_causal_out(st[0], cf), s * sec_causal_out(st[1], cf));
-            float de = Wk * fmaf(c, sec_causal_out(st[2], cf), s * sec_causal_out(st[3], cf));
+        for (int jj = 0; jj < B; ++jj) {
+            const float4 cur = sc.P[jj][lane];
+            sec_update(st[0], cur.x, cf);
+            sec_update(st[1], cur.y, cf);
+            sec_update(st[2], cur.z, cf);
+            sec_update(st[3], cur.w, cf);
+            float cc, ss;
+            fir32::phase_cs(sc.f[sub][jj] - a.c0, om_hi, om_lo, cc, ss);
+            float nu = Wk * fmaf(cc, sec_causal_out(st[0], cf), ss * sec_causal_out(st[1], cf));
+            float de = Wk * fmaf(cc, sec_causal_out(st[2], cf), ss * sec_causal_out(st[3], cf));
             reduce_terms<C>(nu, de);
-            if (writer) {
-                float2* d = ND + (size_t)y * W;
-                if (first) {
-                    *d = make_float2(nu, de);
-                } else {
-                    float2 t = *d;
-                    *d = make_float2(t.x + nu, t.y + de);
-                }
-            }
+            acc[jj] = first ? make_float2(nu, de)
+                            : make_float2(sc.nd[sub][jj].x + nu, sc.nd[sub][jj].y + de);
         }
+        if (writer) {
+#pragma unroll
+            for (int jj = 0; jj < B; ++jj)
+                if (c * B + jj < H) ND[(size_t)(c * B + jj) * W] = acc[jj];
+        }
+        __syncwarp();                             // stage c & 1 is refilled next
     }
-    // up sweep: anti-causal part
+    // up sweep: anti-causal part (rows H-1 down to 0); its (num, den) reads
+    // see the down sweep's stores (same thread wrote them, or the writer of
+    // the same column before this warp-wide point)
+    __syncwarp();
 #pragma unroll
     for (int q = 0; q < 4; ++q) st[q] = Sec{0.f, 0.f, 0.f};
-    for (int y1 = H - 1; y1 >= 0; y1 -= kChunk) {
-        float4 cur[kChunk];
+    fetch(0, false, true);
+    for (int c = 0; c < nchunk; ++c) {
+        if (c + 1 < nchunk) fetch(c + 1, false, true);
+        else cp_async_commit();
+        cp_async_wait1();
+        __syncwarp();
+        const ColStage& sc = stg[c & 1];
+        float2 acc[B];
 #pragma unroll
-        for (int j = 0; j < kChunk; ++j) {
-            const int y = y1 - j;
-            cur[j] = (act && y >= 0) ? P[(size_t)y * pstride] : make_float4(0.f, 0.f, 0.f, 0.f);
-        }
-#pragma unroll
-        for (int j = 0; j < kChunk; ++j) {
-            const int y = y1 - j;
-            if (y < 0) break;
+        for (int jj = 0; jj < B; ++jj) {
+            const float4 cur = sc.P[jj][lane];
             const float oA = sec_anti_out(st[0], cf), oB = sec_anti_out(st[1], cf);
             const float oC = sec_anti_out(st[2], cf), oD = sec_anti_out(st[3], cf);
-            sec_update(st[0], cur[j].x, cf);
-            sec_update(st[1], cur[j].y, cf);
-            sec_update(st[2], cur[j].z, cf);
-            sec_update(st[3], cur[j].w, cf);
-            float c, s;
-            fir32::phase_cs(__ldg(fcol + (size_t)y * a.f_pitch) - a.c0, om_hi, om_lo, c, s);
-            float nu = Wk * fmaf(c, oA, s * oB);
-            float de = Wk * fmaf(c, oC, s * oD);
+            sec_update(st[0], cur.x, cf);
+            sec_update(st[1], cur.y, cf);
+            sec_update(st[2], cur.z, cf);
+            sec_update(st[3], cur.w, cf);
+            float cc, ss;
+            fir32::phase_cs(sc.f[sub][jj] - a.c0, om_hi, om_lo, cc, ss);
+            float nu = Wk * fmaf(cc, oA, ss * oB);
+            float de = Wk * fmaf(cc, oC, ss * oD);
             reduce_terms<C>(nu, de);
-            if (writer) {
-                float2* d = ND + (size_t)y * W;
-                const float2 t = *d;
-                *d = make_float2(t.x + nu, t.y + de);
+            acc[jj] = make_float2(sc.nd[sub][jj].x + nu, sc.nd[sub][jj].y + de);
+        }
+        if (writer) {
+#pragma unroll
+            for (int jj = 0; jj < B; ++jj) {
+                const int y = H - 1 - (c * B + jj);
+                if (y >= 0) ND[(size_t)y * W] = acc[jj];
             }
         }
+        __syncwarp();
     }
+    asm volatile("cp.async.wait_group 0;" ::: "memory");
 }
 
 __global__ void k_yvv_final(YvvArgs a)
@@ -284,7 +429,14 @@ __global__ void k_yvv_final(YvvArgs a)
         if (hd.F < 0) {
             v = fv;                                  // order above the cap: pass through
         } else {
-            const float2 nd = a.nd[(size_t)y * a.W + x];
+            // the groups' partial sums, in group order
+            const size_t hw = (size_t)a.H * a.W;
+            float2 nd = make_float2(0.f, 0.f);
+            for (int g = 0; g < a.n_nd; ++g) {
+                const float2 t = a.nd[g * hw + (size_t)y * a.W + x];
+                nd.x += t.x;
+                nd.y += t.y;
+            }
             if (nd.y > kGuard * (a.mass_y[y] * a.mass_x[x])) {
                 v = __fdiv_rn(nd.x, nd.y) + a.c0;
             } else {
@@ -393,32 +545,31 @@ void yvv_line_mass(double sigma, int n, float* mass)
     }
 }
 
-int yvv_terms_per_pass(int n_terms_cap)
-{
-    if (n_terms_cap <= 8) return 8;
-    if (n_terms_cap <= 16) return 16;
-    return 32;
-}
+// 8 terms per pass for small orders, else 16: at most 15 idle lanes in the
+// last pass whatever the device's N (32 would waste up to 31).  32 / C
+// passes run side by side in one launch (grid.y), so that every launch has
+// one warp per line: the line recursions are sequential and need the warps.
+int yvv_terms_per_pass(int n_terms_cap) { return n_terms_cap <= 8 ? 8 : 16; }
 
-cudaError_t launch_yvv(const YvvArgs& a, int C, int n_passes, cudaStream_t s)
+cudaError_t launch_yvv(const YvvArgs& a0, int C, int n_passes, cudaStream_t s)
 {
+    YvvArgs a = a0;
+    const int G = a.G;
+    const int n_launch = (n_passes + G - 1) / G;
+    a.n_nd = G;                                   // every group's partial is written at launch 0
     const int lines_per_cta = kWarpsPerCta * (32 / C);
     const dim3 block(32 * kWarpsPerCta);
-    const dim3 grow((a.H + lines_per_cta - 1) / lines_per_cta);
-    const dim3 gcol((a.W + lines_per_cta - 1) / lines_per_cta);
-    for (int pass = 0; pass < n_passes; ++pass) {
+    const dim3 grow((a.H + lines_per_cta - 1) / lines_per_cta, G);
+    const dim3 gcol((a.W + lines_per_cta - 1) / lines_per_cta, G);
+    for (int l = 0; l < n_launch; ++l) {
         switch (C) {
         case 8:
-            k_yvv_rows<8><<<grow, block, 0, s>>>(a, pass);
-            k_yvv_cols<8><<<gcol, block, 0, s>>>(a, pass);
+            k_yvv_rows<8><<<grow, block, 0, s>>>(a, l);
+            k_yvv_cols<8><<<gcol, block, 0, s>>>(a, l);
             break;
         case 16:
-            k_yvv_rows<16><<<grow, block, 0, s>>>(a, pass);
-            k_yvv_cols<16><<<gcol, block, 0, s>>>(a, pass);
-            break;
-        case 32:
-            k_yvv_rows<32><<<grow, block, 0, s>>>(a, pass);
-            k_yvv_cols<32><<<gcol, block, 0, s>>>(a, pass);
+            k_yvv_rows<16><<<grow, block, 0, s>>>(a, l);
+            k_yvv_cols<16><<<gcol, block, 0, s>>>(a, l);
             break;
         default:
             return cudaErrorInvalidValue;

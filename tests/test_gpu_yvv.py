@@ -2,8 +2,8 @@
 oracle's recursive mode.
 
 The FP32 bar is the forward's: max-abs 1e-3 gray levels on 8-bit images.
-Sizes are ragged, and cover each of the 8-, 16- and 32-terms-per-pass kernel
-widths, several passes, and both FIXED and GLOBAL T.  At the full
+Sizes are ragged, and cover both the 8- and 16-terms-per-pass kernel widths,
+several passes, single rows and columns, and both FIXED and GLOBAL T.  At the full
 4096 x 4096 size the oracle runs on crops: the recursion's response falls
 below 3e-14 of its peak within 200 pixels at sigma_s = 8, so the outputs
 200 pixels or more inside a crop's interior edges equal those of the whole
@@ -44,7 +44,7 @@ def run(bf, f, sigma_s, sigma_r, eps, **opts):
 
 
 # (H, W, sigma_s, sigma_r, eps, t_mode, rule): sigma_r 60 -> 8 terms per
-# pass, 40 -> 16, 15 -> 32 x 2 passes, 10 -> 32 x 5 passes (caps on N)
+# pass, 40 -> 16, 15 -> 16 x 4 passes, 10 -> 16 x 9 passes (caps on N)
 CASES = [
     (37, 53, 0.8, 60.0, 0.01, "global", "alg2"),
     (96, 80, 2.0, 40.0, 0.0, "global", "trunc"),
