@@ -165,6 +165,15 @@ __device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity, long l
     }
 }
 
+// mbar_wait taken by a whole warp: true only when every lane's wait
+// succeeded, so that the warp leaves its loop as one and the warp-wide
+// (.sync.aligned) TMEM instructions after the wait always run with all lanes.
+__device__ __forceinline__ bool mbar_wait_warp(uint32_t mbar, uint32_t parity, long long limit,
+                                               volatile int* stop)
+{
+    return __all_sync(0xffffffffu, mbar_wait(mbar, parity, limit, stop));
+}
+
 // TMEM loads of this thread's lane; the wait is in the same statement, so no
 // use of the outputs can be scheduled before it.
 __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v)
@@ -467,7 +476,7 @@ __global__ void __launch_bounds__(NT, 1) k_fwd_tc(FwdArgs a, long long spin_limi
                 Wk = p.W;
             }
             // D1 ready: convert my row of each plane to 16 bits (A2, K-major)
-            if (!mbar_wait(bar(kBarC1), k & 1, spin_limit, stop)) { ok = false; break; }
+            if (!mbar_wait_warp(bar(kBarC1), k & 1, spin_limit, stop)) { ok = false; break; }
             fence_after();
             unsigned char* a2row = smem + G.offA2 + (m / 8) * G.sboA2 + (m % 8) * 16;
 #pragma unroll
@@ -490,7 +499,7 @@ __global__ void __launch_bounds__(NT, 1) k_fwd_tc(FwdArgs a, long long spin_limi
             fence_before();
             mbar_arrive(bar(kBarA2Full));
             // D2 ready: demodulate (eqs. (f1), (f2)); TMEM column n is x = 31 - n
-            if (!mbar_wait(bar(kBarC2), k & 1, spin_limit, stop)) { ok = false; break; }
+            if (!mbar_wait_warp(bar(kBarC2), k & 1, spin_limit, stop)) { ok = false; break; }
             fence_after();
 #pragma unroll
             for (int cb = 0; cb < TW / 8; ++cb) {
