@@ -150,8 +150,10 @@ bf_status bf_backward(bf_plan_t plan, const float *f_dev, const float *grad_out_
 
 /* Algorithm 2 on n images, each with its own plan (sizes, sigmas, eps),
  * in one persistent launch fed by a tile work queue.  Images are contiguous
- * (pitch = W of their plan).  All plans must share t_mode, plane_dtype and
- * filter.  The results equal n bf_execute calls bit for bit. */
+ * (pitch = W of their plan).  Each image needs a plan of its own (a plan
+ * named twice is BF_ERR_INVALID_ARG: its workspace serves one image at a
+ * time).  FP32 FIR plans only (else BF_ERR_NOT_SUPPORTED).  The results
+ * equal n bf_execute calls bit for bit. */
 bf_status bf_execute_batch(int n, const bf_plan_t *plans, const float *const *f_dev,
                            float *const *out_dev, void *stream);
 

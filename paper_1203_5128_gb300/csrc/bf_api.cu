@@ -63,6 +63,8 @@ void free_plan(bf_plan_s* p)
     cudaFree(p->d_yvv_S);
     cudaFree(p->d_yvv_nd);
     cudaFree(p->d_yvv_mass);
+    cudaFree(p->d_sep_P);
+    cudaFree(p->d_sep_nd);
     cudaFree(p->d_bwd);
     if (p->ev) {
         for (int i = 0; i < 4 * kMaxTimed; ++i)
@@ -142,6 +144,11 @@ FwdArgs forward_args(bf_plan_s* p, const float* f, size_t fp, float* out, size_t
     a.den_out = nullptr;
     a.den_pitch = 0;
     a.h_taps = p->h_taps;
+    a.sep_P = p->d_sep_P;
+    a.sep_nd = p->d_sep_nd;
+    a.sep_nk = p->sep_nk;
+    a.sep_Wp = p->sep_Wp;
+    a.sep_cap_terms = p->cap_pairs + 1;
     return a;
 }
 
@@ -255,8 +262,13 @@ bf_status bf_plan(int H, int W, double sigma_s, double sigma_r, double eps, cons
     const int R = (int)Rr;
     if (o.t_mode != BF_T_FIXED && R > range_max_radius()) return BF_ERR_NOT_SUPPORTED;
     int th = 0, tw = 0;
+    const bool use_sep = o.filter == BF_FILTER_FIR && o.plane_dtype == BF_PLANES_FP32 &&
+                         o.t_mode != BF_T_TILE && !fwd32t_ok(R, 0) && sep32_ok(R);
     if (o.filter == BF_FILTER_YVV) {
         th = tw = 1;                      // whole lines, no output tiles
+    } else if (use_sep) {
+        th = 128;                         // column-pass tile of the two-pass FIR
+        tw = 32;
     } else if (o.plane_dtype == BF_PLANES_FP32) {
         fwd32_tile(R, &th, &tw);
         if (fwd32t_ok(R, o.t_mode == BF_T_TILE ? o.t_tile : 0)) {
@@ -336,6 +348,24 @@ bf_status bf_plan(int H, int W, double sigma_s, double sigma_r, double eps, cons
     if (o.t_mode == BF_T_FIXED) {
         float T = o.t_fixed;
         ok &= cudaMemcpy(p->d_T, &T, sizeof(float), cudaMemcpyHostToDevice) == cudaSuccess;
+    }
+    if (ok && use_sep) {
+        // row-filtered planes of sep_nk terms at a time (up to 2 GiB), and
+        // the (num, den) partial carried between chunks of terms
+        p->sep_Wp = sep32_width(W);
+        const size_t per_term = (size_t)4 * H * p->sep_Wp * sizeof(float);
+        const size_t budget = (size_t)2 << 30;
+        const int cap_terms = p->cap_pairs + 1;
+        size_t nk = budget / per_term;
+        if (nk < 1) nk = 1;
+        if (nk > (size_t)cap_terms) nk = cap_terms;
+        p->sep_nk = (int)nk;
+        if (cudaMalloc(&p->d_sep_P, nk * per_term) != cudaSuccess ||
+            cudaMalloc(&p->d_sep_nd, (size_t)H * W * sizeof(float2)) != cudaSuccess) {
+            cudaGetLastError();
+            free_plan(p);
+            return BF_ERR_ALLOC;
+        }
     }
     if (ok && o.filter == BF_FILTER_YVV) {
         // terms per pass from the cap (pairs + zero frequency); workspace:

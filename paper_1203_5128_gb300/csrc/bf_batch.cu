@@ -8,6 +8,12 @@
 //      items from an atomic queue head, costliest first (longest-processing-
 //      time order), each item run by the same tile body as bf_execute.
 //
+// Images whose radius is beyond the fused tall tile (and whose plan holds the
+// two-pass workspace) run the two-pass FIR instead, and images large enough
+// to fill a quarter of the GPU with the fused tall tile run that kernel: both
+// as their own launches, after the batched K1 and K2, on side streams of the
+// capture that the graph runs concurrently with the queue.
+//
 // The FP32 forward's arithmetic per output does not depend on the tile shape
 // (every FIR sums its nonzero taps in increasing order; zero-padded taps add
 // exact zeros), so the batch output equals bf_execute's bit for bit whatever
@@ -127,10 +133,27 @@ std::pair<int, int> autotune_tile(bf_plan_s* p, const float* f, float* out, cuda
 bf_status build_state(int n, const bf_plan_t* plans, const float* const* f, float* const* out,
                       BatchState* st, cudaStream_t user)
 {
-    // ---- tile shape per image (autotuned per R, remembered per process)
+    // ---- images whose radius takes the two-pass FIR run it (its own launches
+    // in the graph, after the batched K1 and K2); the others share the queue
+    // (two_pass), and so do images whose fused tall tile covers at least a
+    // quarter wave of the GPU (a launch of their own fills it as well as the
+    // queue would, with the faster tall kernel)
+    int sms0 = 0;
+    if (cudaDeviceGetAttribute(&sms0, cudaDevAttrMultiProcessorCount, st->device) != cudaSuccess)
+        return BF_ERR_CUDA;
+    std::vector<char> two_pass(n, 0);
+    for (int i = 0; i < n; ++i) {
+        bf_plan_s* p = plans[i];
+        const int set_tile = p->opt.t_mode == BF_T_TILE ? p->set_tile : 0;
+        const long long tall_ctas = (long long)((p->H + 127) / 128) * ((p->W + 31) / 32);
+        two_pass[i] = (p->d_sep_P && set_tile == 0 && !fwd32t_ok(p->R, 0) && sep32_ok(p->R)) ||
+                      (fwd32t_ok(p->R, set_tile) && 4 * tall_ctas >= sms0);
+    }
+    // ---- tile shape per queued image (autotuned per R, remembered per process)
     std::vector<std::pair<int, int>> shape(n);
     for (int i = 0; i < n; ++i) {
         bf_plan_s* p = plans[i];
+        if (two_pass[i]) continue;
         auto it = g_tile_choice.find(p->R);
         if (it == g_tile_choice.end()) {
             std::pair<int, int> c = autotune_tile(p, f[i], out[i], user);
@@ -187,6 +210,7 @@ bf_status build_state(int n, const bf_plan_t* plans, const float* const* f, floa
             bset.push_back(sI);
         }
         fimg[i] = forward_args(p, f[i], p->W, out[i], p->W);
+        if (two_pass[i]) continue;
         int c = -1;
         for (size_t k = 0; k < classes.size(); ++k)
             if (classes[k] == shape[i]) c = (int)k;
@@ -264,9 +288,30 @@ bf_status build_state(int n, const bf_plan_t* plans, const float* const* f, floa
         ctas[c] = std::min<int>(sms * per, (int)items[c].size());
     }
 
-    // ---- capture
+    // ---- capture: the per-image launches go to kSide side streams forked
+    // from the capture stream after K2 and joined before its end, so that
+    // the graph runs them concurrently with each other and with the queue
+    constexpr int kSide = 8;
     cudaStream_t cs;
     if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) return BF_ERR_CUDA;
+    cudaStream_t side[kSide] = {};
+    cudaEvent_t fork_ev = nullptr, join_ev[kSide] = {};
+    bool made = cudaEventCreateWithFlags(&fork_ev, cudaEventDisableTiming) == cudaSuccess;
+    for (int k = 0; k < kSide && made; ++k)
+        made = cudaStreamCreateWithFlags(&side[k], cudaStreamNonBlocking) == cudaSuccess &&
+               cudaEventCreateWithFlags(&join_ev[k], cudaEventDisableTiming) == cudaSuccess;
+    auto release = [&]() {
+        for (int k = 0; k < kSide; ++k) {
+            if (side[k]) cudaStreamDestroy(side[k]);
+            if (join_ev[k]) cudaEventDestroy(join_ev[k]);
+        }
+        if (fork_ev) cudaEventDestroy(fork_ev);
+    };
+    if (!made) {
+        release();
+        cudaStreamDestroy(cs);
+        return BF_ERR_CUDA;
+    }
     cudaGraph_t graph = nullptr;
     cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeRelaxed);
     if (e == cudaSuccess) {
@@ -281,17 +326,34 @@ bf_status build_state(int n, const bf_plan_t* plans, const float* const* f, floa
             e = launch_params_batch(reinterpret_cast<const ParamsArgs*>(d + oP),
                                     reinterpret_cast<const int*>(d + oBI),
                                     reinterpret_cast<const int*>(d + oBS), (int)bimg.size(), cs);
+        if (e == cudaSuccess) e = cudaEventRecord(fork_ev, cs);
+        for (int k = 0; k < kSide && e == cudaSuccess; ++k) e = cudaStreamWaitEvent(side[k], fork_ev, 0);
+        // own launches, largest images first, round-robin over the side streams
+        std::vector<int> own;
+        for (int i = 0; i < n; ++i)
+            if (two_pass[i]) own.push_back(i);
+        std::stable_sort(own.begin(), own.end(), [&](int x, int y) {
+            return (long long)plans[x]->H * plans[x]->W * plans[x]->cap_pairs >
+                   (long long)plans[y]->H * plans[y]->W * plans[y]->cap_pairs;
+        });
+        for (size_t j = 0; j < own.size() && e == cudaSuccess; ++j)
+            e = launch_fwd32(fimg[own[j]], side[j % kSide]);
         for (size_t c = 0; c < classes.size() && e == cudaSuccess; ++c)
             e = launch_fwd32_persistent(classes[c].first, classes[c].second, cmaxR[c],
                                         reinterpret_cast<const FwdArgs*>(d + oF),
                                         reinterpret_cast<const int4*>(d + oI[c]),
                                         (int)items[c].size(),
                                         reinterpret_cast<unsigned*>(d + oH) + c, ctas[c], cs);
+        for (int k = 0; k < kSide && e == cudaSuccess; ++k) {
+            e = cudaEventRecord(join_ev[k], side[k]);
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(cs, join_ev[k], 0);
+        }
         cudaError_t e2 = cudaStreamEndCapture(cs, &graph);
         if (e == cudaSuccess) e = e2;
     }
     if (e == cudaSuccess) e = cudaGraphInstantiate(&st->exec, graph, 0);
     if (graph) cudaGraphDestroy(graph);
+    release();
     cudaStreamDestroy(cs);
     return e == cudaSuccess ? BF_OK : BF_ERR_CUDA;
 }
@@ -355,6 +417,13 @@ extern "C" bf_status bf_execute_batch(int n, const bf_plan_t* plans, const float
         if (plans[i]->device != plans[0]->device) return BF_ERR_INVALID_ARG;
         if (plans[i]->opt.plane_dtype != BF_PLANES_FP32 || plans[i]->opt.filter != BF_FILTER_FIR)
             return BF_ERR_NOT_SUPPORTED;
+    }
+    // a plan's workspace (T words, parameter sets, two-pass buffers) serves
+    // one image at a time: each image needs a plan of its own
+    {
+        std::vector<const void*> ps(plans, plans + n);
+        std::sort(ps.begin(), ps.end());
+        if (std::adjacent_find(ps.begin(), ps.end()) != ps.end()) return BF_ERR_INVALID_ARG;
     }
     cudaStream_t s = (cudaStream_t)stream;
     if (cudaSetDevice(plans[0]->device) != cudaSuccess) return BF_ERR_CUDA;

@@ -416,6 +416,29 @@ bool fwd32t_ok(int R, int set_tile)
 
 cudaError_t launch_fwd32(const FwdArgs& a, cudaStream_t s)
 {
+    if (a.sep_P && a.set_tile == 0 && !fwd32t_ok(a.R, 0) && sep32_ok(a.R)) {
+        SepArgs sa;
+        sa.f = a.f;
+        sa.f_pitch = a.f_pitch;
+        sa.out = a.out;
+        sa.out_pitch = a.out_pitch;
+        sa.H = a.H;
+        sa.W = a.W;
+        sa.Wp = a.sep_Wp;
+        sa.R = a.R;
+        sa.c0 = a.c0;
+        sa.hdr = a.hdr;
+        sa.pairs = a.pairs;
+        sa.taps = a.taps;
+        sa.h_taps = a.h_taps;
+        sa.P = a.sep_P;
+        sa.nd = a.sep_nd;
+        sa.nk = a.sep_nk;
+        sa.n_guarded = a.n_guarded;
+        sa.den_out = a.den_out;
+        sa.den_pitch = a.den_pitch;
+        return launch_sep32(sa, a.sep_cap_terms, s);
+    }
     if (a.h_taps && fwd32t_ok(a.R, a.set_tile)) {
         const fir32::Geo2 G(a.R, 128, 32);
         fir32::Taps tp;

@@ -40,6 +40,9 @@ struct bf_plan_s {
     float4* d_yvv_S;         // recursive filter: row states [H][ceil(W/8)][3][32]
     float2* d_yvv_nd;        // recursive filter: (num, den) partials [G][H][W]
     float* d_yvv_mass;       // recursive filter: mass_y[H] then mass_x[W]
+    float* d_sep_P;          // two-pass FIR: row-filtered planes of sep_nk terms
+    float2* d_sep_nd;        // two-pass FIR: (num, den) partial
+    int sep_nk, sep_Wp;
     int timing;              // record events around the kernels
     int n_timed;
     cudaEvent_t* ev;         // 4 per recorded execute
@@ -120,7 +123,34 @@ struct FwdArgs {
     float* den_out;         // optional: den per pixel (backward)
     size_t den_pitch;
     const float* h_taps;    // host copy of taps (null: shared-memory taps only)
+    // two-pass workspace for radii beyond the fused tall tile (null: none)
+    float* sep_P;           // [nk][4][H][sep_Wp] row-filtered planes
+    float2* sep_nd;         // [H][W] (num, den) partial
+    int sep_nk, sep_Wp, sep_cap_terms;
 };
+// K3-sep (FP32 FIR in two passes through HBM, R > 24, one parameter set).
+struct SepArgs {
+    const float* f;
+    size_t f_pitch;
+    float* out;
+    size_t out_pitch;
+    int H, W, Wp, R;        // Wp: row stride of P (multiple of 128)
+    float c0;
+    const SetHdr* hdr;
+    const Pair* pairs;
+    const float* taps;      // device taps (guard mass)
+    const float* h_taps;    // host taps (kernel parameter)
+    float* P;               // [nk][4][H][Wp]
+    float2* nd;             // [H][W]
+    int nk;                 // terms per chunk
+    unsigned long long* n_guarded;
+    float* den_out;
+    size_t den_pitch;
+};
+bool sep32_ok(int R);
+int sep32_width(int W);
+cudaError_t launch_sep32(const SepArgs& a, int n_terms_cap, cudaStream_t s);
+
 // Output tile of the FP32 kernel for a given R (0 if unsupported).
 void fwd32_tile(int R, int* th, int* tw);
 size_t fwd32_smem(int R, int th, int tw);

@@ -163,6 +163,9 @@ extern "C" bf_status bf_execute_noalloc(const float* f, size_t f_pitch, float* o
     for (int k = -R; k <= R; ++k)
         h_taps[k + R] = (float)exp(-(double)k * (double)k / (2.0 * sigma_s * sigma_s));
     fa.h_taps = h_taps;
+    fa.sep_P = nullptr;             // no workspace: the fused tiles serve every radius
+    fa.sep_nd = nullptr;
+    fa.sep_nk = fa.sep_Wp = fa.sep_cap_terms = 0;
     if (launch_fwd32(fa, st) != cudaSuccess) return BF_ERR_CUDA;
     return BF_OK;
 }

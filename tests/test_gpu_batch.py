@@ -98,3 +98,12 @@ def test_batch_rejects_reduced_precision(bf):
     f = torch.zeros((64, 64), device="cuda")
     with pytest.raises(bf.BfError):
         bf.bf_execute_batch([p], [f])
+
+
+def test_batch_rejects_a_plan_named_twice(bf):
+    import torch
+    p = bf.bf_plan(64, 64, 2.0, 20.0, 0.01)
+    f = torch.zeros((64, 64), device="cuda")
+    with pytest.raises(bf.BfError):
+        bf.bf_execute_batch([p, p], [f, f.clone()])
+    p.close()
