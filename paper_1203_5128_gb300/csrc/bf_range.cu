@@ -10,7 +10,8 @@
 // to the columns of the row result.
 //
 // GB300 form: one CTA per 64 x 64 block of outputs.  The block plus its R
-// halo is staged in shared memory once (coalesced).  Each (line, partition)
+// halo is staged in shared memory once (coalesced, by cp.async so that a
+// thread's copies are all in flight together).  Each (line, partition)
 // is one thread running the partition's suffix (then prefix) maxima
 // sequentially -- 3 max operations per point as in the Appendix -- with the
 // 32 lanes of a warp on 32 consecutive lines, so every step is one
@@ -102,22 +103,34 @@ __device__ __forceinline__ void range_body(const float* __restrict__ f, size_t p
     const int Ls = L + 1;           // odd row stride: lanes on consecutive rows hit distinct banks
     const int Wn = 2 * R + 1;       // window = partition length
     const int P = (L + Wn - 1) / Wn;
-    float* reg = sm;                // L x Ls, -inf outside the image
-    float* rmax = reg + L * Ls;     // L x kTp: row pass result
+    // reg (L x Ls, -inf outside the image) is dead after the row pass, so the
+    // column pass result (kT x kTp per filter) is written over it
+    const int reg_floats = max(L * Ls, (kMin ? 2 : 1) * kT * kTp);
+    float* reg = sm;
+    float* rmax = reg + reg_floats;  // L x kTp: row pass result
     float* rmin = rmax + L * kTp;
-    float* cmax = rmin + (kMin ? L * kTp : 0);   // kT x kTp: column pass result
+    float* cmax = reg;               // kT x kTp: column pass result
     float* cmin = cmax + kT * kTp;
 
+    // stage the block + halo: in-image entries by cp.async (all of a thread's
+    // copies in flight at once), -inf elsewhere
     const int gy0 = by - R, gx0 = bx - R;
     for (int r = threadIdx.x / 32; r < L; r += kThreads / 32) {
         const int gy = gy0 + r;
         const bool rin = gy >= 0 && gy < H;
         for (int c = threadIdx.x % 32; c < L; c += 32) {
             const int gx = gx0 + c;
-            reg[r * Ls + c] = (rin && gx >= 0 && gx < W) ? __ldg(f + (size_t)gy * pitch + gx)
-                                                         : -INFINITY;
+            float* dst = reg + r * Ls + c;
+            if (rin && gx >= 0 && gx < W)
+                asm volatile("cp.async.ca.shared.global [%0], [%1], 4;"
+                             ::"r"((uint32_t)__cvta_generic_to_shared(dst)),
+                               "l"(f + (size_t)gy * pitch + gx)
+                             : "memory");
+            else
+                *dst = -INFINITY;
         }
     }
+    asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
     __syncthreads();
 
     // ---- rows: suffix parts (partitions meeting [0, kT)), then prefix parts
@@ -161,7 +174,7 @@ __device__ __forceinline__ void range_body(const float* __restrict__ f, size_t p
         const int gy = by + oy, gx = bx + ox;
         if (gy >= H || gx >= W) continue;
         const float M = cmax[oy * kTp + ox];
-        const float v = reg[(oy + R) * Ls + (ox + R)];
+        const float v = __ldg(f + (size_t)gy * pitch + gx);
         if (kImages) {
             Mx[(size_t)gy * pitch + gx] = M;
             mn[(size_t)gy * pitch + gx] = cmin[oy * kTp + ox];
@@ -216,7 +229,8 @@ size_t range_smem(int R, bool with_min)
 {
     const size_t L = kT + 2 * (size_t)R;
     const size_t lines = with_min ? 2 : 1;
-    return sizeof(float) * (L * (L + 1) + lines * (L * kTp + kT * kTp));
+    const size_t reg = L * (L + 1) > lines * kT * kTp ? L * (L + 1) : lines * kT * kTp;
+    return sizeof(float) * (reg + lines * L * kTp);
 }
 
 template <bool kMin, bool kImages>

@@ -89,16 +89,19 @@ def test_lowp_16bit_image(bf, planes):
     assert err <= 257 * TOL[planes]
 
 
-def test_tuned_metric_workload_sampled(bf):
-    """The metric's tuned form at full size (4096^2 G8, sigma_s = 8,
-    sigma_r = 10, Algorithm 2 with eps = 1e-2, FP16 planes): <= 0.5 gray
-    level against the oracle with the same (T, N, M), at sampled pixels."""
+@pytest.mark.parametrize("mode,tile", [("global", 128), ("tile", 128)])
+def test_tuned_metric_workload_sampled(bf, mode, tile):
+    """The metric's tuned forms at full size (4096^2 G8, sigma_s = 8,
+    sigma_r = 10, Algorithm 2 with eps = 1e-2, FP16 planes; exact T of the
+    whole image or of each 128 x 128 T-tile): <= 0.5 gray level against the
+    oracle with the same (T, N, M) per tile, at sampled pixels (random,
+    corners, T-tile seams)."""
     f = synth.g8(4096, 4096, seed=5)
-    out, p = run(bf, f, 8.0, 10.0, 0.01, "fp16", "global", "alg2", 128)
+    out, p = run(bf, f, 8.0, 10.0, 0.01, "fp16", mode, "alg2", tile)
     rng = np.random.default_rng(9)
     ys = np.concatenate([rng.integers(0, 4096, 150), [0, 4095, 0, 4095, 127, 128, 2048]])
     xs = np.concatenate([rng.integers(0, 4096, 150), [0, 4095, 4095, 0, 31, 32, 2048]])
     ref = oracle.direct(f, 8.0, 10.0, p, points=(ys, xs))
     err = np.max(np.abs(out[ys, xs] - ref))
-    print("tuned fp16 4096^2: max-abs %.4f gray levels at %d pixels" % (err, ys.size))
+    print("tuned fp16 4096^2 %s: max-abs %.4f gray levels at %d pixels" % (mode, err, ys.size))
     assert err <= 0.5
