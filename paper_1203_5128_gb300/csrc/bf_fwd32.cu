@@ -83,9 +83,8 @@ __device__ __forceinline__ void fwd32_body(const FwdArgs& a, int by, int bx, flo
         for (int q = 0; q < 4; ++q) hsm[q * hplane + (size_t)G.RH * TW + i] = 0.f;
 
     // clipped Gaussian mass of my outputs (denominator guard)
-    float cmass = 0.f;
-    for (int t = -R; t <= R; ++t)
-        if (gx + t >= 0 && gx + t < a.W) cmass += a.taps[t + R];
+    const float full = full_mass(a.taps, R);
+    const float cmass = clipped_mass(a.taps, R, gx, a.W, full);
 
     float num[8], den[8];
 #pragma unroll
@@ -144,9 +143,7 @@ __device__ __forceinline__ void fwd32_body(const FwdArgs& a, int by, int bx, flo
         for (int i = 0; i < 8; ++i) {
             const int gy = by + rb * 8 + i;
             if (gy >= a.H) continue;
-            float rmass = 0.f;
-            for (int t = -R; t <= R; ++t)
-                if (gy + t >= 0 && gy + t < a.H) rmass += a.taps[t + R];
+            const float rmass = clipped_mass(a.taps, R, gy, a.H, full);
             float v;
             if (den[i] > kGuard * rmass * cmass) {
                 v = __fdiv_rn(num[i], den[i]) + a.c0;
@@ -208,9 +205,9 @@ __device__ __forceinline__ void fwd32t_body(const FwdArgs& a, const fir32::Taps&
             fsm[r * G.RWp + col] = v;
         }
     }
-    float cmass = 0.f;
-    for (int t = -R; t <= R; ++t)
-        if (gx + t >= 0 && gx + t < a.W) cmass += tp.g[t + Rp + 8];
+    const float* taps = tp.g + Rp + 8 - R;          // taps[t + R] = g(t)
+    const float full = full_mass(taps, R);
+    const float cmass = clipped_mass(taps, R, gx, a.W, full);
     float num[8], den[8];
 #pragma unroll
     for (int i = 0; i < 8; ++i) num[i] = den[i] = 0.f;
@@ -264,9 +261,7 @@ __device__ __forceinline__ void fwd32t_body(const FwdArgs& a, const fir32::Taps&
         for (int i = 0; i < 8; ++i) {
             const int gy = by + rb * 8 + i;
             if (gy >= a.H) continue;
-            float rmass = 0.f;
-            for (int t = -R; t <= R; ++t)
-                if (gy + t >= 0 && gy + t < a.H) rmass += tp.g[t + Rp + 8];
+            const float rmass = clipped_mass(taps, R, gy, a.H, full);
             float v;
             if (den[i] > kGuard * rmass * cmass) {
                 v = __fdiv_rn(num[i], den[i]) + a.c0;

@@ -520,16 +520,13 @@ __global__ void __launch_bounds__(NT, 1) k_fwd_tc(FwdArgs a, long long spin_limi
         }
         if (ok && gy < a.H) {
             // normalise with the guard (FP32 clipped Gaussian mass) and store
-            float rmass = 0.f;
-            for (int t = -R; t <= R; ++t)
-                if (gy + t >= 0 && gy + t < a.H) rmass += a.taps[t + R];
+            const float full = full_mass(a.taps, R);
+            const float rmass = clipped_mass(a.taps, R, gy, a.H, full);
 #pragma unroll
             for (int x = 0; x < TW; ++x) {
                 const int gx = bx + x;
                 if (gx >= a.W) continue;
-                float cmass = 0.f;
-                for (int t = -R; t <= R; ++t)
-                    if (gx + t >= 0 && gx + t < a.W) cmass += a.taps[t + R];
+                const float cmass = clipped_mass(a.taps, R, gx, a.W, full);
                 float v;
                 if (den[x] > kGuard * rmass * cmass) {
                     v = __fdiv_rn(num[x], den[x]) * c0 + c0;

@@ -65,6 +65,26 @@ struct Pair {
     float om_hi, om_lo, W, pad;
 };
 
+// Clipped Gaussian mass along one axis (the denominator guard's
+// (g * 1_Omega) factor): the sum of taps[t + R] over the t with 0 <= i + t < n,
+// added in increasing t.  `full` is the same sum over every t (the same
+// additions in the same order), which is the value at every coordinate at
+// least R from both ends, so only coordinates near the border loop.
+__device__ __forceinline__ float clipped_mass(const float* taps, int R, int i, int n, float full)
+{
+    if (i - R >= 0 && i + R < n) return full;
+    float m = 0.f;
+    for (int t = -R; t <= R; ++t)
+        if (i + t >= 0 && i + t < n) m += taps[t + R];
+    return m;
+}
+__device__ __forceinline__ float full_mass(const float* taps, int R)
+{
+    float m = 0.f;
+    for (int t = -R; t <= R; ++t) m += taps[t + R];
+    return m;
+}
+
 // Device status bits (mirrors BF_DEV_* of bf.h).
 constexpr unsigned kDevOrder = 1u << 0;
 constexpr unsigned kDevTimeout = 1u << 1;

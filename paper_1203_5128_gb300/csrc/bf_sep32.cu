@@ -269,9 +269,8 @@ __global__ void k_sep_final(SepArgs a)
     if (x >= a.W) return;
     const SetHdr hd = a.hdr[0];
     const int R = a.R;
-    float cmass = 0.f;
-    for (int t = -R; t <= R; ++t)
-        if (x + t >= 0 && x + t < a.W) cmass += a.taps[t + R];
+    const float full = full_mass(a.taps, R);
+    const float cmass = clipped_mass(a.taps, R, x, a.W, full);
     for (int y = blockIdx.y; y < a.H; y += gridDim.y) {
         const float fv = a.f[(size_t)y * a.f_pitch + x];
         float v;
@@ -279,9 +278,7 @@ __global__ void k_sep_final(SepArgs a)
         if (hd.F < 0) {
             v = fv;                                  // order above the cap: pass through
         } else {
-            float rmass = 0.f;
-            for (int t = -R; t <= R; ++t)
-                if (y + t >= 0 && y + t < a.H) rmass += a.taps[t + R];
+            const float rmass = clipped_mass(a.taps, R, y, a.H, full);
             const float2 nd = a.nd[(size_t)y * a.W + x];
             den = nd.y;
             if (nd.y > kGuard * rmass * cmass) {
