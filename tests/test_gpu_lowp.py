@@ -105,3 +105,35 @@ def test_tuned_metric_workload_sampled(bf, mode, tile):
     err = np.max(np.abs(out[ys, xs] - ref))
     print("tuned fp16 4096^2 %s: max-abs %.4f gray levels at %d pixels" % (mode, err, ys.size))
     assert err <= 0.5
+
+
+@pytest.mark.parametrize("planes", ["fp16", "bf16"])
+def test_order_cap_passes_image_through(bf, planes):
+    """A set whose N exceeds the plan's cap passes its pixels through (and
+    raises the device status bit); with per-tile T the other tiles are
+    filtered as usual in the same persistent launch."""
+    import torch
+    from paper_1203_5128_gb300 import _native as nat
+    f = synth.g8(256, 320, seed=5)
+    plan = bf.bf_plan(256, 320, 2.0, 5.0, 0.0, plane_dtype=planes, n_max=16)
+    out = bf.bf_execute(plan, to_dev(f))
+    torch.cuda.synchronize()
+    assert np.array_equal(out.cpu().numpy(), f)
+    assert bf.bf_get_device_status(plan) & nat.BF_DEV_ORDER_TOO_LARGE
+    # per-tile: a flat tile keeps a small N, a tile with an edge exceeds the cap
+    g = np.full((256, 256), 100.0, np.float32)
+    g[:, 200:] = 180.0
+    plan = bf.bf_plan(256, 256, 2.0, 20.0, 0.0, plane_dtype=planes, t_mode="tile", t_tile=128,
+                      n_max=4)
+    out = bf.bf_execute(plan, to_dev(g)).cpu().numpy()
+    torch.cuda.synchronize()
+    T, N, M = bf.bf_get_sets(plan)
+    capped = N > 4
+    assert capped.any() and (~capped).any()
+    for s_ in range(4):
+        ty, tx = divmod(s_, 2)
+        blk = (slice(128 * ty, 128 * ty + 128), slice(128 * tx, 128 * tx + 128))
+        if capped[s_]:
+            assert np.array_equal(out[blk], g[blk])
+        else:
+            assert np.max(np.abs(out[blk] - g[blk])) < 1.0   # flat tile: f itself, filtered
