@@ -113,25 +113,48 @@ class ClockSampler:
 
 
 # ------------------------------------------------------------------ CPU oracle
-def cpu_oracle_run(f_np, seconds_target: float):
-    """Times the FP64 oracle (SHIFTABLE-BF, Algorithm 2 parameters from the
-    oracle itself) on a centred crop of the image, sized to take about
-    `seconds_target`.  Returns (Mpx/s, crop side, seconds, threads)."""
+def oracle_tuned_params(f_np):
+    """The oracle's (T, N, M) for the tuned form: exact T per T-tile."""
+    import oracle
+    return oracle.resolve(f_np, SIGMA_S, SIGMA_R, EPS, t_mode=TUNED["t_mode"], rule="alg2",
+                          t_tile=TUNED.get("t_tile", 64))
+
+
+def oracle_crop(f64, p, y0, side):
+    """The FP64 oracle's SHIFTABLE-BF on the crop [y0, y0+side)^2, each part
+    of it with the (N, M) of the T-tile it lies in.  Returns the seconds."""
     import numpy as np
     import oracle
-    p = oracle.resolve(f_np, SIGMA_S, SIGMA_R, EPS, t_mode="global", rule="alg2")
-    f64 = np.ascontiguousarray(f_np, dtype=np.float64)
-    g = oracle.taps(SIGMA_S, p.R)
     lib = oracle._load()
+    g = oracle.taps(SIGMA_S, p.R)
     out = np.empty_like(f64)
+    t0 = time.perf_counter()
+    ty0, ty1 = y0 // p.tile_h, (y0 + side - 1) // p.tile_h if p.tile_h < H else 0
+    for ty in range(ty0 if p.tile_h < H else 0, ty1 + 1):
+        for tx in range(ty0 if p.tile_w < W else 0, ty1 + 1):
+            ys, ye = max(y0, ty * p.tile_h), min(y0 + side, (ty + 1) * p.tile_h)
+            xs, xe = max(y0, tx * p.tile_w), min(y0 + side, (tx + 1) * p.tile_w)
+            if ys >= ye or xs >= xe:
+                continue
+            a, b = (ty, tx) if p.T.size > 1 else (0, 0)
+            lib.orc_shiftable_block(oracle._p(f64), H, W, oracle._p(g), p.R, int(p.N[a, b]),
+                                    int(p.M[a, b]), SIGMA_R, ys, ye, xs, xe,
+                                    oracle._p(out), None, None)
+    return time.perf_counter() - t0
+
+
+def cpu_oracle_run(f_np, seconds_target: float):
+    """Times the FP64 oracle (SHIFTABLE-BF with the tuned form's Algorithm 2
+    parameters, from the oracle itself) on a centred crop of the image,
+    sized to take about `seconds_target`.  Returns (Mpx/s, crop side,
+    seconds, threads)."""
+    import numpy as np
+    import oracle
+    p = oracle_tuned_params(f_np)
+    f64 = np.ascontiguousarray(f_np, dtype=np.float64)
 
     def run(side):
-        y0 = (H - side) // 2
-        t0 = time.perf_counter()
-        lib.orc_shiftable_block(oracle._p(f64), H, W, oracle._p(g), p.R, int(p.N[0, 0]),
-                                int(p.M[0, 0]), SIGMA_R, y0, y0 + side, y0, y0 + side,
-                                oracle._p(out), None, None)
-        return time.perf_counter() - t0
+        return oracle_crop(f64, p, (H - side) // 2, side)
 
     side = 32
     dt = run(side)
@@ -149,27 +172,18 @@ def reference_arm(args, rank: int):
         return
     f_np = synth.g8(H, W, seed=SEED)
     import oracle
-    p = oracle.resolve(f_np, SIGMA_S, SIGMA_R, EPS, t_mode="global", rule="alg2")
+    p = oracle_tuned_params(f_np)
     f64 = np.ascontiguousarray(f_np, dtype=np.float64)
-    g = oracle.taps(SIGMA_S, p.R)
-    lib = oracle._load()
-    out = np.empty_like(f64)
     side = 96
     y0 = (H - side) // 2
-
-    def step():
-        lib.orc_shiftable_block(oracle._p(f64), H, W, oracle._p(g), p.R, int(p.N[0, 0]),
-                                int(p.M[0, 0]), SIGMA_R, y0, y0 + side, y0, y0 + side,
-                                oracle._p(out), None, None)
     for _ in range(args.warmup):
-        step()
-    t0 = time.perf_counter()
+        oracle_crop(f64, p, y0, side)
+    dt = 0.0
     for _ in range(args.steps):
-        step()
-    dt = time.perf_counter() - t0
+        dt += oracle_crop(f64, p, y0, side)
     v = side * side * args.steps / dt / 1e6
-    sample = "centred %dx%d crop of the 4096^2 image per step (FP64 oracle, N=%d M=%d)" % (
-        side, side, int(p.N[0, 0]), int(p.M[0, 0]))
+    sample = ("centred %dx%d crop of the 4096^2 image per step (FP64 oracle, exact T per "
+              "%dx%d T-tile, each part with its tile's N, M)" % (side, side, p.tile_h, p.tile_w))
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "Mpixel/s",
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": dt * 1e3 / args.steps, "higher_is_better": True,
@@ -455,8 +469,8 @@ def main():
     if not args.no_cpu_baseline and world == 1:
         v, side, dt, thr = cpu_oracle_run(f_np, args.cpu_seconds)
         cpu = {"value": v, "unit": "Mpixel/s", "cores": thr, "kind": "oracle",
-               "sample": "centred %dx%d crop of the tuned workload (FP64 shiftable oracle, "
-                         "%.1f s)" % (side, side, dt)}
+               "sample": "centred %dx%d crop of the tuned workload (FP64 shiftable oracle with the "
+                         "tuned form's per-tile T, N, M; %.1f s)" % (side, side, dt)}
 
     line = {
         "metric": METRIC, "value": value, "unit": "Mpixel/s", "n_gpus": world,
