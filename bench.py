@@ -158,9 +158,9 @@ def cpu_oracle_run(f_np, seconds_target: float):
 
     side = 32
     dt = run(side)
-    # cost ~ (side + 2R)^2: grow the crop to the time target
-    while dt < seconds_target / 3 and side < 1024:
-        side *= 2
+    # cost ~ side^2: grow the crop (up to the whole image) to the time target
+    while dt < seconds_target / 3 and side < min(H, W):
+        side = min(2 * side, min(H, W))
         dt = run(side)
     return side * side / dt / 1e6, side, dt, oracle.num_threads()
 
@@ -174,7 +174,7 @@ def reference_arm(args, rank: int):
     import oracle
     p = oracle_tuned_params(f_np)
     f64 = np.ascontiguousarray(f_np, dtype=np.float64)
-    side = 96
+    side = 512
     y0 = (H - side) // 2
     for _ in range(args.warmup):
         oracle_crop(f64, p, y0, side)

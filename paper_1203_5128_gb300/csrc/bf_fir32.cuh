@@ -168,45 +168,53 @@ __device__ __forceinline__ void col_pass(const Geo& G, const float* hsm, const f
 namespace bf {
 namespace fir32 {
 
-// ---- tall-tile variant: two row-filtered planes at a time, exact taps ------
+// ---- tall tile, packed pairs: the cos and sin planes of a pass ride in one
+// 64-bit register pair and advance together in packed FP32 multiply-adds
+// (fma.rn.f32x2, sm_100 and later), which halves the issue slots of the FIR.
 //
 // The radius is padded to Rp = 4 ceil(R/4) (taps beyond R are zero and add
-// exact zeros), so that 2 Rp is a multiple of 8: the first 8-input step of
-// an 8-output block then only meets taps j - i >= 0 (lower triangle) and the
-// last one only taps j - i <= 0 (upper triangle), and the FIR executes
-// exactly 2 Rp + 1 multiply-adds per output.  The row-filtered planes are
-// stored with the 16-byte quads of each row permuted by (row & 7), which
-// spreads the vector stores of a warp over all 32 banks.
+// exact zeros), so that 2 Rp is a multiple of 8: the first 8-input step of an
+// 8-output block then only meets taps j - i >= 0 (lower triangle) and the
+// last one only taps j - i <= 0 (upper triangle), and the FIR executes exactly
+// 2 Rp + 1 multiply-adds per output.  With NCH (the number of 8-input steps,
+// Rp / 4 + 1) a template parameter the FIR loops unroll completely, every tap
+// index is a constant and the taps are read from the kernel's parameter bank.
+//
+// Shared memory (NCH fixes every size):
+//   cs   RH x CSp float2   (cos, sin) of the halo pixels; CSp = RW + 2 makes a
+//                           row an odd number of 16-byte chunks, so the eight
+//                           rows a quarter-warp reads fall on distinct banks;
+//   fz   RH x FP  float    centred f; FP = RW + 4, an odd number of chunks;
+//   hz   RH x TW  float2   row-filtered pair, 16-byte chunks of row r
+//                           permuted by (r & 7).
 
-struct Geo2 {
-    int R, Rp, nch, RH, RW, RWp, RHp, ngz;
-    __host__ __device__ Geo2(int R_, int TH, int TW)
-    {
-        R = R_;
-        Rp = (R + 3) / 4 * 4;
-        nch = Rp / 4 + 1;                       // (2 Rp + 8) / 8 input steps
-        RH = TH + 2 * Rp;
-        RW = TW + 2 * Rp;
-        RWp = TW - 8 + 8 * nch + 4;             // = RW + 4: rows 16 B aligned, banks staggered
-        RHp = TH - 8 + 8 * nch;                 // = RH
-        ngz = 8 * nch + 16;
-    }
-    // the sin array and the second row-filtered plane start 4 words (16 B)
-    // past a bank-aligned offset, so that the two arrays a quarter-warp
-    // reads or writes together fall on different banks
-    __host__ __device__ size_t region() const { return (size_t)RH * RWp; }
-    __host__ __device__ size_t hplane(int TW) const { return (size_t)RHp * TW + 4; }
-    __host__ __device__ size_t floats(int TW) const
-    {
-        return 3 * region() + 4 + 2 * hplane(TW) + (size_t)ngz;
-    }
+constexpr int kTapsMaxRp = 24;    // the tall tile's largest padded radius
+struct Taps {
+    float g[8 * (kTapsMaxRp / 4 + 1) + 16];   // g[t + 8] = g(t - Rp), 0 outside |t - Rp| <= R
+};
+struct Taps2 {
+    float2 g[8 * (kTapsMaxRp / 4 + 1) + 16];  // (g, g) with g as in Taps
 };
 
-// word offset of element (row r, column x) of a swizzled row-filtered plane
-template <int TW>
-__device__ __forceinline__ int hsw(int r, int x)
+template <int TH, int TW, int NCH>
+struct TallGeo {
+    static constexpr int Rp = 4 * (NCH - 1);
+    static constexpr int RH = TH + 2 * Rp;
+    static constexpr int RW = TW + 2 * Rp;
+    static constexpr int CSp = RW + 2;
+    static constexpr int FP = RW + 4;
+    static constexpr size_t cs_bytes = (size_t)RH * CSp * 8;
+    static constexpr size_t fz_bytes = (size_t)RH * FP * 4;
+    static constexpr size_t hz_bytes = (size_t)RH * TW * 8;
+    static constexpr size_t bytes = cs_bytes + fz_bytes + hz_bytes;
+    static_assert(TW == 32, "the swizzle assumes 16 chunks per row-filtered row");
+    static_assert(RH % 8 == 0 && (CSp / 2) % 2 == 1 && (FP / 4) % 2 == 1, "bank layout");
+};
+
+// float2 index of element (row r, column x) of the swizzled row-filtered pair
+__device__ __forceinline__ int hz_at(int r, int x)
 {
-    return r * TW + ((((x >> 2) ^ (r & 7)) & (TW / 4 - 1)) << 2) + (x & 3);
+    return r * 32 + ((((x >> 1) ^ (r & 7)) << 1) | (x & 1));
 }
 
 // One 8x8 step of an 8-output FIR block: acc[i] += g[j - i + 7] * v[j] for
@@ -224,174 +232,105 @@ __device__ __forceinline__ void fir_step(float (&acc)[8], const float (&g)[15], 
         }
 }
 
-// Row pass for one plane per item: plane value m * cs (m = m1s, or 1 when
-// m1s is null), items (halo row r, 8-column block cb, plane p of the pair
-// (p = 0 uses cos, p = 1 sin)); output to hsm plane p (swizzled rows).
-template <int TW>
-__device__ __forceinline__ void row_pass2(const Geo2& G, const float* m1s, const float* csm,
-                                          const float* ssm, const float* gz, float* hsm, int tid,
-                                          int nthreads)
+// One input step on pairs: acc[i] += g(d - Rp) v[j] with d = s0 + j - i, for
+// the (j, i) whose d lies in [0, 2 Rp]; s0 is a compile-time constant after
+// unrolling, so the window test costs nothing and tp.g[d + 8] is a constant-
+// bank operand.
+template <int NO, int NI, int Rp>
+__device__ __forceinline__ void fir_x2(float2 (&acc)[NO], const Taps2& tp, int s0,
+                                       const float2 (&v)[NI])
 {
-    const size_t hplane = G.hplane(TW);
-    for (int it = tid; it < G.RH * (TW / 8) * 2; it += nthreads) {
-        const int p = it & 1, rc = it >> 1;
-        const int r = rc / (TW / 8), cb = rc - r * (TW / 8);
-        const float* src = (p ? ssm : csm) + r * G.RWp + cb * 8;
-        const float* mr = m1s ? m1s + r * G.RWp + cb * 8 : nullptr;
-        float acc[8];
 #pragma unroll
-        for (int i = 0; i < 8; ++i) acc[i] = 0.f;
-        for (int ch = 0; ch < G.nch; ++ch) {
-            const int a0 = ch * 8;
-            float g[15];
+    for (int j = 0; j < NI; ++j)
 #pragma unroll
-            for (int d = 0; d < 15; ++d) g[d] = gz[a0 + d + 1];   // tap a0 + d - 7
-            const float4 v0 = *(const float4*)(src + a0), v1 = *(const float4*)(src + a0 + 4);
-            float v[8] = {v0.x, v0.y, v0.z, v0.w, v1.x, v1.y, v1.z, v1.w};
-            if (mr) {
-                const float4 f0 = *(const float4*)(mr + a0), f1 = *(const float4*)(mr + a0 + 4);
-                v[0] *= f0.x; v[1] *= f0.y; v[2] *= f0.z; v[3] *= f0.w;
-                v[4] *= f1.x; v[5] *= f1.y; v[6] *= f1.z; v[7] *= f1.w;
-            }
-            if (ch == 0) fir_step<1>(acc, g, v);
-            else if (ch == G.nch - 1) fir_step<2>(acc, g, v);
-            else fir_step<0>(acc, g, v);
+        for (int i = 0; i < NO; ++i) {
+            const int d = s0 + j - i;
+            if (d < 0 || d > 2 * Rp) continue;
+            acc[i] = __ffma2_rn(tp.g[d + 8], v[j], acc[i]);
         }
-        float* hp = hsm + p * hplane;
-        *(float4*)(hp + hsw<TW>(r, cb * 8)) = make_float4(acc[0], acc[1], acc[2], acc[3]);
-        *(float4*)(hp + hsw<TW>(r, cb * 8 + 4)) = make_float4(acc[4], acc[5], acc[6], acc[7]);
+}
+
+// Row FIR of NO consecutive outputs (NO = 4 or 8) of the pair (m c, m s),
+// m = f (kNum) or 1: inputs src[0 .. NO + 2 Rp), in steps of NO.
+template <int NO, int NCH, bool kNum>
+__device__ __forceinline__ void row_item_x2(const Taps2& tp, const float2* src, const float* fr,
+                                            float2 (&acc)[NO])
+{
+    constexpr int Rp = 4 * (NCH - 1), NS = (NO + 2 * Rp) / NO;
+#pragma unroll
+    for (int i = 0; i < NO; ++i) acc[i] = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int st = 0; st < NS; ++st) {
+        float2 v[NO];
+#pragma unroll
+        for (int q = 0; q < NO / 2; ++q) {
+            const float4 w = *(const float4*)(src + st * NO + 2 * q);
+            v[2 * q] = make_float2(w.x, w.y);
+            v[2 * q + 1] = make_float2(w.z, w.w);
+        }
+        if (kNum) {
+#pragma unroll
+            for (int q = 0; q < NO / 4; ++q) {
+                const float4 m = *(const float4*)(fr + st * NO + 4 * q);
+                v[4 * q] = __fmul2_rn(make_float2(m.x, m.x), v[4 * q]);
+                v[4 * q + 1] = __fmul2_rn(make_float2(m.y, m.y), v[4 * q + 1]);
+                v[4 * q + 2] = __fmul2_rn(make_float2(m.z, m.z), v[4 * q + 2]);
+                v[4 * q + 3] = __fmul2_rn(make_float2(m.w, m.w), v[4 * q + 3]);
+            }
+        }
+        fir_x2<NO, NO, Rp>(acc, tp, st * NO, v);
     }
 }
 
-// Column pass of two planes for one item: column o, output rows rb*8 .. rb*8+7.
-template <int TW>
-__device__ __forceinline__ void col_pass2(const Geo2& G, const float* hsm, const float* gz, int o,
-                                          int rb, float (&acc)[2][8])
+// Row pass of the pair into the swizzled hz.  The first NT-multiple of the
+// RH x 4 items (halo row r, 8-column block) runs as 8-output items, the
+// eight rows of a quarter-warp consecutive; the rest, fewer than NT items,
+// runs as twice as many 4-output items in one round, so that the last round
+// takes half as long.
+template <int TH, int TW, int NCH, int NT, bool kNum>
+__device__ __forceinline__ void row_pass_x2(const Taps2& tp, const float2* cs, const float* fz,
+                                            float2* hz, int tid)
 {
-    const size_t hplane = G.hplane(TW);
+    using G = TallGeo<TH, TW, NCH>;
+    constexpr int kItems = G::RH * (TW / 8);
+    constexpr int kFull = kItems / NT * NT;
+    constexpr int kHalf = 2 * (kItems - kFull);
+    static_assert(kFull % 32 == 0 && kHalf <= NT && (kHalf % 64) == 0, "row pass split");
+    for (int it = tid; it < kFull; it += NT) {
+        const int cb = (it >> 3) & 3, r = (it & 7) + ((it >> 5) << 3);
+        float2 acc[8];
+        row_item_x2<8, NCH, kNum>(tp, cs + r * G::CSp + cb * 8, fz + r * G::FP + cb * 8, acc);
 #pragma unroll
-    for (int q = 0; q < 2; ++q)
+        for (int q = 0; q < 4; ++q)
+            *(float4*)(hz + hz_at(r, cb * 8 + 2 * q)) =
+                make_float4(acc[2 * q].x, acc[2 * q].y, acc[2 * q + 1].x, acc[2 * q + 1].y);
+    }
+    if (tid < kHalf) {
+        const int r = kFull / 4 + (tid & 7) + ((tid >> 6) << 3), x0 = ((tid >> 3) & 7) * 4;
+        float2 acc[4];
+        row_item_x2<4, NCH, kNum>(tp, cs + r * G::CSp + x0, fz + r * G::FP + x0, acc);
 #pragma unroll
-        for (int i = 0; i < 8; ++i) acc[q][i] = 0.f;
-    for (int ch = 0; ch < G.nch; ++ch) {
-        const int a0 = ch * 8;
-        float g[15];
-#pragma unroll
-        for (int d = 0; d < 15; ++d) g[d] = gz[a0 + d + 1];
-        float v0[8], v1[8];
-#pragma unroll
-        for (int j = 0; j < 8; ++j) {
-            const int r = rb * 8 + a0 + j;
-            const int w = hsw<TW>(r, o);
-            v0[j] = hsm[w];
-            v1[j] = hsm[hplane + w];
-        }
-        if (ch == 0) {
-            fir_step<1>(acc[0], g, v0);
-            fir_step<1>(acc[1], g, v1);
-        } else if (ch == G.nch - 1) {
-            fir_step<2>(acc[0], g, v0);
-            fir_step<2>(acc[1], g, v1);
-        } else {
-            fir_step<0>(acc[0], g, v0);
-            fir_step<0>(acc[1], g, v1);
-        }
+        for (int q = 0; q < 2; ++q)
+            *(float4*)(hz + hz_at(r, x0 + 2 * q)) =
+                make_float4(acc[2 * q].x, acc[2 * q].y, acc[2 * q + 1].x, acc[2 * q + 1].y);
     }
 }
 
-}  // namespace fir32
-}  // namespace bf
-
-namespace bf {
-namespace fir32 {
-
-// ---- compile-time tap count: taps as kernel parameters ---------------------
-//
-// With NCH (the number of 8-input steps, Rp / 4 + 1) a template parameter the
-// FIR loops unroll completely and every tap index is a constant, so the taps
-// are read from the kernel's parameter bank as FFMA operands instead of being
-// loaded from shared memory.  R >= 1 makes NCH >= 2, so the first and last
-// steps are distinct.
-
-constexpr int kTapsMaxRp = 24;    // the tall tile's largest padded radius
-struct Taps {
-    float g[8 * (kTapsMaxRp / 4 + 1) + 16];   // g[t + 8] = g(t - Rp), 0 outside |t - Rp| <= R
-};
-
-template <int TW, int NCH>
-__device__ __forceinline__ void row_pass2c(const Geo2& G, const Taps& tp, const float* m1s,
-                                           const float* csm, const float* ssm, float* hsm,
-                                           int tid, int nthreads)
+// Column pass of the pair for one item: column o, output rows rb*CO .. rb*CO+CO-1,
+// input rows in steps of 8; tap d = input - output + Rp.
+template <int TH, int TW, int NCH, int CO>
+__device__ __forceinline__ void col_pass_x2(const Taps2& tp, const float2* hz, int o, int rb,
+                                            float2 (&acc)[CO])
 {
-    const size_t hplane = G.hplane(TW);
-    for (int it = tid; it < G.RH * (TW / 8) * 2; it += nthreads) {
-        const int p = it & 1, rc = it >> 1;
-        const int r = rc / (TW / 8), cb = rc - r * (TW / 8);
-        const float* src = (p ? ssm : csm) + r * G.RWp + cb * 8;
-        const float* mr = m1s ? m1s + r * G.RWp + cb * 8 : nullptr;
-        float acc[8];
+    constexpr int Rp = 4 * (NCH - 1), NS = (CO + 2 * Rp) / 8;
 #pragma unroll
-        for (int i = 0; i < 8; ++i) acc[i] = 0.f;
+    for (int i = 0; i < CO; ++i) acc[i] = make_float2(0.f, 0.f);
 #pragma unroll
-        for (int ch = 0; ch < NCH; ++ch) {
-            const int a0 = ch * 8;
-            float g[15];
+    for (int ch = 0; ch < NS; ++ch) {
+        float2 v[8];
 #pragma unroll
-            for (int d = 0; d < 15; ++d) g[d] = tp.g[a0 + d + 1];
-            const float4 v0 = *(const float4*)(src + a0), v1 = *(const float4*)(src + a0 + 4);
-            float v[8] = {v0.x, v0.y, v0.z, v0.w, v1.x, v1.y, v1.z, v1.w};
-            if (mr) {
-                const float4 f0 = *(const float4*)(mr + a0), f1 = *(const float4*)(mr + a0 + 4);
-                v[0] *= f0.x; v[1] *= f0.y; v[2] *= f0.z; v[3] *= f0.w;
-                v[4] *= f1.x; v[5] *= f1.y; v[6] *= f1.z; v[7] *= f1.w;
-            }
-            if (ch == 0) {
-                fir_step<1>(acc, g, v);
-            } else if (ch == NCH - 1) {
-                fir_step<2>(acc, g, v);
-            } else {
-                fir_step<0>(acc, g, v);
-            }
-        }
-        float* hp = hsm + p * hplane;
-        *(float4*)(hp + hsw<TW>(r, cb * 8)) = make_float4(acc[0], acc[1], acc[2], acc[3]);
-        *(float4*)(hp + hsw<TW>(r, cb * 8 + 4)) = make_float4(acc[4], acc[5], acc[6], acc[7]);
-    }
-}
-
-template <int TW, int NCH>
-__device__ __forceinline__ void col_pass2c(const Geo2& G, const Taps& tp, const float* hsm, int o,
-                                           int rb, float (&acc)[2][8])
-{
-    const size_t hplane = G.hplane(TW);
-#pragma unroll
-    for (int q = 0; q < 2; ++q)
-#pragma unroll
-        for (int i = 0; i < 8; ++i) acc[q][i] = 0.f;
-#pragma unroll
-    for (int ch = 0; ch < NCH; ++ch) {
-        const int a0 = ch * 8;
-        float g[15];
-#pragma unroll
-        for (int d = 0; d < 15; ++d) g[d] = tp.g[a0 + d + 1];
-        float v0[8], v1[8];
-#pragma unroll
-        for (int j = 0; j < 8; ++j) {
-            const int r = rb * 8 + a0 + j;
-            const int w = hsw<TW>(r, o);
-            v0[j] = hsm[w];
-            v1[j] = hsm[hplane + w];
-        }
-        if (ch == 0) {
-            fir_step<1>(acc[0], g, v0);
-            fir_step<1>(acc[1], g, v1);
-        } else if (ch == NCH - 1) {
-            fir_step<2>(acc[0], g, v0);
-            fir_step<2>(acc[1], g, v1);
-        } else {
-            fir_step<0>(acc[0], g, v0);
-            fir_step<0>(acc[1], g, v1);
-        }
+        for (int j = 0; j < 8; ++j) v[j] = hz[hz_at(rb * CO + ch * 8 + j, o)];
+        fir_x2<CO, 8, Rp>(acc, tp, ch * 8, v);
     }
 }
 

@@ -157,29 +157,88 @@ __device__ __forceinline__ void fwd32_body(const FwdArgs& a, int by, int bx, flo
     }
 }
 
-// Tall-tile form (128 x 32 outputs, 512 threads): row-filtered planes two at
-// a time in a swizzled buffer, exact taps (see Geo2).  Same arithmetic per
-// output as fwd32_body: the nonzero taps are summed in the same order and
-// the skipped ones would have added exact zeros.
-//
-// NCH = Rp / 4 + 1 is a template parameter and the taps arrive as a kernel
-// parameter (tp.g[t + 8] = g(t - Rp)), so the fully unrolled FIR takes every
-// tap from the constant bank; the taps are the plan's FP32 taps, the same
-// words the shared-memory form reads.
-template <int TH, int TW, int NCH>
-__device__ __forceinline__ void fwd32t_body(const FwdArgs& a, const fir32::Taps& tp, int by,
-                                            int bx, float* sm)
-{
-    constexpr int NT = TH * TW / 8;
-    constexpr int NW = NT / 32;
-    const fir32::Geo2 G(a.R, TH, TW);
-    const int R = a.R, Rp = G.Rp;
-    float* fsm = sm;                              // RH x RWp  centred f, 0 outside
-    float* csm = fsm + G.region();                // RH x RWp  cos
-    float* ssm = csm + G.region() + 4;            // RH x RWp  sin (bank-staggered)
-    float* hsm = ssm + G.region();                // 2 planes of RHp x TW (+4), row-filtered
+// Phase sweep of a tall tile: the first S * RW threads own one halo column
+// each (col = tid % RW) and rows r0 + S m, r0 = tid / RW, m = 0 .. ITERS-1, so
+// that every shared-memory address is a per-thread base plus a constant.
+template <class G, int NT>
+struct PhaseSweep {
+    static constexpr int S = NT / G::RW;
+    static constexpr int ITERS = (G::RH + S - 1) / S;
+    bool on, x_in;
+    int r0, fbase, cbase, gyb;
+    __device__ __forceinline__ PhaseSweep(int tid, int gy0, int gx0, int W)
+    {
+        on = tid < S * G::RW;
+        r0 = tid / G::RW;
+        const int col = tid - r0 * G::RW;
+        x_in = (unsigned)(gx0 + col) < (unsigned)W;
+        fbase = r0 * G::FP + col;
+        cbase = r0 * G::CSp + col;
+        gyb = gy0 + r0;
+    }
+    // (cos, sin) of row r0 + S m for the frequency (om_hi + om_lo); zero outside the image
+    template <int m>
+    __device__ __forceinline__ void step(const float* fz, float2* cs, int H, float om_hi,
+                                         float om_lo) const
+    {
+        if (m >= ITERS) return;
+        if (!on || (m == ITERS - 1 && r0 + S * m >= G::RH)) return;
+        float c, sn;
+        phase_cs(fz[fbase + S * m * G::FP], om_hi, om_lo, c, sn);
+        const bool in = x_in && (unsigned)(gyb + S * m) < (unsigned)H;
+        cs[cbase + S * m * G::CSp] = in ? make_float2(c, sn) : make_float2(0.f, 0.f);
+    }
+};
 
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+template <class PS, int m0, int n>
+struct PhaseSteps {
+    __device__ __forceinline__ static void run(const PS& ps, const float* fz, float2* cs, int H,
+                                               float om_hi, float om_lo)
+    {
+        ps.template step<m0>(fz, cs, H, om_hi, om_lo);
+        PhaseSteps<PS, m0 + 1, n - 1>::run(ps, fz, cs, H, om_hi, om_lo);
+    }
+};
+template <class PS, int m0>
+struct PhaseSteps<PS, m0, 0> {
+    __device__ __forceinline__ static void run(const PS&, const float*, float2*, int, float, float) {}
+};
+
+// Tall-tile form (128 x 32 outputs, 512 threads): the cos and sin planes of
+// a pass are filtered together as packed pairs (see TallGeo).  Same
+// arithmetic per output as fwd32_body: each lane of a packed multiply-add
+// rounds like fmaf, the nonzero taps are summed in the same order and the
+// skipped ones would have added exact zeros.
+//
+// NCH = Rp / 4 + 1 is a template parameter and the taps arrive as kernel
+// parameters (tp.g[t + 8] = g(t - Rp), tp2 the same as pairs), so the fully
+// unrolled FIR takes every tap from the constant bank; the taps are the
+// plan's FP32 taps, the same words the shared-memory form reads.
+//
+// Per pair k: row pass of (f' c, f' s) -> column pass -> numerator; row pass
+// of (c, s) -> column pass -> denominator.  The last column pass reads only
+// the row-filtered buffer, so the phases of pair k + 1 are written into cs
+// during it, their independent SFU / FMA chains filling the issue slots the
+// packed multiply-adds leave free; the denominator's demodulation then takes
+// cos / sin of pair k at its own outputs from the same phase function.
+template <int TH, int TW, int NCH>
+__device__ __forceinline__ void fwd32t_body(const FwdArgs& a, const fir32::Taps& tp,
+                                            const fir32::Taps2& tp2, int by, int bx, char* sm)
+{
+    using G = fir32::TallGeo<TH, TW, NCH>;
+    constexpr int CO = 8;                      // a thread owns CO outputs of one column
+    constexpr int NT = TH * TW / CO;
+    constexpr int Rp = G::Rp;
+    constexpr int NPX = G::RH * G::RW;         // halo pixels
+    static_assert(NT / G::RW >= 1, "phase sweep");
+    constexpr int NS = CO / 8 + NCH - 1;       // input steps of the column pass
+    using PS = PhaseSweep<G, NT>;
+    constexpr int PPS = (PS::ITERS + NS - 1) / NS;               // phase rows per column step
+    float2* cs = (float2*)sm;                                   // RH x CSp (cos, sin)
+    float* fz = (float*)(sm + G::cs_bytes);                     // RH x FP  centred f
+    float2* hz = (float2*)(sm + G::cs_bytes + G::fz_bytes);     // RH x TW  row-filtered pair
+
+    const int tid = threadIdx.x;
     const int gy0 = by - Rp, gx0 = bx - Rp;
     const int set = a.set_tile ? (by / a.set_tile) * a.sets_x + (bx / a.set_tile) : 0;
     const SetHdr hd = a.hdr[set];
@@ -187,79 +246,112 @@ __device__ __forceinline__ void fwd32t_body(const FwdArgs& a, const fir32::Taps&
     const int gx = bx + o;
 
     if (hd.F < 0) {          // order above the cap: pass the image through
-        for (int i = 0; i < 8; ++i) {
-            const int gy = by + rb * 8 + i;
+        for (int i = 0; i < CO; ++i) {
+            const int gy = by + rb * CO + i;
             if (gy < a.H && gx < a.W)
                 a.out[(size_t)gy * a.out_pitch + gx] = a.f[(size_t)gy * a.f_pitch + gx];
         }
         return;
     }
-    for (int r = warp; r < G.RH; r += NW) {
-        const int gy = gy0 + r;
-        const bool rin = gy >= 0 && gy < a.H;
-        for (int col = lane; col < G.RWp; col += 32) {
-            const int x = gx0 + col;
-            float v = 0.f;
-            if (rin && col < G.RW && x >= 0 && x < a.W)
-                v = __ldg(a.f + (size_t)gy * a.f_pitch + x) - a.c0;
-            fsm[r * G.RWp + col] = v;
-        }
+    for (int e = tid; e < NPX; e += NT) {
+        const int r = e / G::RW, col = e - r * G::RW;
+        const int gy = gy0 + r, x = gx0 + col;
+        float v = 0.f;
+        if (gy >= 0 && gy < a.H && x >= 0 && x < a.W)
+            v = __ldg(a.f + (size_t)gy * a.f_pitch + x) - a.c0;
+        fz[r * G::FP + col] = v;
     }
+    const int R = a.R;
     const float* taps = tp.g + Rp + 8 - R;          // taps[t + R] = g(t)
     const float full = full_mass(taps, R);
     const float cmass = clipped_mass(taps, R, gx, a.W, full);
-    float num[8], den[8];
+    float num[CO], den[CO];
 #pragma unroll
-    for (int i = 0; i < 8; ++i) num[i] = den[i] = 0.f;
-    __syncthreads();
+    for (int i = 0; i < CO; ++i) num[i] = den[i] = 0.f;
 
     const Pair* pr = a.pairs + (size_t)set * a.cap_pairs;
     const int K = hd.F + hd.z;
-    for (int k = 0; k < K; ++k) {
-        float om_hi = 0.f, om_lo = 0.f, Wk = hd.w0;
+    // frequency and weight of pair k (the zero-frequency term last)
+    auto pair_of = [&](int k, float& om_hi, float& om_lo, float& Wk) {
+        om_hi = 0.f;
+        om_lo = 0.f;
+        Wk = hd.w0;
         if (k < hd.F) {
             const Pair p = pr[k];
             om_hi = p.om_hi;
             om_lo = p.om_lo;
             Wk = p.W;
         }
-        for (int r = warp; r < G.RH; r += NW) {
-            const int gy = gy0 + r;
-            const bool rin = gy >= 0 && gy < a.H;
-            for (int col = lane; col < G.RWp; col += 32) {
-                const int x = gx0 + col;
-                float c = 0.f, s = 0.f;
-                if (rin && col < G.RW && x >= 0 && x < a.W)
-                    phase_cs(fsm[r * G.RWp + col], om_hi, om_lo, c, s);
-                csm[r * G.RWp + col] = c;
-                ssm[r * G.RWp + col] = s;
+    };
+    float om_hi, om_lo, Wk;
+    pair_of(0, om_hi, om_lo, Wk);
+    const PS ps(tid, gy0, gx0, a.W);
+    __syncthreads();
+    PhaseSteps<PS, 0, PS::ITERS>::run(ps, fz, cs, a.H, om_hi, om_lo);
+    __syncthreads();
+
+    for (int k = 0; k < K; ++k) {
+        // numerator pair (f' c, f' s)
+        fir32::row_pass_x2<TH, TW, NCH, NT, true>(tp2, cs, fz, hz, tid);
+        __syncthreads();
+        {
+            float2 nab[CO];
+            fir32::col_pass_x2<TH, TW, NCH, CO>(tp2, hz, o, rb, nab);
+#pragma unroll
+            for (int i = 0; i < CO; ++i) {
+                const float2 cc = cs[(rb * CO + i + Rp) * G::CSp + o + Rp];
+                num[i] = fmaf(Wk, fmaf(cc.x, nab[i].x, cc.y * nab[i].y), num[i]);
             }
         }
         __syncthreads();
-        // numerator planes f' c, f' s
-        fir32::row_pass2c<TW, NCH>(G, tp, fsm, csm, ssm, hsm, tid, NT);
+        // denominator pair (c, s)
+        fir32::row_pass_x2<TH, TW, NCH, NT, false>(tp2, cs, fz, hz, tid);
         __syncthreads();
-        float nab[2][8];
-        fir32::col_pass2c<TW, NCH>(G, tp, hsm, o, rb, nab);
-        __syncthreads();
-        // denominator planes c, s
-        fir32::row_pass2c<TW, NCH>(G, tp, nullptr, csm, ssm, hsm, tid, NT);
-        __syncthreads();
-        float dcd[2][8];
-        fir32::col_pass2c<TW, NCH>(G, tp, hsm, o, rb, dcd);
+        {
+            const bool next = k + 1 < K;
+            float nx_hi, nx_lo, nW;
+            pair_of(k + 1, nx_hi, nx_lo, nW);
+            float2 dcd[CO];
 #pragma unroll
-        for (int i = 0; i < 8; ++i) {
-            const int ry = rb * 8 + i + Rp;
-            const float c = csm[ry * G.RWp + o + Rp], s = ssm[ry * G.RWp + o + Rp];
-            num[i] = fmaf(Wk, fmaf(c, nab[0][i], s * nab[1][i]), num[i]);
-            den[i] = fmaf(Wk, fmaf(c, dcd[0][i], s * dcd[1][i]), den[i]);
+            for (int i = 0; i < CO; ++i) dcd[i] = make_float2(0.f, 0.f);
+#pragma unroll
+            for (int ch = 0; ch < NS; ++ch) {
+                float2 v[8];
+#pragma unroll
+                for (int j = 0; j < 8; ++j) v[j] = hz[fir32::hz_at(rb * CO + ch * 8 + j, o)];
+                fir32::fir_x2<CO, 8, Rp>(dcd, tp2, ch * 8, v);
+                if (next) {
+#pragma unroll
+                    for (int u = 0; u < PPS; ++u) {
+                        const int m = ch * PPS + u;
+                        if (m < PS::ITERS) {
+                            float c, sn;
+                            if (ps.on && (m < PS::ITERS - 1 || ps.r0 + PS::S * m < G::RH)) {
+                                phase_cs(fz[ps.fbase + PS::S * m * G::FP], nx_hi, nx_lo, c, sn);
+                                const bool in = ps.x_in && (unsigned)(ps.gyb + PS::S * m) < (unsigned)a.H;
+                                cs[ps.cbase + PS::S * m * G::CSp] =
+                                    in ? make_float2(c, sn) : make_float2(0.f, 0.f);
+                            }
+                        }
+                    }
+                }
+            }
+#pragma unroll
+            for (int i = 0; i < CO; ++i) {
+                float c, sn;
+                phase_cs(fz[(rb * CO + i + Rp) * G::FP + o + Rp], om_hi, om_lo, c, sn);
+                den[i] = fmaf(Wk, fmaf(c, dcd[i].x, sn * dcd[i].y), den[i]);
+            }
+            om_hi = nx_hi;
+            om_lo = nx_lo;
+            Wk = nW;
         }
         __syncthreads();
     }
     if (gx < a.W) {
 #pragma unroll
-        for (int i = 0; i < 8; ++i) {
-            const int gy = by + rb * 8 + i;
+        for (int i = 0; i < CO; ++i) {
+            const int gy = by + rb * CO + i;
             if (gy >= a.H) continue;
             const float rmass = clipped_mass(taps, R, gy, a.H, full);
             float v;
@@ -277,20 +369,22 @@ __device__ __forceinline__ void fwd32t_body(const FwdArgs& a, const fir32::Taps&
 
 template <int TH, int TW, int NCH>
 __global__ void __launch_bounds__(TH * TW / 8, 1)
-k_fwd32t(FwdArgs a, const __grid_constant__ fir32::Taps tp)
+k_fwd32t(FwdArgs a, const __grid_constant__ fir32::Taps tp, const __grid_constant__ fir32::Taps2 tp2)
 {
-    extern __shared__ __align__(16) float sm[];
-    fwd32t_body<TH, TW, NCH>(a, tp, blockIdx.y * TH, blockIdx.x * TW, sm);
+    extern __shared__ __align__(16) char smc[];
+    fwd32t_body<TH, TW, NCH>(a, tp, tp2, blockIdx.y * TH, blockIdx.x * TW, smc);
 }
 
 template <int NCH>
-cudaError_t launch_tall(const FwdArgs& a, const fir32::Taps& tp, size_t smem, cudaStream_t s)
+cudaError_t launch_tall(const FwdArgs& a, const fir32::Taps& tp, const fir32::Taps2& tp2,
+                        cudaStream_t s)
 {
+    constexpr size_t smem = fir32::TallGeo<128, 32, NCH>::bytes;
     cudaError_t e = cudaFuncSetAttribute(k_fwd32t<128, 32, NCH>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     dim3 grid((a.W + 31) / 32, (a.H + 127) / 128);
-    k_fwd32t<128, 32, NCH><<<grid, 512, smem, s>>>(a, tp);
+    k_fwd32t<128, 32, NCH><<<grid, 512, smem, s>>>(a, tp, tp2);
     return cudaGetLastError();
 }
 
@@ -398,7 +492,18 @@ cudaError_t launch_fwd32_persistent(int th, int tw, int max_R, const FwdArgs* im
     return e;
 }
 
-size_t fwd32t_smem(int R) { return fir32::Geo2(R, 128, 32).floats(32) * sizeof(float); }
+size_t fwd32t_smem(int R)
+{
+    switch ((R + 3) / 4 + 1) {
+        case 2: return fir32::TallGeo<128, 32, 2>::bytes;
+        case 3: return fir32::TallGeo<128, 32, 3>::bytes;
+        case 4: return fir32::TallGeo<128, 32, 4>::bytes;
+        case 5: return fir32::TallGeo<128, 32, 5>::bytes;
+        case 6: return fir32::TallGeo<128, 32, 6>::bytes;
+        case 7: return fir32::TallGeo<128, 32, 7>::bytes;
+        default: return (size_t)-1;
+    }
+}
 
 // The 128 x 32 tall tile serves a launch when its padded radius has a
 // compiled tap count, its shared memory fits and its tiles nest inside the
@@ -435,20 +540,21 @@ cudaError_t launch_fwd32(const FwdArgs& a, cudaStream_t s)
         return launch_sep32(sa, a.sep_cap_terms, s);
     }
     if (a.h_taps && fwd32t_ok(a.R, a.set_tile)) {
-        const fir32::Geo2 G(a.R, 128, 32);
+        const int Rp = (a.R + 3) / 4 * 4;
         fir32::Taps tp;
+        fir32::Taps2 tp2;
         for (int i = 0; i < (int)(sizeof(tp.g) / sizeof(float)); ++i) {
-            const int k = i - 8 - G.Rp;
+            const int k = i - 8 - Rp;
             tp.g[i] = (k >= -a.R && k <= a.R) ? a.h_taps[k + a.R] : 0.f;
+            tp2.g[i] = make_float2(tp.g[i], tp.g[i]);
         }
-        const size_t smem = fwd32t_smem(a.R);
-        switch (G.nch) {
-            case 2: return launch_tall<2>(a, tp, smem, s);
-            case 3: return launch_tall<3>(a, tp, smem, s);
-            case 4: return launch_tall<4>(a, tp, smem, s);
-            case 5: return launch_tall<5>(a, tp, smem, s);
-            case 6: return launch_tall<6>(a, tp, smem, s);
-            case 7: return launch_tall<7>(a, tp, smem, s);
+        switch (Rp / 4 + 1) {
+            case 2: return launch_tall<2>(a, tp, tp2, s);
+            case 3: return launch_tall<3>(a, tp, tp2, s);
+            case 4: return launch_tall<4>(a, tp, tp2, s);
+            case 5: return launch_tall<5>(a, tp, tp2, s);
+            case 6: return launch_tall<6>(a, tp, tp2, s);
+            case 7: return launch_tall<7>(a, tp, tp2, s);
             default: break;
         }
     }
