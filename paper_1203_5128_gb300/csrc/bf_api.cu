@@ -623,6 +623,7 @@ cudaError_t launch_backward(bf_plan_s* p, const float* f, const float* gout, flo
     cudaError_t e = launch_fwd32(fa, s);
     if (e != cudaSuccess) return e;
     BwdArgs ba;
+    ba.h_taps = p->h_taps;
     ba.f = f;
     ba.u = gout;
     ba.grad = gin;

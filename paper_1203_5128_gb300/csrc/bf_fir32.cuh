@@ -334,5 +334,162 @@ __device__ __forceinline__ void col_pass_x2(const Taps2& tp, const float2* hz, i
     }
 }
 
+// Row FIR of NO outputs for two pairs: (m1 c, m1 s) and (m2 c, m2 s), m2 = 1
+// when kOnes.
+template <int NO, int NCH, bool kOnes>
+__device__ __forceinline__ void row_item_2x2(const Taps2& tp, const float2* src, const float* m1,
+                                             const float* m2, float2 (&acc1)[NO],
+                                             float2 (&acc2)[NO])
+{
+    constexpr int Rp = 4 * (NCH - 1), NS = (NO + 2 * Rp) / NO;
+#pragma unroll
+    for (int i = 0; i < NO; ++i) acc1[i] = acc2[i] = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int st = 0; st < NS; ++st) {
+        float2 v[NO], va[NO], vb[NO];
+#pragma unroll
+        for (int q = 0; q < NO / 2; ++q) {
+            const float4 w = *(const float4*)(src + st * NO + 2 * q);
+            v[2 * q] = make_float2(w.x, w.y);
+            v[2 * q + 1] = make_float2(w.z, w.w);
+        }
+#pragma unroll
+        for (int q = 0; q < NO / 4; ++q) {
+            const float4 m = *(const float4*)(m1 + st * NO + 4 * q);
+            va[4 * q] = __fmul2_rn(make_float2(m.x, m.x), v[4 * q]);
+            va[4 * q + 1] = __fmul2_rn(make_float2(m.y, m.y), v[4 * q + 1]);
+            va[4 * q + 2] = __fmul2_rn(make_float2(m.z, m.z), v[4 * q + 2]);
+            va[4 * q + 3] = __fmul2_rn(make_float2(m.w, m.w), v[4 * q + 3]);
+            if (kOnes) {
+                vb[4 * q] = v[4 * q];
+                vb[4 * q + 1] = v[4 * q + 1];
+                vb[4 * q + 2] = v[4 * q + 2];
+                vb[4 * q + 3] = v[4 * q + 3];
+            } else {
+                const float4 n = *(const float4*)(m2 + st * NO + 4 * q);
+                vb[4 * q] = __fmul2_rn(make_float2(n.x, n.x), v[4 * q]);
+                vb[4 * q + 1] = __fmul2_rn(make_float2(n.y, n.y), v[4 * q + 1]);
+                vb[4 * q + 2] = __fmul2_rn(make_float2(n.z, n.z), v[4 * q + 2]);
+                vb[4 * q + 3] = __fmul2_rn(make_float2(n.w, n.w), v[4 * q + 3]);
+            }
+        }
+        fir_x2<NO, NO, Rp>(acc1, tp, st * NO, va);
+        fir_x2<NO, NO, Rp>(acc2, tp, st * NO, vb);
+    }
+}
+
+template <int NO>
+__device__ __forceinline__ void store_row_x2(float2* hz, int r, int x0, const float2 (&acc)[NO])
+{
+#pragma unroll
+    for (int q = 0; q < NO / 2; ++q)
+        *(float4*)(hz + hz_at(r, x0 + 2 * q)) =
+            make_float4(acc[2 * q].x, acc[2 * q].y, acc[2 * q + 1].x, acc[2 * q + 1].y);
+}
+
+// Row pass of two pairs into the swizzled planes hz1, hz2 (TW = 32, rows of
+// the halo RH, pitches CSp / FP of the geometry G).  Items (halo row, 8-column
+// block), the eight rows of a quarter-warp consecutive: full rounds of
+// 8-output items, then the rest as twice as many 4-output items when they
+// fit one round, else as 8-output items.
+template <class G, int NCH, int NT, bool kOnes>
+__device__ __forceinline__ void row_pass_2x2(const Taps2& tp, const float2* cs, const float* m1,
+                                             const float* m2, float2* hz1, float2* hz2, int tid)
+{
+    constexpr int TW = 32;
+    constexpr int kItems = G::RH * (TW / 8);
+    constexpr int kFull = kItems / NT * NT;
+    constexpr bool kSplit = 2 * (kItems - kFull) <= NT;
+    constexpr int kMain = kSplit ? kFull : kItems;
+    constexpr int kHalf = kSplit ? 2 * (kItems - kFull) : 0;
+    static_assert(kItems % 32 == 0 && kFull % 32 == 0, "row pass items");
+    for (int it = tid; it < kMain; it += NT) {
+        const int cb = (it >> 3) & 3, r = (it & 7) + ((it >> 5) << 3);
+        float2 acc1[8], acc2[8];
+        row_item_2x2<8, NCH, kOnes>(tp, cs + r * G::CSp + cb * 8, m1 + r * G::FP + cb * 8,
+                                    m2 + r * G::FP + cb * 8, acc1, acc2);
+        store_row_x2<8>(hz1, r, cb * 8, acc1);
+        store_row_x2<8>(hz2, r, cb * 8, acc2);
+    }
+    if (kHalf > 0 && tid < kHalf) {
+        const int r = kFull / 4 + (tid & 7) + ((tid >> 6) << 3), x0 = ((tid >> 3) & 7) * 4;
+        float2 acc1[4], acc2[4];
+        row_item_2x2<4, NCH, kOnes>(tp, cs + r * G::CSp + x0, m1 + r * G::FP + x0,
+                                    m2 + r * G::FP + x0, acc1, acc2);
+        store_row_x2<4>(hz1, r, x0, acc1);
+        store_row_x2<4>(hz2, r, x0, acc2);
+    }
+}
+
+// Column pass of two pairs for one item: column o, output rows rb*8 .. rb*8+7.
+template <int NCH>
+__device__ __forceinline__ void col_pass_2x2(const Taps2& tp, const float2* hz1, const float2* hz2,
+                                             int o, int rb, float2 (&acc1)[8], float2 (&acc2)[8])
+{
+    constexpr int Rp = 4 * (NCH - 1), NS = NCH;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) acc1[i] = acc2[i] = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int ch = 0; ch < NS; ++ch) {
+        float2 v1[8], v2[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            const int w = hz_at(rb * 8 + ch * 8 + j, o);
+            v1[j] = hz1[w];
+            v2[j] = hz2[w];
+        }
+        fir_x2<8, 8, Rp>(acc1, tp, ch * 8, v1);
+        fir_x2<8, 8, Rp>(acc2, tp, ch * 8, v2);
+    }
+}
+
+// Phase sweep of a tile (geometry G: RH x RW halo, cs / fz pitches CSp / FP):
+// the first S * RW threads own one halo column
+// each (col = tid % RW) and rows r0 + S m, r0 = tid / RW, m = 0 .. ITERS-1, so
+// that every shared-memory address is a per-thread base plus a constant.
+template <class G, int NT>
+struct PhaseSweep {
+    static constexpr int S = NT / G::RW;
+    static constexpr int ITERS = (G::RH + S - 1) / S;
+    bool on, x_in;
+    int r0, fbase, cbase, gyb;
+    __device__ __forceinline__ PhaseSweep(int tid, int gy0, int gx0, int W)
+    {
+        on = tid < S * G::RW;
+        r0 = tid / G::RW;
+        const int col = tid - r0 * G::RW;
+        x_in = (unsigned)(gx0 + col) < (unsigned)W;
+        fbase = r0 * G::FP + col;
+        cbase = r0 * G::CSp + col;
+        gyb = gy0 + r0;
+    }
+    // (cos, sin) of row r0 + S m for the frequency (om_hi + om_lo); zero outside the image
+    template <int m>
+    __device__ __forceinline__ void step(const float* fz, float2* cs, int H, float om_hi,
+                                         float om_lo) const
+    {
+        if (m >= ITERS) return;
+        if (!on || (m == ITERS - 1 && r0 + S * m >= G::RH)) return;
+        float c, sn;
+        phase_cs(fz[fbase + S * m * G::FP], om_hi, om_lo, c, sn);
+        const bool in = x_in && (unsigned)(gyb + S * m) < (unsigned)H;
+        cs[cbase + S * m * G::CSp] = in ? make_float2(c, sn) : make_float2(0.f, 0.f);
+    }
+};
+
+template <class PS, int m0, int n>
+struct PhaseSteps {
+    __device__ __forceinline__ static void run(const PS& ps, const float* fz, float2* cs, int H,
+                                               float om_hi, float om_lo)
+    {
+        ps.template step<m0>(fz, cs, H, om_hi, om_lo);
+        PhaseSteps<PS, m0 + 1, n - 1>::run(ps, fz, cs, H, om_hi, om_lo);
+    }
+};
+template <class PS, int m0>
+struct PhaseSteps<PS, m0, 0> {
+    __device__ __forceinline__ static void run(const PS&, const float*, float2*, int, float, float) {}
+};
+
 }  // namespace fir32
 }  // namespace bf

@@ -157,53 +157,6 @@ __device__ __forceinline__ void fwd32_body(const FwdArgs& a, int by, int bx, flo
     }
 }
 
-// Phase sweep of a tall tile: the first S * RW threads own one halo column
-// each (col = tid % RW) and rows r0 + S m, r0 = tid / RW, m = 0 .. ITERS-1, so
-// that every shared-memory address is a per-thread base plus a constant.
-template <class G, int NT>
-struct PhaseSweep {
-    static constexpr int S = NT / G::RW;
-    static constexpr int ITERS = (G::RH + S - 1) / S;
-    bool on, x_in;
-    int r0, fbase, cbase, gyb;
-    __device__ __forceinline__ PhaseSweep(int tid, int gy0, int gx0, int W)
-    {
-        on = tid < S * G::RW;
-        r0 = tid / G::RW;
-        const int col = tid - r0 * G::RW;
-        x_in = (unsigned)(gx0 + col) < (unsigned)W;
-        fbase = r0 * G::FP + col;
-        cbase = r0 * G::CSp + col;
-        gyb = gy0 + r0;
-    }
-    // (cos, sin) of row r0 + S m for the frequency (om_hi + om_lo); zero outside the image
-    template <int m>
-    __device__ __forceinline__ void step(const float* fz, float2* cs, int H, float om_hi,
-                                         float om_lo) const
-    {
-        if (m >= ITERS) return;
-        if (!on || (m == ITERS - 1 && r0 + S * m >= G::RH)) return;
-        float c, sn;
-        phase_cs(fz[fbase + S * m * G::FP], om_hi, om_lo, c, sn);
-        const bool in = x_in && (unsigned)(gyb + S * m) < (unsigned)H;
-        cs[cbase + S * m * G::CSp] = in ? make_float2(c, sn) : make_float2(0.f, 0.f);
-    }
-};
-
-template <class PS, int m0, int n>
-struct PhaseSteps {
-    __device__ __forceinline__ static void run(const PS& ps, const float* fz, float2* cs, int H,
-                                               float om_hi, float om_lo)
-    {
-        ps.template step<m0>(fz, cs, H, om_hi, om_lo);
-        PhaseSteps<PS, m0 + 1, n - 1>::run(ps, fz, cs, H, om_hi, om_lo);
-    }
-};
-template <class PS, int m0>
-struct PhaseSteps<PS, m0, 0> {
-    __device__ __forceinline__ static void run(const PS&, const float*, float2*, int, float, float) {}
-};
-
 // Tall-tile form (128 x 32 outputs, 512 threads): the cos and sin planes of
 // a pass are filtered together as packed pairs (see TallGeo).  Same
 // arithmetic per output as fwd32_body: each lane of a packed multiply-add
@@ -232,7 +185,7 @@ __device__ __forceinline__ void fwd32t_body(const FwdArgs& a, const fir32::Taps&
     constexpr int NPX = G::RH * G::RW;         // halo pixels
     static_assert(NT / G::RW >= 1, "phase sweep");
     constexpr int NS = CO / 8 + NCH - 1;       // input steps of the column pass
-    using PS = PhaseSweep<G, NT>;
+    using PS = fir32::PhaseSweep<G, NT>;
     constexpr int PPS = (PS::ITERS + NS - 1) / NS;               // phase rows per column step
     float2* cs = (float2*)sm;                                   // RH x CSp (cos, sin)
     float* fz = (float*)(sm + G::cs_bytes);                     // RH x FP  centred f
@@ -287,7 +240,7 @@ __device__ __forceinline__ void fwd32t_body(const FwdArgs& a, const fir32::Taps&
     pair_of(0, om_hi, om_lo, Wk);
     const PS ps(tid, gy0, gx0, a.W);
     __syncthreads();
-    PhaseSteps<PS, 0, PS::ITERS>::run(ps, fz, cs, a.H, om_hi, om_lo);
+    fir32::PhaseSteps<PS, 0, PS::ITERS>::run(ps, fz, cs, a.H, om_hi, om_lo);
     __syncthreads();
 
     for (int k = 0; k < K; ++k) {

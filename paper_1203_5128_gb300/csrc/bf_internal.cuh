@@ -179,6 +179,7 @@ cudaError_t launch_fwd32(const FwdArgs& a, cudaStream_t s);
 
 // K5 (adjoint, FP32 planes, FIR): needs the forward's out and den images.
 struct BwdArgs {
+    const float* h_taps;    // host copy of the taps (null: shared-memory taps only)
     const float* f;
     const float* u;         // dL/d out
     float* grad;            // dL/d f

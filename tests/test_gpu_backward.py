@@ -51,7 +51,10 @@ CASES = [
     (70, 45, 2.0, 15.0, 0.01, "fixed", 64),
     (128, 96, 1.2, 30.0, 0.01, "tile", 64),
     (33, 65, 4.0, 25.0, 0.01, "global", 64),     # R = 12, ragged
-    (50, 50, 8.0, 40.0, 0.05, "global", 64),     # R = 24
+    (50, 50, 8.0, 40.0, 0.05, "global", 64),     # R = 24 (scalar form)
+    (96, 130, 5.0, 30.0, 0.01, "global", 64),    # R = 15: 5 input steps
+    (80, 70, 6.0, 40.0, 0.01, "tile", 64),       # R = 18: 6 steps, per-tile T
+    (200, 150, 4.0, 20.0, 0.01, "tile", 64),     # R = 12, several T-tiles per halo
 ]
 
 
