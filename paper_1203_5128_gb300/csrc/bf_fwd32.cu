@@ -484,7 +484,7 @@ cudaError_t launch_fwd32(const FwdArgs& a, cudaStream_t s)
         sa.pairs = a.pairs;
         sa.taps = a.taps;
         sa.h_taps = a.h_taps;
-        sa.P = a.sep_P;
+        sa.P = reinterpret_cast<float2*>(a.sep_P);
         sa.nd = a.sep_nd;
         sa.nk = a.sep_nk;
         sa.n_guarded = a.n_guarded;

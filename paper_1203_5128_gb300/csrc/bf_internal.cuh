@@ -160,7 +160,7 @@ struct SepArgs {
     const Pair* pairs;
     const float* taps;      // device taps (guard mass)
     const float* h_taps;    // host taps (kernel parameter)
-    float* P;               // [nk][4][H][Wp]
+    float2* P;              // [nk][2][H][Wp]: pairs (f'c, f's), (c, s)
     float2* nd;             // [H][W]
     int nk;                 // terms per chunk
     unsigned long long* n_guarded;

@@ -7,21 +7,24 @@
 // 7-50 times the outputs.  Here the two separable passes meet in HBM:
 //
 //   k_sep_rows  a CTA takes 8 image rows x 128 output columns (+ R halo
-//               columns): f once, then per term its phases and the 4 planes
-//               f'c, f's, c, s filtered along the row (8 outputs x 8 inputs
-//               per register-blocked step, taps as constant-bank operands),
-//               written to a buffer of nk terms, [term][plane][H][Wp];
-//   k_sep_cols  a CTA takes 128 x 32 outputs: per term and plane pair, the
+//               columns): f once, then per term its phases and the pairs
+//               (f'c, f's), (c, s) filtered along the row as packed pairs
+//               (fma.rn.f32x2; 8 outputs x 8 inputs per register-blocked
+//               step, taps as constant-bank operands), written to a buffer of
+//               nk terms, [term][pair][H][Wp] float2;
+//   k_sep_cols  a CTA takes 128 x 32 outputs: per term and pair, the
 //               (128 + 2R) x 32 column strip arrives by cp.async in a
 //               two-stage shared-memory ring while the previous one is
-//               filtered; demodulation into num / den registers, carried
-//               between chunks of terms as an FP32 (num, den) partial;
+//               filtered (packed pairs again); demodulation into num / den
+//               registers, carried between chunks of terms as an FP32
+//               (num, den) partial;
 //   k_sep_final num / den + value_range / 2 with the denominator guard.
 //
-// Every FIR sums its taps in increasing input order starting from zero, and
-// every demodulation step is the same FMA sequence as the fused kernels', so
-// the results equal the fused kernels' bit for bit (zero taps, where the
-// blocks are aligned differently, add exact zeros).
+// Every FIR sums its taps in increasing input order starting from zero (each
+// lane of a packed multiply-add rounds like fmaf), and every demodulation step
+// is the same FMA sequence as the fused kernels', so the results equal the
+// fused kernels' bit for bit (zero taps, where the blocks are aligned
+// differently, add exact zeros).
 #include "bf_fir32.cuh"
 
 namespace bf {
@@ -30,7 +33,7 @@ namespace {
 
 constexpr int kSepMaxRp = 64;
 struct TapsL {
-    float g[8 * (kSepMaxRp / 4 + 1) + 16];   // g[t + 8] = g(t - Rp), 0 outside |t - Rp| <= R
+    float2 g[8 * (kSepMaxRp / 4 + 1) + 16];  // (g, g), g[t + 8] = g(t - Rp), 0 outside |t - Rp| <= R
 };
 
 constexpr int kRowsR = 8;       // image rows per row-pass CTA
@@ -55,44 +58,65 @@ __device__ __forceinline__ void term_phase(const SepArgs& a, const SetHdr& hd, i
     }
 }
 
-// One 8-output FIR block from 8 * NCH inputs starting at in[0] (FP32,
-// 16-byte aligned), taps from tp; m (may be null) multiplies each input.
-template <int NCH>
-__device__ __forceinline__ void fir_block(const TapsL& tp, const float* in, const float* m,
-                                          float (&acc)[8])
+// acc[i] += g(d - Rp) v[j], d = s0 + j - i in [0, 2 Rp] (s0 a constant after unrolling).
+template <int Rp>
+__device__ __forceinline__ void fir8_x2(float2 (&acc)[8], const TapsL& tp, int s0, const float2 (&v)[8])
 {
 #pragma unroll
-    for (int i = 0; i < 8; ++i) acc[i] = 0.f;
+    for (int j = 0; j < 8; ++j)
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            const int d = s0 + j - i;
+            if (d < 0 || d > 2 * Rp) continue;
+            acc[i] = __ffma2_rn(tp.g[d + 8], v[j], acc[i]);
+        }
+}
+
+// One 8-output FIR block of a pair from 8 * NCH input pairs starting at
+// in[0] (16-byte aligned), m (may be null) multiplying each input pair.
+template <int NCH>
+__device__ __forceinline__ void fir_block_x2(const TapsL& tp, const float2* in, const float* m,
+                                             float2 (&acc)[8])
+{
+    constexpr int Rp = (NCH - 1) * 4;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) acc[i] = make_float2(0.f, 0.f);
 #pragma unroll
     for (int ch = 0; ch < NCH; ++ch) {
         const int a0 = ch * 8;
-        float g[15];
+        float2 v[8];
 #pragma unroll
-        for (int d = 0; d < 15; ++d) g[d] = tp.g[a0 + d + 1];
-        const float4 v0 = *(const float4*)(in + a0), v1 = *(const float4*)(in + a0 + 4);
-        float v[8] = {v0.x, v0.y, v0.z, v0.w, v1.x, v1.y, v1.z, v1.w};
+        for (int q = 0; q < 4; ++q) {
+            const float4 w = *(const float4*)(in + a0 + 2 * q);
+            v[2 * q] = make_float2(w.x, w.y);
+            v[2 * q + 1] = make_float2(w.z, w.w);
+        }
         if (m) {
             const float4 f0 = *(const float4*)(m + a0), f1 = *(const float4*)(m + a0 + 4);
-            v[0] *= f0.x; v[1] *= f0.y; v[2] *= f0.z; v[3] *= f0.w;
-            v[4] *= f1.x; v[5] *= f1.y; v[6] *= f1.z; v[7] *= f1.w;
+            const float mm[8] = {f0.x, f0.y, f0.z, f0.w, f1.x, f1.y, f1.z, f1.w};
+#pragma unroll
+            for (int j = 0; j < 8; ++j) v[j] = __fmul2_rn(make_float2(mm[j], mm[j]), v[j]);
         }
-        if (ch == 0) fir32::fir_step<1>(acc, g, v);
-        else if (ch == NCH - 1) fir32::fir_step<2>(acc, g, v);
-        else fir32::fir_step<0>(acc, g, v);
+        fir8_x2<Rp>(acc, tp, a0, v);
     }
 }
 
+// Row pass.  Shared memory: centred f (row pitch RW + 4 floats) and the
+// (cos, sin) pairs (row pitch RW + 2 float2, an odd number of 16-byte
+// chunks); a quarter-warp takes the 8 rows of one 8-column block, so its
+// vector loads fall on 8 different bank groups.
 template <int NCH>
 __global__ void __launch_bounds__(kRowsNT)
 k_sep_rows(SepArgs a, const __grid_constant__ TapsL tp, int k0)
 {
     constexpr int Rp = (NCH - 1) * 4;
     constexpr int RW = kRowsW + 2 * Rp;          // halo'd columns
-    constexpr int RWs = RW + 4;                  // row stride (bank stagger)
+    constexpr int FP = RW + 4;                   // f row pitch (floats)
+    constexpr int CSp = RW + 2;                  // (cos, sin) row pitch (pairs)
+    static_assert((FP / 4) % 2 == 1 && (CSp / 2) % 2 == 1 && kRowsR == 8, "bank layout");
     extern __shared__ __align__(16) float sm[];
-    float* fsm = sm;                             // centred f, 0 outside the image
-    float* csm = fsm + kRowsR * RWs;             // cos
-    float* ssm = csm + kRowsR * RWs + 4;         // sin (bank-staggered)
+    float2* cs = (float2*)sm;                    // kRowsR x CSp
+    float* fsm = sm + 2 * kRowsR * CSp;          // kRowsR x FP
     const SetHdr hd = a.hdr[0];
     const int nterms = sep_terms(hd);
     if (k0 >= nterms) return;
@@ -100,39 +124,38 @@ k_sep_rows(SepArgs a, const __grid_constant__ TapsL tp, int k0)
     const int tid = threadIdx.x;
     const int y0 = blockIdx.y * kRowsR, xt = blockIdx.x * kRowsW, gx0 = xt - Rp;
 
-    for (int i = tid; i < kRowsR * RWs; i += kRowsNT) {
-        const int r = i / RWs, col = i - r * RWs;
+    for (int i = tid; i < kRowsR * RW; i += kRowsNT) {
+        const int r = i / RW, col = i - r * RW;
         const int gy = y0 + r, x = gx0 + col;
         float v = 0.f;
-        if (gy < a.H && col < RW && x >= 0 && x < a.W) v = __ldg(a.f + (size_t)gy * a.f_pitch + x) - a.c0;
-        fsm[i] = v;
+        if (gy < a.H && x >= 0 && x < a.W) v = __ldg(a.f + (size_t)gy * a.f_pitch + x) - a.c0;
+        fsm[r * FP + col] = v;
     }
     __syncthreads();
     for (int kk = 0; kk < nk; ++kk) {
         float om_hi, om_lo, Wk;
         term_phase(a, hd, k0 + kk, om_hi, om_lo, Wk);
-        for (int i = tid; i < kRowsR * RWs; i += kRowsNT) {
-            const int r = i / RWs, col = i - r * RWs;
+        for (int i = tid; i < kRowsR * RW; i += kRowsNT) {
+            const int r = i / RW, col = i - r * RW;
             const int gy = y0 + r, x = gx0 + col;
-            float c = 0.f, s = 0.f;
-            if (gy < a.H && col < RW && x >= 0 && x < a.W) fir32::phase_cs(fsm[i], om_hi, om_lo, c, s);
-            csm[i] = c;
-            ssm[i] = s;
+            float c = 0.f, sn = 0.f;
+            if (gy < a.H && x >= 0 && x < a.W) fir32::phase_cs(fsm[r * FP + col], om_hi, om_lo, c, sn);
+            cs[r * CSp + col] = make_float2(c, sn);
         }
         __syncthreads();
-        // items: (plane p, row r, block cb); consecutive threads -> consecutive cb
-        for (int it = tid; it < 4 * kRowsR * (kRowsW / 8); it += kRowsNT) {
-            const int cb = it % (kRowsW / 8), r = (it / (kRowsW / 8)) % kRowsR;
-            const int p = it / (kRowsR * (kRowsW / 8));
+        // items (pair h, block cb, row r): consecutive threads -> consecutive rows
+        for (int it = tid; it < 2 * kRowsR * (kRowsW / 8); it += kRowsNT) {
+            const int r = it % kRowsR, cb = (it / kRowsR) % (kRowsW / 8);
+            const int h = it / (kRowsR * (kRowsW / 8));
             const int gy = y0 + r;
-            const float* src = ((p & 1) ? ssm : csm) + r * RWs + cb * 8;
-            const float* mr = p < 2 ? fsm + r * RWs + cb * 8 : nullptr;
-            float acc[8];
-            fir_block<NCH>(tp, src, mr, acc);
+            float2 acc[8];
+            fir_block_x2<NCH>(tp, cs + r * CSp + cb * 8, h == 0 ? fsm + r * FP + cb * 8 : nullptr, acc);
             if (gy < a.H) {
-                float* dst = a.P + (((size_t)kk * 4 + p) * a.H + gy) * a.Wp + xt + cb * 8;
-                *(float4*)dst = make_float4(acc[0], acc[1], acc[2], acc[3]);
-                *(float4*)(dst + 4) = make_float4(acc[4], acc[5], acc[6], acc[7]);
+                float2* dst = a.P + (((size_t)kk * 2 + h) * a.H + gy) * a.Wp + xt + cb * 8;
+#pragma unroll
+                for (int q = 0; q < 4; ++q)
+                    *(float4*)(dst + 2 * q) =
+                        make_float4(acc[2 * q].x, acc[2 * q].y, acc[2 * q + 1].x, acc[2 * q + 1].y);
             }
         }
         __syncthreads();
@@ -152,8 +175,9 @@ k_sep_cols(SepArgs a, const __grid_constant__ TapsL tp, int k0)
 {
     constexpr int Rp = (NCH - 1) * 4;
     constexpr int RHt = kColsH + 2 * Rp;              // halo'd rows of a strip
-    constexpr int kStage = 2 * RHt * kColsW;          // floats: two planes
+    constexpr int kStage = RHt * kColsW;              // pairs: one strip
     extern __shared__ __align__(16) float sm[];       // two stages
+    float2* sp = (float2*)sm;
     const SetHdr hd = a.hdr[0];
     const int nterms = sep_terms(hd);
     if (k0 >= nterms) return;
@@ -163,17 +187,17 @@ k_sep_cols(SepArgs a, const __grid_constant__ TapsL tp, int k0)
     const int o = lane, rb = warp;
     const int gx = bx + o;
 
-    // stage s of the sequence (term kk = s / 2, plane pair h = s % 2): strip
-    // rows by - Rp .. by + 127 + Rp of planes 2h, 2h + 1, 16 bytes per copy
+    // stage s of the sequence (term kk = s / 2, pair h = s % 2): strip rows
+    // by - Rp .. by + 127 + Rp of that pair, 16 bytes (two pairs) per copy
     auto fetch = [&](int s) {
-        float* dst = sm + (s & 1) * kStage;
+        float2* dst = sp + (s & 1) * kStage;
         const int kk = s >> 1, h = s & 1;
-        for (int i = tid; i < 2 * RHt * (kColsW / 4); i += kColsNT) {
-            const int q = i % (kColsW / 4), r = (i / (kColsW / 4)) % RHt, pl = i / (RHt * (kColsW / 4));
+        for (int i = tid; i < RHt * (kColsW / 2); i += kColsNT) {
+            const int q = i % (kColsW / 2), r = i / (kColsW / 2);
             const int gy = by - Rp + r;
             const bool ok = gy >= 0 && gy < a.H;
-            const float* src = a.P + (((size_t)kk * 4 + 2 * h + pl) * a.H + (ok ? gy : 0)) * a.Wp + bx + 4 * q;
-            cp_async16z(dst + (pl * RHt + r) * kColsW + 4 * q, src, ok);
+            const float2* src = a.P + (((size_t)kk * 2 + h) * a.H + (ok ? gy : 0)) * a.Wp + bx + 2 * q;
+            cp_async16z((float*)(dst + r * kColsW + 2 * q), (const float*)src, ok);
         }
         asm volatile("cp.async.commit_group;" ::: "memory");
     };
@@ -200,47 +224,27 @@ k_sep_cols(SepArgs a, const __grid_constant__ TapsL tp, int k0)
 
     const int nst = 2 * nk;
     fetch(0);
-    float nab[2][8];
+    float2 nab[8];
     for (int s = 0; s < nst; ++s) {
         if (s + 1 < nst) fetch(s + 1);
         else asm volatile("cp.async.commit_group;" ::: "memory");
         asm volatile("cp.async.wait_group 1;" ::: "memory");
         __syncthreads();
-        const float* st = sm + (s & 1) * kStage;
-        float acc[2][8];
+        const float2* st = sp + (s & 1) * kStage;
+        float2 acc[8];
 #pragma unroll
-        for (int q = 0; q < 2; ++q)
-#pragma unroll
-            for (int i = 0; i < 8; ++i) acc[q][i] = 0.f;
+        for (int i = 0; i < 8; ++i) acc[i] = make_float2(0.f, 0.f);
 #pragma unroll
         for (int ch = 0; ch < NCH; ++ch) {
             const int a0 = ch * 8;
-            float g[15];
+            float2 v[8];
 #pragma unroll
-            for (int d = 0; d < 15; ++d) g[d] = tp.g[a0 + d + 1];
-            float v0[8], v1[8];
-#pragma unroll
-            for (int j = 0; j < 8; ++j) {
-                const int r = rb * 8 + a0 + j;
-                v0[j] = st[r * kColsW + o];
-                v1[j] = st[(RHt + r) * kColsW + o];
-            }
-            if (ch == 0) {
-                fir32::fir_step<1>(acc[0], g, v0);
-                fir32::fir_step<1>(acc[1], g, v1);
-            } else if (ch == NCH - 1) {
-                fir32::fir_step<2>(acc[0], g, v0);
-                fir32::fir_step<2>(acc[1], g, v1);
-            } else {
-                fir32::fir_step<0>(acc[0], g, v0);
-                fir32::fir_step<0>(acc[1], g, v1);
-            }
+            for (int j = 0; j < 8; ++j) v[j] = st[(rb * 8 + a0 + j) * kColsW + o];
+            fir8_x2<Rp>(acc, tp, a0, v);
         }
         if ((s & 1) == 0) {
 #pragma unroll
-            for (int q = 0; q < 2; ++q)
-#pragma unroll
-                for (int i = 0; i < 8; ++i) nab[q][i] = acc[q][i];
+            for (int i = 0; i < 8; ++i) nab[i] = acc[i];
         } else {
             float om_hi, om_lo, Wk;
             term_phase(a, hd, k0 + (s >> 1), om_hi, om_lo, Wk);
@@ -249,8 +253,8 @@ k_sep_cols(SepArgs a, const __grid_constant__ TapsL tp, int k0)
                 float c, sn;
                 fir32::phase_cs(fo[i], om_hi, om_lo, c, sn);
                 if (!(by + rb * 8 + i < a.H && gx < a.W)) c = sn = 0.f;
-                num[i] = fmaf(Wk, fmaf(c, nab[0][i], sn * nab[1][i]), num[i]);
-                den[i] = fmaf(Wk, fmaf(c, acc[0][i], sn * acc[1][i]), den[i]);
+                num[i] = fmaf(Wk, fmaf(c, nab[i].x, sn * nab[i].y), num[i]);
+                den[i] = fmaf(Wk, fmaf(c, acc[i].x, sn * acc[i].y), den[i]);
             }
         }
         __syncthreads();                               // stage s & 1 is refilled next
@@ -297,8 +301,9 @@ template <int NCH>
 cudaError_t launch_nch(const SepArgs& a, const TapsL& tp, int n_chunks, cudaStream_t s)
 {
     constexpr int Rp = (NCH - 1) * 4;
-    const size_t smem_rows = (size_t)(3 * kRowsR * (kRowsW + 2 * Rp + 4) + 4) * sizeof(float);
-    const size_t smem_cols = (size_t)2 * 2 * (kColsH + 2 * Rp) * kColsW * sizeof(float);
+    constexpr int RW = kRowsW + 2 * Rp;
+    const size_t smem_rows = (size_t)kRowsR * (2 * (RW + 2) + RW + 4) * sizeof(float);
+    const size_t smem_cols = (size_t)2 * (kColsH + 2 * Rp) * kColsW * sizeof(float2);
     cudaError_t e = cudaFuncSetAttribute(k_sep_rows<NCH>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem_rows);
     if (e != cudaSuccess) return e;
@@ -329,9 +334,10 @@ cudaError_t launch_sep32(const SepArgs& a, int n_terms_cap, cudaStream_t s)
     if (!sep32_ok(a.R) || !a.h_taps || a.nk < 1) return cudaErrorInvalidValue;
     const int Rp = (a.R + 3) / 4 * 4;
     TapsL tp;
-    for (int i = 0; i < (int)(sizeof(tp.g) / sizeof(float)); ++i) {
+    for (int i = 0; i < (int)(sizeof(tp.g) / sizeof(float2)); ++i) {
         const int k = i - 8 - Rp;
-        tp.g[i] = (k >= -a.R && k <= a.R) ? a.h_taps[k + a.R] : 0.f;
+        const float g = (k >= -a.R && k <= a.R) ? a.h_taps[k + a.R] : 0.f;
+        tp.g[i] = make_float2(g, g);
     }
     const int n_chunks = (n_terms_cap + a.nk - 1) / a.nk;
     switch (Rp / 4 + 1) {
