@@ -86,7 +86,7 @@ def test_maxmin_pitched(bf):
 # ---------------------------------------------------------------- K1 + K2 + K3
 SMALL = [
     # H, W, sigma_s, sigma_r, eps, mode, rule, tile, value_range, t_fixed
-    (256, 256, 3.0, 30.0, 0.0, "fixed", "alg2", 64, 255.0, 255.0),     # configs[0]
+    (256, 256, 3.0, 30.0, 0.0, "fixed", "alg2", 64, 255.0, 255.0),     # 256^2 plain workload
     (100, 77, 2.0, 15.0, 0.01, "global", "trunc", 64, 255.0, None),     # ragged tiles
     (130, 200, 1.5, 12.0, 0.01, "tile", "alg2", 64, 255.0, None),       # per-tile T
     (90, 150, 2.5, 8.0, 0.01, "global", "alg2", 64, 255.0, None),       # Chernoff band
@@ -96,6 +96,10 @@ SMALL = [
     (10, 13, 5.0, 20.0, 0.01, "global", "alg2", 64, 255.0, None),       # R > image
     (65, 97, 10.0, 20.0, 0.01, "global", "trunc", 64, 255.0, None),     # R = 30
     (48, 52, 16.0, 40.0, 0.01, "global", "trunc", 64, 255.0, None),     # R = 48
+    # the tall packed-pair tile at each tap-step count not met above
+    (90, 70, 1.2, 20.0, 0.01, "global", "alg2", 64, 255.0, None),       # R = 4: 2 steps
+    (150, 130, 6.0, 30.0, 0.01, "global", "alg2", 64, 255.0, None),     # R = 18: 6 steps
+    (300, 100, 7.5, 25.0, 0.01, "tile", "alg2", 128, 255.0, None),      # R = 23: 7 steps, per-tile T
 ]
 
 
