@@ -120,6 +120,10 @@ YvvArgs yvv_args(bf_plan_s* p, const float* f, size_t fp, float* out, size_t op)
     a.mass_x = p->d_yvv_mass + p->H;
     a.n_guarded = p->d_nguard;
     yvv_design(p->sigma_s, &a.coef, nullptr);
+    const YvvCoef& k = a.coef;
+    auto two = [](float v) { return make_float2(v, v); };
+    a.coef2 = YvvCoef2{two(k.P0), two(k.Pr), two(k.Pi), two(-k.Pi), two(k.C0), two(k.Cr), two(-k.Ci),
+                       two(k.D0), two(k.Dr), two(-k.Di)};
     return a;
 }
 

@@ -207,6 +207,12 @@ struct YvvCoef {
     float C0, Cr, Ci;
     float D0, Dr, Di;
 };
+// The same coefficients as (x, x) pairs for packed multiply-adds (nPi = -Pi ...).
+struct YvvCoef2 {
+    float2 P0, Pr, Pi, nPi;
+    float2 C0, Cr, nCi;
+    float2 D0, Dr, nDi;
+};
 struct YvvArgs {
     const float* f;
     size_t f_pitch;
@@ -218,13 +224,14 @@ struct YvvArgs {
     const Pair* pairs;
     int G;                  // pass groups per launch (G * C = 32 term columns)
     int n_nd;               // (num, den) partials summed by the final kernel
-    float4* P;              // [H][W][G * C] row-filtered planes
+    float4* P;              // [H][W][G * C] row-filtered planes (f'c, c, f's, s)
     float4* S;              // [H][ceil(W/8)][3][G * C] anti-causal row states
     float2* nd;             // [G][H][W] (num, den) partials
     const float* mass_y;    // [H]
     const float* mass_x;    // [W]
     unsigned long long* n_guarded;
     YvvCoef coef;
+    YvvCoef2 coef2;
 };
 // Plan-time design (false when sigma < 0.5, outside the recursion's range);
 // poles_c (may be null) receives p0, Re p1, Im p1, c0, Re c1, Im c1.

@@ -51,30 +51,35 @@ namespace {
 
 constexpr int kWarpsPerCta = 4;
 
-struct Sec {
-    float a, re, im;      // real-pole state, complex-pole state
+// Two planes' first-order sections side by side: lane x and lane y of
+// each float2 are two planes, advanced together by packed multiply-adds
+// (fma.rn.f32x2; each lane rounds like fmaf).  The planes are paired as
+// (f'c, c) and (f's, s), so that the demodulation of one output forms
+// (num, den) as a pair.
+struct Sec2 {
+    float2 a, re, im;     // real-pole state, complex-pole state
 };
 
 // u <- p u + x for the real pole and the complex pole.
-__device__ __forceinline__ void sec_update(Sec& s, float x, const YvvCoef& k)
+__device__ __forceinline__ void sec_update(Sec2& s, float2 x, const YvvCoef2& k)
 {
-    s.a = fmaf(k.P0, s.a, x);
-    const float re = fmaf(k.Pr, s.re, fmaf(-k.Pi, s.im, x));
-    const float im = fmaf(k.Pr, s.im, k.Pi * s.re);
+    s.a = __ffma2_rn(k.P0, s.a, x);
+    const float2 re = __ffma2_rn(k.Pr, s.re, __ffma2_rn(k.nPi, s.im, x));
+    const float2 im = __ffma2_rn(k.Pr, s.im, __fmul2_rn(k.Pi, s.re));
     s.re = re;
     s.im = im;
 }
 
 // c0 u_0 + 2 Re(c1 u_1): the causal output after the update.
-__device__ __forceinline__ float sec_causal_out(const Sec& s, const YvvCoef& k)
+__device__ __forceinline__ float2 sec_causal_out(const Sec2& s, const YvvCoef2& k)
 {
-    return fmaf(k.C0, s.a, fmaf(k.Cr, s.re, -k.Ci * s.im));
+    return __ffma2_rn(k.C0, s.a, __ffma2_rn(k.Cr, s.re, __fmul2_rn(k.nCi, s.im)));
 }
 
 // c0 p0 v_0 + 2 Re(c1 p1 v_1): the anti-causal output, before the update.
-__device__ __forceinline__ float sec_anti_out(const Sec& s, const YvvCoef& k)
+__device__ __forceinline__ float2 sec_anti_out(const Sec2& s, const YvvCoef2& k)
 {
-    return fmaf(k.D0, s.a, fmaf(k.Dr, s.re, -k.Di * s.im));
+    return __ffma2_rn(k.D0, s.a, __ffma2_rn(k.Dr, s.re, __fmul2_rn(k.nDi, s.im)));
 }
 
 __device__ __forceinline__ void term_of(const YvvArgs& a, const SetHdr& hd, int k, float& om_hi,
@@ -91,14 +96,13 @@ __device__ __forceinline__ void term_of(const YvvArgs& a, const SetHdr& hd, int 
     }
 }
 
-__device__ __forceinline__ void planes_at(float v, float om_hi, float om_lo, float (&in)[4])
+// The plane pairs (v c, c) and (v s, s) of a sample.
+__device__ __forceinline__ void planes_at(float v, float om_hi, float om_lo, float2 (&in)[2])
 {
     float c, s;
     fir32::phase_cs(v, om_hi, om_lo, c, s);
-    in[0] = v * c;
-    in[1] = v * s;
-    in[2] = c;
-    in[3] = s;
+    in[0] = make_float2(v * c, c);
+    in[1] = make_float2(v * s, s);
 }
 
 // Row kernel in two sweeps so that each row-filtered sample is written once:
@@ -129,7 +133,7 @@ k_yvv_rows(YvvArgs a, int launch)
     const bool act = k < nterms;
     float om_hi, om_lo, Wk;
     term_of(a, hd, k, om_hi, om_lo, Wk);
-    const YvvCoef cf = a.coef;
+    const YvvCoef2& cf = a.coef2;
     const int W = a.W;
     const int nch = (W + B - 1) / B;
     const int col = g * C + slot;
@@ -139,9 +143,10 @@ k_yvv_rows(YvvArgs a, int launch)
 
     // sweep A: anti-causal states at the chunk boundaries (the next chunk's
     // f is fetched while this one is processed)
-    Sec st[4];
+    const float2 z2 = make_float2(0.f, 0.f);
+    Sec2 st[2];
 #pragma unroll
-    for (int q = 0; q < 4; ++q) st[q] = Sec{0.f, 0.f, 0.f};
+    for (int q = 0; q < 2; ++q) st[q] = Sec2{z2, z2, z2};
     float fn[B];
 #pragma unroll
     for (int i = 0; i < B; ++i) {
@@ -151,9 +156,9 @@ k_yvv_rows(YvvArgs a, int launch)
     for (int j = nch - 1; j >= 0; --j) {
         if (act) {
             float4* d = S + (size_t)j * 3 * GC;
-            d[0] = make_float4(st[0].a, st[0].re, st[0].im, st[1].a);
-            d[GC] = make_float4(st[1].re, st[1].im, st[2].a, st[2].re);
-            d[2 * GC] = make_float4(st[2].im, st[3].a, st[3].re, st[3].im);
+            d[0] = make_float4(st[0].a.x, st[0].a.y, st[0].re.x, st[0].re.y);
+            d[GC] = make_float4(st[0].im.x, st[0].im.y, st[1].a.x, st[1].a.y);
+            d[2 * GC] = make_float4(st[1].re.x, st[1].re.y, st[1].im.x, st[1].im.y);
         }
         const int x0 = j * B;
         float fv[B];
@@ -165,28 +170,26 @@ k_yvv_rows(YvvArgs a, int launch)
 #pragma unroll
         for (int i = B - 1; i >= 0; --i) {
             if (x0 + i >= W) continue;
-            float in[4];
+            float2 in[2];
             planes_at(fv[i] - a.c0, om_hi, om_lo, in);
 #pragma unroll
-            for (int q = 0; q < 4; ++q) sec_update(st[q], in[q], cf);
+            for (int q = 0; q < 2; ++q) sec_update(st[q], in[q], cf);
         }
     }
     // sweep B: both parts per chunk, one store per sample (the next chunk's
     // saved state and f are fetched while this one is processed)
-    Sec cs[4];
+    Sec2 cs[2];
 #pragma unroll
-    for (int q = 0; q < 4; ++q) cs[q] = Sec{0.f, 0.f, 0.f};
+    for (int q = 0; q < 2; ++q) cs[q] = Sec2{z2, z2, z2};
     const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
     float4 n0 = act ? S[0] : z4, n1 = act ? S[GC] : z4, n2 = act ? S[2 * GC] : z4;
 #pragma unroll
     for (int i = 0; i < B; ++i) fn[i] = i < W ? __ldg(frow + i) : 0.f;
     for (int j = 0; j < nch; ++j) {
         const int x0 = j * B;
-        Sec vs[4];
-        vs[0] = Sec{n0.x, n0.y, n0.z};
-        vs[1] = Sec{n0.w, n1.x, n1.y};
-        vs[2] = Sec{n1.z, n1.w, n2.x};
-        vs[3] = Sec{n2.y, n2.z, n2.w};
+        Sec2 vs[2];
+        vs[0] = Sec2{make_float2(n0.x, n0.y), make_float2(n0.z, n0.w), make_float2(n1.x, n1.y)};
+        vs[1] = Sec2{make_float2(n1.z, n1.w), make_float2(n2.x, n2.y), make_float2(n2.z, n2.w)};
         float fv[B];
 #pragma unroll
         for (int i = 0; i < B; ++i) fv[i] = fn[i];
@@ -198,14 +201,14 @@ k_yvv_rows(YvvArgs a, int launch)
 #pragma unroll
             for (int i = 0; i < B; ++i) fn[i] = x0 + B + i < W ? __ldg(frow + x0 + B + i) : 0.f;
         }
-        float in[B][4], ym[B][4];
+        float2 in[B][2], ym[B][2];
 #pragma unroll
         for (int i = 0; i < B; ++i) planes_at(x0 + i < W ? fv[i] - a.c0 : 0.f, om_hi, om_lo, in[i]);
 #pragma unroll
         for (int i = B - 1; i >= 0; --i) {
             if (x0 + i >= W) continue;            // past the row: the state stays v[W] = 0
 #pragma unroll
-            for (int q = 0; q < 4; ++q) {
+            for (int q = 0; q < 2; ++q) {
                 ym[i][q] = sec_anti_out(vs[q], cf);
                 sec_update(vs[q], in[i][q], cf);
             }
@@ -213,13 +216,13 @@ k_yvv_rows(YvvArgs a, int launch)
 #pragma unroll
         for (int i = 0; i < B; ++i) {
             if (x0 + i >= W) break;
-            float o[4];
+            float2 o[2];
 #pragma unroll
-            for (int q = 0; q < 4; ++q) {
+            for (int q = 0; q < 2; ++q) {
                 sec_update(cs[q], in[i][q], cf);
-                o[q] = sec_causal_out(cs[q], cf) + ym[i][q];
+                o[q] = __fadd2_rn(sec_causal_out(cs[q], cf), ym[i][q]);
             }
-            if (act) P[(size_t)(x0 + i) * GC] = make_float4(o[0], o[1], o[2], o[3]);
+            if (act) P[(size_t)(x0 + i) * GC] = make_float4(o[0].x, o[0].y, o[1].x, o[1].y);
         }
     }
 }
@@ -301,7 +304,7 @@ k_yvv_cols(YvvArgs a, int launch)
     float om_hi, om_lo, Wk;
     term_of(a, hd, k, om_hi, om_lo, Wk);
     if (!act) Wk = 0.f;
-    const YvvCoef cf = a.coef;
+    const YvvCoef2& cf = a.coef2;
     const int H = a.H, W = a.W;
     const int xc = xin ? x : 0;
     const float4* P = a.P + (size_t)xc * GC + g * C + slot;   // (y, x, col) at P[y * W * GC]
@@ -342,9 +345,11 @@ k_yvv_cols(YvvArgs a, int launch)
     const int nchunk = (H + B - 1) / B;
     const int sub = lane / C;
 
-    Sec st[4];
+    const float2 z2 = make_float2(0.f, 0.f);
+    const float2 W2 = make_float2(Wk, Wk);
+    Sec2 st[2];
 #pragma unroll
-    for (int q = 0; q < 4; ++q) st[q] = Sec{0.f, 0.f, 0.f};
+    for (int q = 0; q < 2; ++q) st[q] = Sec2{z2, z2, z2};
     // down sweep: causal part
     fetch(0, true, !first);
     for (int c = 0; c < nchunk; ++c) {
@@ -357,14 +362,15 @@ k_yvv_cols(YvvArgs a, int launch)
 #pragma unroll
         for (int jj = 0; jj < B; ++jj) {
             const float4 cur = sc.P[jj][lane];
-            sec_update(st[0], cur.x, cf);
-            sec_update(st[1], cur.y, cf);
-            sec_update(st[2], cur.z, cf);
-            sec_update(st[3], cur.w, cf);
+            sec_update(st[0], make_float2(cur.x, cur.y), cf);
+            sec_update(st[1], make_float2(cur.z, cur.w), cf);
             float cc, ss;
             fir32::phase_cs(sc.f[sub][jj] - a.c0, om_hi, om_lo, cc, ss);
-            float nu = Wk * fmaf(cc, sec_causal_out(st[0], cf), ss * sec_causal_out(st[1], cf));
-            float de = Wk * fmaf(cc, sec_causal_out(st[2], cf), ss * sec_causal_out(st[3], cf));
+            // (num, den) = Wk (c (oA, oC) + s (oB, oD))
+            const float2 nd = __fmul2_rn(W2, __ffma2_rn(make_float2(cc, cc), sec_causal_out(st[0], cf),
+                                                        __fmul2_rn(make_float2(ss, ss),
+                                                                   sec_causal_out(st[1], cf))));
+            float nu = nd.x, de = nd.y;
             reduce_terms<C>(nu, de);
             acc[jj] = first ? make_float2(nu, de)
                             : make_float2(sc.nd[sub][jj].x + nu, sc.nd[sub][jj].y + de);
@@ -381,7 +387,7 @@ k_yvv_cols(YvvArgs a, int launch)
     // the same column before this warp-wide point)
     __syncwarp();
 #pragma unroll
-    for (int q = 0; q < 4; ++q) st[q] = Sec{0.f, 0.f, 0.f};
+    for (int q = 0; q < 2; ++q) st[q] = Sec2{z2, z2, z2};
     fetch(0, false, true);
     for (int c = 0; c < nchunk; ++c) {
         if (c + 1 < nchunk) fetch(c + 1, false, true);
@@ -393,16 +399,14 @@ k_yvv_cols(YvvArgs a, int launch)
 #pragma unroll
         for (int jj = 0; jj < B; ++jj) {
             const float4 cur = sc.P[jj][lane];
-            const float oA = sec_anti_out(st[0], cf), oB = sec_anti_out(st[1], cf);
-            const float oC = sec_anti_out(st[2], cf), oD = sec_anti_out(st[3], cf);
-            sec_update(st[0], cur.x, cf);
-            sec_update(st[1], cur.y, cf);
-            sec_update(st[2], cur.z, cf);
-            sec_update(st[3], cur.w, cf);
+            const float2 oAC = sec_anti_out(st[0], cf), oBD = sec_anti_out(st[1], cf);
+            sec_update(st[0], make_float2(cur.x, cur.y), cf);
+            sec_update(st[1], make_float2(cur.z, cur.w), cf);
             float cc, ss;
             fir32::phase_cs(sc.f[sub][jj] - a.c0, om_hi, om_lo, cc, ss);
-            float nu = Wk * fmaf(cc, oA, ss * oB);
-            float de = Wk * fmaf(cc, oC, ss * oD);
+            const float2 nd = __fmul2_rn(W2, __ffma2_rn(make_float2(cc, cc), oAC,
+                                                        __fmul2_rn(make_float2(ss, ss), oBD)));
+            float nu = nd.x, de = nd.y;
             reduce_terms<C>(nu, de);
             acc[jj] = make_float2(sc.nd[sub][jj].x + nu, sc.nd[sub][jj].y + de);
         }
