@@ -267,23 +267,16 @@ def main():
     import paper_1203_5128_gb300 as bf
     from paper_1203_5128_gb300 import synth
 
+    from paper_1203_5128_gb300.replicas import Replicas
+
     torch.cuda.set_device(local)
-    dist = None
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    reps = Replicas("nccl", torch.device("cuda", local))
 
     def barrier():
-        if dist is not None:
-            dist.barrier()
+        reps.barrier()
         torch.cuda.synchronize()
 
-    def max_over_ranks(x: float) -> float:
-        if dist is None:
-            return x
-        t = torch.tensor([x], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+    max_over_ranks = reps.max
 
     f_np = synth.g8(H, W, seed=SEED)
     f = torch.from_numpy(f_np).cuda()
@@ -439,8 +432,7 @@ def main():
     e2e_value = world * px * e2e_steps / (e2e_s * 1e6)
 
     if rank != 0:
-        if dist is not None:
-            dist.destroy_process_group()
+        reps.close()
         return
 
     # ---- roofline of the dominant kernel: K3-tc (tensor cores, FP16 planes)
@@ -528,8 +520,7 @@ def main():
                      "ms": d_ms},
     }
     print(json.dumps(line), flush=True)
-    if dist is not None:
-        dist.destroy_process_group()
+    reps.close()
 
 
 if __name__ == "__main__":
