@@ -18,8 +18,9 @@
 // conflict-free shared load per lane and the loops carry no branches.  Only
 // the entries the combine reads are kept: suffix maxima on [0, 64) are
 // written first, then the prefix maxima on [2R, 2R+64) are folded in.
-// Per-tile T needs max and min; the image-wide T needs only the max (Prop.
-// 2.1).  The block's largest local range goes to its T word with an
+// Per-tile T needs max and min (each (line, partition) then gives a max item
+// and a min item, run by different threads); the image-wide T needs only the
+// max (Prop. 2.1).  The block's largest local range goes to its T word with an
 // atomicMax on the float's bit pattern (valid: the values are >= 0).
 #include <math.h>
 
@@ -38,56 +39,42 @@ __device__ __forceinline__ float min_operand(float v)
     return v == -INFINITY ? INFINITY : v;
 }
 
-// Suffix maxima of smax[q0..q1) (and minima of smin[q0..q1)), stride `st`
-// between entries, written to dmax / dmin [q * dst_st] for q < lim.
-template <bool kMin>
-__device__ __forceinline__ void suffix_part(const float* smax, const float* smin, int st, int q0,
-                                            int q1, int lim, float* dmax, float* dmin, int dst_st)
+// Suffix maxima (kIsMin: minima) of src[q0..q1), stride `st` between
+// entries, written to dst[q * dst_st] for q < lim.
+template <bool kIsMin>
+__device__ __forceinline__ void suffix_part(const float* src, int st, int q0, int q1, int lim,
+                                            float* dst, int dst_st)
 {
-    float hi = -INFINITY, lo = INFINITY;
+    float acc = kIsMin ? INFINITY : -INFINITY;
     int q = q1 - 1;
     const int qs = min(q1, lim);          // entries below qs are stored
 #pragma unroll 4
-    for (; q >= qs; --q) {
-        hi = fmaxf(hi, smax[q * st]);
-        if (kMin) lo = fminf(lo, min_operand(smin[q * st]));
-    }
+    for (; q >= qs; --q)
+        acc = kIsMin ? fminf(acc, min_operand(src[q * st])) : fmaxf(acc, src[q * st]);
 #pragma unroll 4
     for (; q >= q0; --q) {
-        hi = fmaxf(hi, smax[q * st]);
-        dmax[q * dst_st] = hi;
-        if (kMin) {
-            lo = fminf(lo, min_operand(smin[q * st]));
-            dmin[q * dst_st] = lo;
-        }
+        acc = kIsMin ? fminf(acc, min_operand(src[q * st])) : fmaxf(acc, src[q * st]);
+        dst[q * dst_st] = acc;
     }
 }
 
-// Prefix maxima of smax[q0..qe) (and minima of smin), folded into
-// dmax / dmin [(q - off) * dst_st] for q >= off: the combine
-// max(r[i], l[i + 2R]) of the Appendix.
-template <bool kMin>
-__device__ __forceinline__ void prefix_part(const float* smax, const float* smin, int st, int q0,
-                                            int qe, int off, float* dmax, float* dmin, int dst_st)
+// Prefix maxima (minima) of src[q0..qe), folded into dst[(q - off) * dst_st]
+// for q >= off: the combine max(r[i], l[i + 2R]) of the Appendix.
+template <bool kIsMin>
+__device__ __forceinline__ void prefix_part(const float* src, int st, int q0, int qe, int off,
+                                            float* dst, int dst_st)
 {
-    float hi = -INFINITY, lo = INFINITY;
+    float acc = kIsMin ? INFINITY : -INFINITY;
     int q = q0;
     const int qs = max(q0, off);
 #pragma unroll 4
-    for (; q < qs; ++q) {
-        hi = fmaxf(hi, smax[q * st]);
-        if (kMin) lo = fminf(lo, min_operand(smin[q * st]));
-    }
+    for (; q < qs; ++q)
+        acc = kIsMin ? fminf(acc, min_operand(src[q * st])) : fmaxf(acc, src[q * st]);
 #pragma unroll 4
     for (; q < qe; ++q) {
-        hi = fmaxf(hi, smax[q * st]);
-        float* dm = dmax + (q - off) * dst_st;
-        *dm = fmaxf(*dm, hi);
-        if (kMin) {
-            lo = fminf(lo, min_operand(smin[q * st]));
-            float* dn = dmin + (q - off) * dst_st;
-            *dn = fminf(*dn, lo);
-        }
+        acc = kIsMin ? fminf(acc, min_operand(src[q * st])) : fmaxf(acc, src[q * st]);
+        float* d = dst + (q - off) * dst_st;
+        *d = kIsMin ? fminf(*d, acc) : fmaxf(*d, acc);
     }
 }
 
@@ -134,35 +121,52 @@ __device__ __forceinline__ void range_body(const float* __restrict__ f, size_t p
     __syncthreads();
 
     // ---- rows: suffix parts (partitions meeting [0, kT)), then prefix parts
-    //      (partitions meeting [2R, 2R + kT)); lane = row
+    //      (partitions meeting [2R, 2R + kT)); lane = row.  With the min filter
+    //      the max and min of a (line, partition) are separate items, so that
+    //      every phase spreads over more of the block's threads.
+    constexpr int NF = kMin ? 2 : 1;
     const int pr_hi = (kT - 1) / Wn;              // last partition meeting [0, kT)
     const int pl_lo = (2 * R) / Wn, pl_hi = (2 * R + kT - 1) / Wn;
-    for (int it = threadIdx.x; it < L * (pr_hi + 1); it += kThreads) {
-        const int p = it / L, r = it - p * L;
+    const int nrs = L * (pr_hi + 1);
+    for (int it = threadIdx.x; it < NF * nrs; it += kThreads) {
+        const bool mn_item = kMin && it >= nrs;
+        const int jt = mn_item ? it - nrs : it;
+        const int p = jt / L, r = jt - p * L;
         const int q0 = p * Wn, q1 = min(q0 + Wn, L);
-        suffix_part<kMin>(reg + r * Ls, reg + r * Ls, 1, q0, q1, kT, rmax + r * kTp,
-                          rmin + r * kTp, 1);
+        if (mn_item) suffix_part<true>(reg + r * Ls, 1, q0, q1, kT, rmin + r * kTp, 1);
+        else suffix_part<false>(reg + r * Ls, 1, q0, q1, kT, rmax + r * kTp, 1);
     }
     __syncthreads();
-    for (int it = threadIdx.x; it < L * (pl_hi - pl_lo + 1); it += kThreads) {
-        const int p = pl_lo + it / L, r = it % L;
+    const int nrp = L * (pl_hi - pl_lo + 1);
+    for (int it = threadIdx.x; it < NF * nrp; it += kThreads) {
+        const bool mn_item = kMin && it >= nrp;
+        const int jt = mn_item ? it - nrp : it;
+        const int p = pl_lo + jt / L, r = jt % L;
         const int q0 = p * Wn, qe = min(min(q0 + Wn, L), 2 * R + kT);
-        prefix_part<kMin>(reg + r * Ls, reg + r * Ls, 1, q0, qe, 2 * R, rmax + r * kTp,
-                          rmin + r * kTp, 1);
+        if (mn_item) prefix_part<true>(reg + r * Ls, 1, q0, qe, 2 * R, rmin + r * kTp, 1);
+        else prefix_part<false>(reg + r * Ls, 1, q0, qe, 2 * R, rmax + r * kTp, 1);
     }
     __syncthreads();
 
     // ---- columns of the row result; lane = column
-    for (int it = threadIdx.x; it < kT * (pr_hi + 1); it += kThreads) {
-        const int p = it / kT, c = it % kT;
+    const int ncs = kT * (pr_hi + 1);
+    for (int it = threadIdx.x; it < NF * ncs; it += kThreads) {
+        const bool mn_item = kMin && it >= ncs;
+        const int jt = mn_item ? it - ncs : it;
+        const int p = jt / kT, c = jt % kT;
         const int q0 = p * Wn, q1 = min(q0 + Wn, L);
-        suffix_part<kMin>(rmax + c, rmin + c, kTp, q0, q1, kT, cmax + c, cmin + c, kTp);
+        if (mn_item) suffix_part<true>(rmin + c, kTp, q0, q1, kT, cmin + c, kTp);
+        else suffix_part<false>(rmax + c, kTp, q0, q1, kT, cmax + c, kTp);
     }
     __syncthreads();
-    for (int it = threadIdx.x; it < kT * (pl_hi - pl_lo + 1); it += kThreads) {
-        const int p = pl_lo + it / kT, c = it % kT;
+    const int ncp = kT * (pl_hi - pl_lo + 1);
+    for (int it = threadIdx.x; it < NF * ncp; it += kThreads) {
+        const bool mn_item = kMin && it >= ncp;
+        const int jt = mn_item ? it - ncp : it;
+        const int p = pl_lo + jt / kT, c = jt % kT;
         const int q0 = p * Wn, qe = min(min(q0 + Wn, L), 2 * R + kT);
-        prefix_part<kMin>(rmax + c, rmin + c, kTp, q0, qe, 2 * R, cmax + c, cmin + c, kTp);
+        if (mn_item) prefix_part<true>(rmin + c, kTp, q0, qe, 2 * R, cmin + c, kTp);
+        else prefix_part<false>(rmax + c, kTp, q0, qe, 2 * R, cmax + c, kTp);
     }
     __syncthreads();
     (void)P;
