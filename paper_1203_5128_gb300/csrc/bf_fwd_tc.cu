@@ -27,6 +27,8 @@
 //   warps 4-11  modulate the halo planes of pair k+1 while the tensor core
 //               and warps 0-3 work on pair k;
 //   warp 12     allocates TMEM, issues the MMAs, frees TMEM.
+// The conversion of D1 signals each plane of A2 on a barrier of its own, so
+// the horizontal product of plane p runs while plane p + 1 is converted.
 // Handshakes are mbarriers; every wait is bounded (spin_limit polls) and a
 // wait that runs out sets BF_DEV_TIMEOUT, tells the other roles to stop,
 // lets the tensor core drain (again bounded) and frees TMEM.
@@ -265,12 +267,12 @@ struct TcGeo {
         offA2 = offB1 + 4u * RWp * RHp * 2;
         offPn = offA2 + 4u * planeA2;
         offBar = offPn + TH * kPnStride * 4;
-        bytes = offBar + 64;
+        bytes = offBar + 96;
     }
 };
 
 // barrier slots (8 bytes each) after the operand buffers
-enum { kBarB1Full = 0, kBarC1, kBarA2Full, kBarC2, kBarD2Free, kNumBars };
+enum { kBarB1Full = 0, kBarC1, kBarA2Full, kBarA2F1, kBarA2F2, kBarA2F3, kBarC2, kBarD2Free, kNumBars };
 
 template <bool kBF16, int NCH>
 __global__ void __launch_bounds__(NT, 1) k_fwd_tc(FwdArgs a, long long spin_limit,
@@ -311,7 +313,7 @@ __global__ void __launch_bounds__(NT, 1) k_fwd_tc(FwdArgs a, long long spin_limi
     if (tid == 0) {
         mbar_init(bar(kBarB1Full), kModThreads);
         mbar_init(bar(kBarC1), 1);
-        mbar_init(bar(kBarA2Full), kEpiThreads);
+        for (int pl = 0; pl < 4; ++pl) mbar_init(bar(kBarA2Full + pl), kEpiThreads);
         mbar_init(bar(kBarC2), 1);
         mbar_init(bar(kBarD2Free), kEpiThreads);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -425,17 +427,24 @@ __global__ void __launch_bounds__(NT, 1) k_fwd_tc(FwdArgs a, long long spin_limi
                 }
                 mma_commit(bar(kBarC1));
                 ++issued1;
-                if (!mbar_wait(bar(kBarA2Full), k & 1, spin_limit, stop)) break;
                 if (k > 0 && !mbar_wait(bar(kBarD2Free), (k - 1) & 1, spin_limit, stop)) break;
-                fence_after();
+                // each plane's horizontal product as soon as that plane of A2 is written
+                bool planes_ok = true;
+                for (int pl = 0; pl < 4; ++pl) {
+                    if (!mbar_wait(bar(kBarA2Full + pl), k & 1, spin_limit, stop)) { planes_ok = false; break; }
+                    fence_after();
 #pragma unroll
-                for (int ks = 0; ks < NCH; ++ks) {
-                    const uint64_t db = sdesc(sbase + G.offB2 + ks * 256, 128, 128);
-                    for (int pl = 0; pl < 4; ++pl) {
+                    for (int ks = 0; ks < NCH; ++ks) {
+                        const uint64_t db = sdesc(sbase + G.offB2 + ks * 256, 128, 128);
                         const uint64_t da = sdesc(sbase + G.offA2 + pl * G.planeA2 + ks * 256, 128,
                                                   G.sboA2);
                         mma_f16(tD2 + pl * TW, da, db, idesc2, ks > 0);
                     }
+                }
+                if (!planes_ok) {
+                    mma_commit(bar(kBarC2));      // so that the drain below waits for them
+                    ++issued2;
+                    break;
                 }
                 mma_commit(bar(kBarC2));
                 ++issued2;
@@ -494,10 +503,10 @@ __global__ void __launch_bounds__(NT, 1) k_fwd_tc(FwdArgs a, long long spin_limi
                         store_row8<kBF16>(dst + 384, v + 24);
                     }
                 }
+                fence_async_smem();
+                fence_before();
+                mbar_arrive(bar(kBarA2Full + pl));
             }
-            fence_async_smem();
-            fence_before();
-            mbar_arrive(bar(kBarA2Full));
             // D2 ready: demodulate (eqs. (f1), (f2)); TMEM column n is x = 31 - n
             if (!mbar_wait_warp(bar(kBarC2), k & 1, spin_limit, stop)) { ok = false; break; }
             fence_after();
