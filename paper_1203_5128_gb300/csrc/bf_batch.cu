@@ -179,6 +179,7 @@ bf_status build_state(int n, const bf_plan_t* plans, const float* const* f, floa
     std::vector<std::vector<std::pair<double, int4>>> citems;
     std::vector<int> cmaxR;
     int maxR_range = 0;
+    bool range_min = false;          // some image has per-tile T: the min filter runs
     std::vector<unsigned*> zero_T;
     std::vector<int> zero_n;
     std::vector<unsigned long long*> zero_g;
@@ -200,6 +201,7 @@ bf_status build_state(int n, const bf_plan_t* plans, const float* const* f, floa
                 for (int bx = 0; bx < p->W; bx += range_tile())
                     ritems.push_back(make_int4(ri, by, bx, 0));
             maxR_range = std::max(maxR_range, p->R);
+            range_min = range_min || g.set_tile != 0;
             zero_T.push_back(p->d_T);
             zero_n.push_back(p->n_sets);
         }
@@ -320,7 +322,7 @@ bf_status build_state(int n, const bf_plan_t* plans, const float* const* f, floa
         if (e == cudaSuccess && !ritems.empty())
             e = launch_local_range_batch(reinterpret_cast<const RangeImg*>(d + oR),
                                          reinterpret_cast<const int4*>(d + oRI),
-                                         (int)ritems.size(), maxR_range,
+                                         (int)ritems.size(), maxR_range, range_min,
                                          std::min<int>((int)ritems.size(), 4 * sms), cs);
         if (e == cudaSuccess)
             e = launch_params_batch(reinterpret_cast<const ParamsArgs*>(d + oP),

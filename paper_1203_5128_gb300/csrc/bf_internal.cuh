@@ -251,7 +251,7 @@ struct RangeImg {
 int range_tile();
 size_t range_smem_bytes(int R);
 cudaError_t launch_local_range_batch(const RangeImg* imgs, const int4* items, int n_items,
-                                     int max_R, int n_ctas, cudaStream_t s);
+                                     int max_R, bool with_min, int n_ctas, cudaStream_t s);
 cudaError_t launch_params_batch(const ParamsArgs* imgs, const int* block_img, const int* block_set,
                                 int n_blocks, cudaStream_t s);
 cudaError_t launch_fwd32_persistent(int th, int tw, int max_R, const FwdArgs* imgs,

@@ -212,9 +212,9 @@ k_local_range(const float* __restrict__ f, size_t pitch, int H, int W, int R, in
                               blockIdx.y * kT, blockIdx.x * kT, sm, red);
 }
 
-// Batched: CTAs stride over (image, block row, block column) items.  Max and
-// min are both computed, which leaves the image-wide T unchanged (Prop. 2.1:
-// max (M - f) and max (f - m) over the image are equal).
+// Batched: CTAs stride over (image, block row, block column) items; the min
+// filter runs for images with per-tile T only (Prop. 2.1: the image-wide T
+// needs the max filter alone).
 __global__ void __launch_bounds__(kThreads)
 k_local_range_batch(const RangeImg* __restrict__ imgs, const int4* __restrict__ items, int n_items)
 {
@@ -224,8 +224,12 @@ k_local_range_batch(const RangeImg* __restrict__ imgs, const int4* __restrict__ 
         const int4 it = items[i];
         const RangeImg g = imgs[it.x];
         __syncthreads();
-        range_body<true, false>(g.f, g.pitch, g.H, g.W, g.R, g.set_tile, g.sets_x, g.Tbits,
-                                nullptr, nullptr, it.y, it.z, sm, red);
+        if (g.set_tile)
+            range_body<true, false>(g.f, g.pitch, g.H, g.W, g.R, g.set_tile, g.sets_x, g.Tbits,
+                                    nullptr, nullptr, it.y, it.z, sm, red);
+        else
+            range_body<false, false>(g.f, g.pitch, g.H, g.W, g.R, 0, 1, g.Tbits, nullptr, nullptr,
+                                     it.y, it.z, sm, red);
     }
 }
 
@@ -258,9 +262,9 @@ int range_tile() { return kT; }
 size_t range_smem_bytes(int R) { return range_smem(R, true); }
 
 cudaError_t launch_local_range_batch(const RangeImg* imgs, const int4* items, int n_items,
-                                     int max_R, int n_ctas, cudaStream_t s)
+                                     int max_R, bool with_min, int n_ctas, cudaStream_t s)
 {
-    const size_t smem = range_smem(max_R, true);
+    const size_t smem = range_smem(max_R, with_min);
     cudaError_t e = cudaFuncSetAttribute(k_local_range_batch,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
