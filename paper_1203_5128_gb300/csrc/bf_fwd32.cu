@@ -243,58 +243,70 @@ __device__ __forceinline__ void fwd32t_body(const FwdArgs& a, const fir32::Taps&
     fir32::PhaseSteps<PS, 0, PS::ITERS>::run(ps, fz, cs, a.H, om_hi, om_lo);
     __syncthreads();
 
+    // sweep row m of this thread is in the halo (the last row block may overhang)
+    auto sweep_row = [&](int m) {
+        return ps.on && (m < PS::ITERS - 1 || ps.r0 + PS::S * m < G::RH);
+    };
+    // column pass of the row-filtered pair with job(m), m = ch * PPS + u, run
+    // between its input steps
+    auto col_pass_with = [&](float2 (&acc)[CO], auto&& job) {
+#pragma unroll
+        for (int i = 0; i < CO; ++i) acc[i] = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int ch = 0; ch < NS; ++ch) {
+            float2 v[8];
+#pragma unroll
+            for (int j = 0; j < 8; ++j) v[j] = hz[fir32::hz_at(rb * CO + ch * 8 + j, o)];
+            fir32::fir_x2<CO, 8, Rp>(acc, tp2, ch * 8, v);
+#pragma unroll
+            for (int u = 0; u < PPS; ++u)
+                if (ch * PPS + u < PS::ITERS) job(ch * PPS + u);
+        }
+    };
+
     for (int k = 0; k < K; ++k) {
-        // numerator pair (f' c, f' s)
-        fir32::row_pass_x2<TH, TW, NCH, NT, true>(tp2, cs, fz, hz, tid);
+        // denominator pair (c, s); cos / sin at my outputs kept for both
+        // demodulations, read before cs is rescaled
+        fir32::row_pass_x2<TH, TW, NCH, NT, false>(tp2, cs, fz, hz, tid);
+        float2 cc[CO];
+#pragma unroll
+        for (int i = 0; i < CO; ++i) cc[i] = cs[(rb * CO + i + Rp) * G::CSp + o + Rp];
         __syncthreads();
         {
-            float2 nab[CO];
-            fir32::col_pass_x2<TH, TW, NCH, CO>(tp2, hz, o, rb, nab);
+            // during the column pass: (c, s) -> (f'c, f's) in place, once per pixel
+            float2 dcd[CO];
+            col_pass_with(dcd, [&](int m) {
+                if (sweep_row(m)) {
+                    const int ci = ps.cbase + PS::S * m * G::CSp;
+                    const float fv = fz[ps.fbase + PS::S * m * G::FP];
+                    cs[ci] = __fmul2_rn(make_float2(fv, fv), cs[ci]);
+                }
+            });
 #pragma unroll
-            for (int i = 0; i < CO; ++i) {
-                const float2 cc = cs[(rb * CO + i + Rp) * G::CSp + o + Rp];
-                num[i] = fmaf(Wk, fmaf(cc.x, nab[i].x, cc.y * nab[i].y), num[i]);
-            }
+            for (int i = 0; i < CO; ++i)
+                den[i] = fmaf(Wk, fmaf(cc[i].x, dcd[i].x, cc[i].y * dcd[i].y), den[i]);
         }
         __syncthreads();
-        // denominator pair (c, s)
+        // numerator pair (f'c, f's), already formed
         fir32::row_pass_x2<TH, TW, NCH, NT, false>(tp2, cs, fz, hz, tid);
         __syncthreads();
         {
+            // during the column pass: the phases of pair k + 1 into cs
             const bool next = k + 1 < K;
             float nx_hi, nx_lo, nW;
             pair_of(k + 1, nx_hi, nx_lo, nW);
-            float2 dcd[CO];
-#pragma unroll
-            for (int i = 0; i < CO; ++i) dcd[i] = make_float2(0.f, 0.f);
-#pragma unroll
-            for (int ch = 0; ch < NS; ++ch) {
-                float2 v[8];
-#pragma unroll
-                for (int j = 0; j < 8; ++j) v[j] = hz[fir32::hz_at(rb * CO + ch * 8 + j, o)];
-                fir32::fir_x2<CO, 8, Rp>(dcd, tp2, ch * 8, v);
-                if (next) {
-#pragma unroll
-                    for (int u = 0; u < PPS; ++u) {
-                        const int m = ch * PPS + u;
-                        if (m < PS::ITERS) {
-                            float c, sn;
-                            if (ps.on && (m < PS::ITERS - 1 || ps.r0 + PS::S * m < G::RH)) {
-                                phase_cs(fz[ps.fbase + PS::S * m * G::FP], nx_hi, nx_lo, c, sn);
-                                const bool in = ps.x_in && (unsigned)(ps.gyb + PS::S * m) < (unsigned)a.H;
-                                cs[ps.cbase + PS::S * m * G::CSp] =
-                                    in ? make_float2(c, sn) : make_float2(0.f, 0.f);
-                            }
-                        }
-                    }
+            float2 nab[CO];
+            col_pass_with(nab, [&](int m) {
+                if (next && sweep_row(m)) {
+                    float c, sn;
+                    phase_cs(fz[ps.fbase + PS::S * m * G::FP], nx_hi, nx_lo, c, sn);
+                    const bool in = ps.x_in && (unsigned)(ps.gyb + PS::S * m) < (unsigned)a.H;
+                    cs[ps.cbase + PS::S * m * G::CSp] = in ? make_float2(c, sn) : make_float2(0.f, 0.f);
                 }
-            }
+            });
 #pragma unroll
-            for (int i = 0; i < CO; ++i) {
-                float c, sn;
-                phase_cs(fz[(rb * CO + i + Rp) * G::FP + o + Rp], om_hi, om_lo, c, sn);
-                den[i] = fmaf(Wk, fmaf(c, dcd[i].x, sn * dcd[i].y), den[i]);
-            }
+            for (int i = 0; i < CO; ++i)
+                num[i] = fmaf(Wk, fmaf(cc[i].x, nab[i].x, cc[i].y * nab[i].y), num[i]);
             om_hi = nx_hi;
             om_lo = nx_lo;
             Wk = nW;
