@@ -217,21 +217,6 @@ __device__ __forceinline__ int hz_at(int r, int x)
     return r * 32 + ((((x >> 1) ^ (r & 7)) << 1) | (x & 1));
 }
 
-// One 8x8 step of an 8-output FIR block: acc[i] += g[j - i + 7] * v[j] for
-// the (j, i) allowed by kPart (0 full, 1 lower triangle j >= i, 2 upper j <= i).
-template <int kPart>
-__device__ __forceinline__ void fir_step(float (&acc)[8], const float (&g)[15], const float (&v)[8])
-{
-#pragma unroll
-    for (int j = 0; j < 8; ++j)
-#pragma unroll
-        for (int i = 0; i < 8; ++i) {
-            if (kPart == 1 && j < i) continue;
-            if (kPart == 2 && j > i) continue;
-            acc[i] = fmaf(g[j - i + 7], v[j], acc[i]);
-        }
-}
-
 // One input step on pairs: acc[i] += g(d - Rp) v[j] with d = s0 + j - i, for
 // the (j, i) whose d lies in [0, 2 Rp]; s0 is a compile-time constant after
 // unrolling, so the window test costs nothing and tp.g[d + 8] is a constant-
@@ -250,11 +235,10 @@ __device__ __forceinline__ void fir_x2(float2 (&acc)[NO], const Taps2& tp, int s
         }
 }
 
-// Row FIR of NO consecutive outputs (NO = 4 or 8) of the pair (m c, m s),
-// m = f (kNum) or 1: inputs src[0 .. NO + 2 Rp), in steps of NO.
-template <int NO, int NCH, bool kNum>
-__device__ __forceinline__ void row_item_x2(const Taps2& tp, const float2* src, const float* fr,
-                                            float2 (&acc)[NO])
+// Row FIR of NO consecutive outputs (NO = 4 or 8) of a pair plane: inputs
+// src[0 .. NO + 2 Rp), in steps of NO.
+template <int NO, int NCH>
+__device__ __forceinline__ void row_item_x2(const Taps2& tp, const float2* src, float2 (&acc)[NO])
 {
     constexpr int Rp = 4 * (NCH - 1), NS = (NO + 2 * Rp) / NO;
 #pragma unroll
@@ -268,28 +252,17 @@ __device__ __forceinline__ void row_item_x2(const Taps2& tp, const float2* src, 
             v[2 * q] = make_float2(w.x, w.y);
             v[2 * q + 1] = make_float2(w.z, w.w);
         }
-        if (kNum) {
-#pragma unroll
-            for (int q = 0; q < NO / 4; ++q) {
-                const float4 m = *(const float4*)(fr + st * NO + 4 * q);
-                v[4 * q] = __fmul2_rn(make_float2(m.x, m.x), v[4 * q]);
-                v[4 * q + 1] = __fmul2_rn(make_float2(m.y, m.y), v[4 * q + 1]);
-                v[4 * q + 2] = __fmul2_rn(make_float2(m.z, m.z), v[4 * q + 2]);
-                v[4 * q + 3] = __fmul2_rn(make_float2(m.w, m.w), v[4 * q + 3]);
-            }
-        }
         fir_x2<NO, NO, Rp>(acc, tp, st * NO, v);
     }
 }
 
-// Row pass of the pair into the swizzled hz.  The first NT-multiple of the
+// Row pass of a pair plane into the swizzled hz.  The first NT-multiple of the
 // RH x 4 items (halo row r, 8-column block) runs as 8-output items, the
 // eight rows of a quarter-warp consecutive; the rest, fewer than NT items,
 // runs as twice as many 4-output items in one round, so that the last round
 // takes half as long.
-template <int TH, int TW, int NCH, int NT, bool kNum>
-__device__ __forceinline__ void row_pass_x2(const Taps2& tp, const float2* cs, const float* fz,
-                                            float2* hz, int tid)
+template <int TH, int TW, int NCH, int NT>
+__device__ __forceinline__ void row_pass_x2(const Taps2& tp, const float2* cs, float2* hz, int tid)
 {
     using G = TallGeo<TH, TW, NCH>;
     constexpr int kItems = G::RH * (TW / 8);
@@ -299,7 +272,7 @@ __device__ __forceinline__ void row_pass_x2(const Taps2& tp, const float2* cs, c
     for (int it = tid; it < kFull; it += NT) {
         const int cb = (it >> 3) & 3, r = (it & 7) + ((it >> 5) << 3);
         float2 acc[8];
-        row_item_x2<8, NCH, kNum>(tp, cs + r * G::CSp + cb * 8, fz + r * G::FP + cb * 8, acc);
+        row_item_x2<8, NCH>(tp, cs + r * G::CSp + cb * 8, acc);
 #pragma unroll
         for (int q = 0; q < 4; ++q)
             *(float4*)(hz + hz_at(r, cb * 8 + 2 * q)) =
@@ -308,29 +281,11 @@ __device__ __forceinline__ void row_pass_x2(const Taps2& tp, const float2* cs, c
     if (tid < kHalf) {
         const int r = kFull / 4 + (tid & 7) + ((tid >> 6) << 3), x0 = ((tid >> 3) & 7) * 4;
         float2 acc[4];
-        row_item_x2<4, NCH, kNum>(tp, cs + r * G::CSp + x0, fz + r * G::FP + x0, acc);
+        row_item_x2<4, NCH>(tp, cs + r * G::CSp + x0, acc);
 #pragma unroll
         for (int q = 0; q < 2; ++q)
             *(float4*)(hz + hz_at(r, x0 + 2 * q)) =
                 make_float4(acc[2 * q].x, acc[2 * q].y, acc[2 * q + 1].x, acc[2 * q + 1].y);
-    }
-}
-
-// Column pass of the pair for one item: column o, output rows rb*CO .. rb*CO+CO-1,
-// input rows in steps of 8; tap d = input - output + Rp.
-template <int TH, int TW, int NCH, int CO>
-__device__ __forceinline__ void col_pass_x2(const Taps2& tp, const float2* hz, int o, int rb,
-                                            float2 (&acc)[CO])
-{
-    constexpr int Rp = 4 * (NCH - 1), NS = (CO + 2 * Rp) / 8;
-#pragma unroll
-    for (int i = 0; i < CO; ++i) acc[i] = make_float2(0.f, 0.f);
-#pragma unroll
-    for (int ch = 0; ch < NS; ++ch) {
-        float2 v[8];
-#pragma unroll
-        for (int j = 0; j < 8; ++j) v[j] = hz[hz_at(rb * CO + ch * 8 + j, o)];
-        fir_x2<CO, 8, Rp>(acc, tp, ch * 8, v);
     }
 }
 

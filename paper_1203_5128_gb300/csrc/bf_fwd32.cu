@@ -267,7 +267,7 @@ __device__ __forceinline__ void fwd32t_body(const FwdArgs& a, const fir32::Taps&
     for (int k = 0; k < K; ++k) {
         // denominator pair (c, s); cos / sin at my outputs kept for both
         // demodulations, read before cs is rescaled
-        fir32::row_pass_x2<TH, TW, NCH, NT, false>(tp2, cs, fz, hz, tid);
+        fir32::row_pass_x2<TH, TW, NCH, NT>(tp2, cs, hz, tid);
         float2 cc[CO];
 #pragma unroll
         for (int i = 0; i < CO; ++i) cc[i] = cs[(rb * CO + i + Rp) * G::CSp + o + Rp];
@@ -288,7 +288,7 @@ __device__ __forceinline__ void fwd32t_body(const FwdArgs& a, const fir32::Taps&
         }
         __syncthreads();
         // numerator pair (f'c, f's), already formed
-        fir32::row_pass_x2<TH, TW, NCH, NT, false>(tp2, cs, fz, hz, tid);
+        fir32::row_pass_x2<TH, TW, NCH, NT>(tp2, cs, hz, tid);
         __syncthreads();
         {
             // during the column pass: the phases of pair k + 1 into cs
