@@ -275,8 +275,9 @@ bf_status bf_plan(int H, int W, double sigma_s, double sigma_r, double eps, cons
         tw = 32;
     } else if (o.plane_dtype == BF_PLANES_FP32) {
         fwd32_tile(R, &th, &tw);
-        if (fwd32t_ok(R, o.t_mode == BF_T_TILE ? o.t_tile : 0)) {
-            th = 128;
+        const int st = o.t_mode == BF_T_TILE ? o.t_tile : 0;
+        if (fwd32t_ok(R, st)) {
+            th = fwd32t_rows(st);
             tw = 32;
         }
     } else if (R <= fwd_tc_max_radius()) {

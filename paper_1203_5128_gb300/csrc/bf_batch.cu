@@ -145,7 +145,8 @@ bf_status build_state(int n, const bf_plan_t* plans, const float* const* f, floa
     for (int i = 0; i < n; ++i) {
         bf_plan_s* p = plans[i];
         const int set_tile = p->opt.t_mode == BF_T_TILE ? p->set_tile : 0;
-        const long long tall_ctas = (long long)((p->H + 127) / 128) * ((p->W + 31) / 32);
+        const int rows = fwd32t_rows(set_tile) > 0 ? fwd32t_rows(set_tile) : 128;
+        const long long tall_ctas = (long long)((p->H + rows - 1) / rows) * ((p->W + 31) / 32);
         two_pass[i] = (p->d_sep_P && set_tile == 0 && !fwd32t_ok(p->R, 0) && sep32_ok(p->R)) ||
                       (fwd32t_ok(p->R, set_tile) && 4 * tall_ctas >= sms0);
     }

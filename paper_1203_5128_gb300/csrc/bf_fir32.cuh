@@ -258,18 +258,20 @@ __device__ __forceinline__ void row_item_x2(const Taps2& tp, const float2* src, 
 
 // Row pass of a pair plane into the swizzled hz.  The first NT-multiple of the
 // RH x 4 items (halo row r, 8-column block) runs as 8-output items, the
-// eight rows of a quarter-warp consecutive; the rest, fewer than NT items,
-// runs as twice as many 4-output items in one round, so that the last round
-// takes half as long.
+// eight rows of a quarter-warp consecutive; the rest runs, when it fits one
+// round that way, as twice as many 4-output items (the last round then takes
+// half as long), else as 8-output items too.
 template <int TH, int TW, int NCH, int NT>
 __device__ __forceinline__ void row_pass_x2(const Taps2& tp, const float2* cs, float2* hz, int tid)
 {
     using G = TallGeo<TH, TW, NCH>;
     constexpr int kItems = G::RH * (TW / 8);
     constexpr int kFull = kItems / NT * NT;
-    constexpr int kHalf = 2 * (kItems - kFull);
-    static_assert(kFull % 32 == 0 && kHalf <= NT && (kHalf % 64) == 0, "row pass split");
-    for (int it = tid; it < kFull; it += NT) {
+    constexpr bool kSplit = 2 * (kItems - kFull) <= NT;
+    constexpr int kMain = kSplit ? kFull : kItems;
+    constexpr int kHalf = kSplit ? 2 * (kItems - kFull) : 0;
+    static_assert(kItems % 32 == 0 && kFull % 32 == 0, "row pass items");
+    for (int it = tid; it < kMain; it += NT) {
         const int cb = (it >> 3) & 3, r = (it & 7) + ((it >> 5) << 3);
         float2 acc[8];
         row_item_x2<8, NCH>(tp, cs + r * G::CSp + cb * 8, acc);
@@ -278,7 +280,7 @@ __device__ __forceinline__ void row_pass_x2(const Taps2& tp, const float2* cs, f
             *(float4*)(hz + hz_at(r, cb * 8 + 2 * q)) =
                 make_float4(acc[2 * q].x, acc[2 * q].y, acc[2 * q + 1].x, acc[2 * q + 1].y);
     }
-    if (tid < kHalf) {
+    if (kHalf > 0 && tid < kHalf) {
         const int r = kFull / 4 + (tid & 7) + ((tid >> 6) << 3), x0 = ((tid >> 3) & 7) * 4;
         float2 acc[4];
         row_item_x2<4, NCH>(tp, cs + r * G::CSp + x0, acc);

@@ -340,17 +340,26 @@ k_fwd32t(FwdArgs a, const __grid_constant__ fir32::Taps tp, const __grid_constan
     fwd32t_body<TH, TW, NCH>(a, tp, tp2, blockIdx.y * TH, blockIdx.x * TW, smc);
 }
 
+template <int TH, int NCH>
+cudaError_t launch_tall_th(const FwdArgs& a, const fir32::Taps& tp, const fir32::Taps2& tp2,
+                           cudaStream_t s)
+{
+    constexpr size_t smem = fir32::TallGeo<TH, 32, NCH>::bytes;
+    cudaError_t e = cudaFuncSetAttribute(k_fwd32t<TH, 32, NCH>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    dim3 grid((a.W + 31) / 32, (a.H + TH - 1) / TH);
+    k_fwd32t<TH, 32, NCH><<<grid, TH * 4, smem, s>>>(a, tp, tp2);
+    return cudaGetLastError();
+}
+
+// 128-row tiles, or 64-row tiles where the T-tiles are 64 (not 128) rows high.
 template <int NCH>
 cudaError_t launch_tall(const FwdArgs& a, const fir32::Taps& tp, const fir32::Taps2& tp2,
                         cudaStream_t s)
 {
-    constexpr size_t smem = fir32::TallGeo<128, 32, NCH>::bytes;
-    cudaError_t e = cudaFuncSetAttribute(k_fwd32t<128, 32, NCH>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    dim3 grid((a.W + 31) / 32, (a.H + 127) / 128);
-    k_fwd32t<128, 32, NCH><<<grid, 512, smem, s>>>(a, tp, tp2);
-    return cudaGetLastError();
+    if (fwd32t_rows(a.set_tile) == 64) return launch_tall_th<64, NCH>(a, tp, tp2, s);
+    return launch_tall_th<128, NCH>(a, tp, tp2, s);
 }
 
 template <int TH, int TW>
@@ -457,26 +466,38 @@ cudaError_t launch_fwd32_persistent(int th, int tw, int max_R, const FwdArgs* im
     return e;
 }
 
-size_t fwd32t_smem(int R)
+// Output rows of the tall tile for T-tiles of set_tile rows (0: one set):
+// the tile must nest inside a T-tile.
+int fwd32t_rows(int set_tile)
 {
-    switch ((R + 3) / 4 + 1) {
-        case 2: return fir32::TallGeo<128, 32, 2>::bytes;
-        case 3: return fir32::TallGeo<128, 32, 3>::bytes;
-        case 4: return fir32::TallGeo<128, 32, 4>::bytes;
-        case 5: return fir32::TallGeo<128, 32, 5>::bytes;
-        case 6: return fir32::TallGeo<128, 32, 6>::bytes;
-        case 7: return fir32::TallGeo<128, 32, 7>::bytes;
-        default: return (size_t)-1;
-    }
+    if (set_tile == 0 || set_tile % 128 == 0) return 128;
+    if (set_tile % 64 == 0) return 64;
+    return 0;
 }
 
-// The 128 x 32 tall tile serves a launch when its padded radius has a
-// compiled tap count, its shared memory fits and its tiles nest inside the
-// T-tiles.
+size_t fwd32t_smem(int R, int rows)
+{
+#define BF_TALL_SMEM(N_)                                                                 \
+    case N_: return rows == 64 ? fir32::TallGeo<64, 32, N_>::bytes : fir32::TallGeo<128, 32, N_>::bytes;
+    switch ((R + 3) / 4 + 1) {
+        BF_TALL_SMEM(2)
+        BF_TALL_SMEM(3)
+        BF_TALL_SMEM(4)
+        BF_TALL_SMEM(5)
+        BF_TALL_SMEM(6)
+        BF_TALL_SMEM(7)
+        default: return (size_t)-1;
+    }
+#undef BF_TALL_SMEM
+}
+
+// The tall tile serves a launch when its padded radius has a compiled tap
+// count, its shared memory fits and its tiles nest inside the T-tiles.
 bool fwd32t_ok(int R, int set_tile)
 {
-    return R >= 1 && (R + 3) / 4 * 4 <= fir32::kTapsMaxRp && fwd32t_smem(R) <= kSmemLimit &&
-           (set_tile == 0 || set_tile % 128 == 0);
+    const int rows = fwd32t_rows(set_tile);
+    return R >= 1 && (R + 3) / 4 * 4 <= fir32::kTapsMaxRp && rows > 0 &&
+           fwd32t_smem(R, rows) <= kSmemLimit;
 }
 
 cudaError_t launch_fwd32(const FwdArgs& a, cudaStream_t s)

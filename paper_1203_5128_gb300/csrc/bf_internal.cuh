@@ -174,7 +174,8 @@ cudaError_t launch_sep32(const SepArgs& a, int n_terms_cap, cudaStream_t s);
 // Output tile of the FP32 kernel for a given R (0 if unsupported).
 void fwd32_tile(int R, int* th, int* tw);
 size_t fwd32_smem(int R, int th, int tw);
-bool fwd32t_ok(int R, int set_tile);   // the 128 x 32 tall tile serves this launch
+bool fwd32t_ok(int R, int set_tile);   // the tall tile serves this launch
+int fwd32t_rows(int set_tile);         // its output rows (128, or 64 for 64-row T-tiles)
 cudaError_t launch_fwd32(const FwdArgs& a, cudaStream_t s);
 
 // K5 (adjoint, FP32 planes, FIR): needs the forward's out and den images.

@@ -100,6 +100,8 @@ SMALL = [
     (90, 70, 1.2, 20.0, 0.01, "global", "alg2", 64, 255.0, None),       # R = 4: 2 steps
     (150, 130, 6.0, 30.0, 0.01, "global", "alg2", 64, 255.0, None),     # R = 18: 6 steps
     (300, 100, 7.5, 25.0, 0.01, "tile", "alg2", 128, 255.0, None),      # R = 23: 7 steps, per-tile T
+    (200, 150, 7.5, 25.0, 0.01, "tile", "alg2", 64, 255.0, None),       # 64-row tall tile, 7 steps
+    (150, 90, 3.5, 20.0, 0.01, "tile", "alg2", 64, 255.0, None),        # 64-row tall tile, R = 11
 ]
 
 
