@@ -206,6 +206,23 @@ def test_accelerated_1024_sampled(bf, ss, sr, mode):
     assert err <= TOL8, "max-abs %.3g gray levels" % err
 
 
+@pytest.mark.parametrize("tile", [128, 64])
+def test_tuned_fp32_4096_sampled(bf, tile):
+    """The FP32 tuned form at full size: 4096^2 G8, sigma_s = 8, sigma_r =
+    10, Algorithm 2 with eps = 1e-2, exact T per tile x tile T-tile (the
+    128-row tall tile for tile = 128, the 64-row one for tile = 64); every
+    T-tile's (T, N, M) equals the oracle's, and the output at sampled pixels
+    (random, corners, borders, T-tile seams) is within the FP32 bar."""
+    f = synth.g8(4096, 4096, seed=5)
+    plan, out, p = run(bf, f, 8.0, 10.0, 0.01, "tile", "alg2", tile)
+    assert bf.bf_get_info(plan).tile_h == tile
+    ys, xs = sample_points(4096, 4096, 150, seed=40 + tile, tile=tile, R=p.R)
+    ref = oracle.direct(f, 8.0, 10.0, p, points=(ys, xs))
+    err = np.max(np.abs(out[ys, xs] - ref))
+    print("fp32 tuned 4096^2, %d-row T-tiles: max-abs %.2e gray levels" % (tile, err))
+    assert err <= TOL8
+
+
 def test_plain_1024_sampled(bf):
     """1024^2 G8, the unaccelerated method: T = 255, no truncation."""
     f = synth.g8(1024, 1024, seed=1)
