@@ -38,6 +38,10 @@ TUNED_FP32 = dict(t_mode="tile", t_tile=128, trunc_rule="alg2", plane_dtype="fp3
 TUNED_YVV = dict(t_mode="global", trunc_rule="alg2", plane_dtype="fp32", filter="yvv")
 PLAIN = dict(t_mode="fixed", t_fixed=255.0, trunc_rule="alg2", plane_dtype="fp32", filter="fir")
 SM_COUNT_NOMINAL = 152
+# DRAM bytes of one k_fwd_tc launch on the tuned 4096^2 workload, read + write,
+# from an ncu capture of the kernel as built (67.76 MB + 25.98 MB); set to None
+# whenever the kernel changes until it is captured again
+K3TC_DRAM_BYTES = 67755520 + 25984512
 FP32_LANES_PER_SM = 128
 
 
@@ -447,7 +451,9 @@ def main():
                           TUNED.get("t_tile", 64))
     achieved = flops / (k3_ms * 1e-3) / 1e12
     roof = {"bound": "tensor", "achieved": achieved, "peak": peak_tc, "unit": "TFLOP/s",
-            "frac": achieved / peak_tc, "traffic": None,
+            "frac": achieved / peak_tc, "traffic": K3TC_DRAM_BYTES,
+            "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum, one launch of "
+                              "this kernel on this workload (bytes per launch)",
             "kernel": "k_fwd_tc<fp16> (modulate / tcgen05 Toeplitz FIR / demodulate)",
             "peak_source": "%s bf16_tflops (FP16 and BF16 share the dense tensor rate)" % pk_kind,
             "algorithmic_flops_per_launch": flops,
