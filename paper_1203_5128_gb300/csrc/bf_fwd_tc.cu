@@ -21,12 +21,15 @@
 // read with both descriptor strides equal to 128 bytes, stands for the whole
 // matrix (6 KB instead of 50 KB of shared memory).
 //
-// Roles (416 threads, one CTA per SM):
+// Roles (512 threads, one CTA per SM):
 //   warps 0-3   TMEM lane quarters: D1 -> V (shared), then D2 -> demodulate
 //               into num / den registers (their output row), normalise, store;
-//   warps 4-11  modulate the halo planes of pair k+1 while the tensor core
+//   warps 4-14  modulate the halo planes of pair k+1 while the tensor core
 //               and warps 0-3 work on pair k;
-//   warp 12     allocates TMEM, issues the MMAs, frees TMEM.
+//   warp 15     allocates TMEM, issues the MMAs, frees TMEM.
+// Eleven modulation warps split the 80 x 22 (column, 8-row block) items of the
+// R = 24 halo evenly, five per thread; with 16 warps the SM's register file
+// gives each thread 128 registers.
 // The conversion of D1 signals each plane of A2 on a barrier of its own, so
 // the horizontal product of plane p runs while plane p + 1 is converted.
 // Handshakes are mbarriers; every wait is bounded (spin_limit polls) and a
@@ -48,11 +51,11 @@ namespace {
 constexpr int TH = 128;          // output rows per tile = MMA M
 constexpr int TW = 32;           // output columns per tile
 constexpr int kEpiWarps = 4;
-constexpr int kModWarps = 8;
-constexpr int NT = (kEpiWarps + kModWarps + 1) * 32;   // 416
+constexpr int kModWarps = 11;
+constexpr int NT = (kEpiWarps + kModWarps + 1) * 32;   // 512
 constexpr int kModThreads = kModWarps * 32;
 constexpr int kEpiThreads = kEpiWarps * 32;
-constexpr int kMaxItems = 7;     // modulation items per thread (R <= 24)
+constexpr int kMaxItems = 5;     // modulation items per thread (R <= 24)
 constexpr int kTmemCols = 512;
 constexpr int kPnStride = TW + 1;   // fp32 words per row of the output pixels' scaled f
 
