@@ -22,8 +22,9 @@
 // matrix (6 KB instead of 50 KB of shared memory).
 //
 // Roles (512 threads, one CTA per SM):
-//   warps 0-3   TMEM lane quarters: D1 -> V (shared), then D2 -> demodulate
-//               into num / den registers (their output row), normalise, store;
+//   warps 0-3   TMEM lane quarters: D1 -> V (shared, one TMEM wait per plane),
+//               then D2 -> demodulate into num / den (their output row, kept
+//               in the 64 TMEM columns after D2), normalise, store;
 //   warps 4-14  modulate the halo planes of pair k+1 while the tensor core
 //               and warps 0-3 work on pair k;
 //   warp 15     allocates TMEM, issues the MMAs, frees TMEM.
@@ -218,6 +219,101 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v)
 }
 
 // Eight columns from each of four TMEM column ranges (one wait).
+
+// TMEM loads of this thread's lane, several per wait (outputs only after it)
+__device__ __forceinline__ void tmem_ld_48(uint32_t t0, uint32_t t1, float* v)
+{
+    uint32_t r[48];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%48];\n\t"
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%32,%33,%34,%35,%36,%37,%38,%39,%40,%41,%42,%43,%44,%45,%46,%47}, [%49];\n\t"
+        "tcgen05.wait::ld.sync.aligned;"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31]), "=r"(r[32]), "=r"(r[33]), "=r"(r[34]), "=r"(r[35]), "=r"(r[36]), "=r"(r[37]), "=r"(r[38]), "=r"(r[39]), "=r"(r[40]), "=r"(r[41]), "=r"(r[42]), "=r"(r[43]), "=r"(r[44]), "=r"(r[45]), "=r"(r[46]), "=r"(r[47])
+        : "r"(t0), "r"(t1)
+        : "memory");
+#pragma unroll
+    for (int i = 0; i < 48; ++i) v[i] = __uint_as_float(r[i]);
+}
+__device__ __forceinline__ void tmem_ld_64(uint32_t t0, float* v)
+{
+    uint32_t r[64];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x64.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31,%32,%33,%34,%35,%36,%37,%38,%39,%40,%41,%42,%43,%44,%45,%46,%47,%48,%49,%50,%51,%52,%53,%54,%55,%56,%57,%58,%59,%60,%61,%62,%63}, [%64];\n\t"
+        "tcgen05.wait::ld.sync.aligned;"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31]), "=r"(r[32]), "=r"(r[33]), "=r"(r[34]), "=r"(r[35]), "=r"(r[36]), "=r"(r[37]), "=r"(r[38]), "=r"(r[39]), "=r"(r[40]), "=r"(r[41]), "=r"(r[42]), "=r"(r[43]), "=r"(r[44]), "=r"(r[45]), "=r"(r[46]), "=r"(r[47]), "=r"(r[48]), "=r"(r[49]), "=r"(r[50]), "=r"(r[51]), "=r"(r[52]), "=r"(r[53]), "=r"(r[54]), "=r"(r[55]), "=r"(r[56]), "=r"(r[57]), "=r"(r[58]), "=r"(r[59]), "=r"(r[60]), "=r"(r[61]), "=r"(r[62]), "=r"(r[63])
+        : "r"(t0)
+        : "memory");
+#pragma unroll
+    for (int i = 0; i < 64; ++i) v[i] = __uint_as_float(r[i]);
+}
+__device__ __forceinline__ void tmem_ld_80(uint32_t t0, uint32_t t1, float* v)
+{
+    uint32_t r[80];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x64.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31,%32,%33,%34,%35,%36,%37,%38,%39,%40,%41,%42,%43,%44,%45,%46,%47,%48,%49,%50,%51,%52,%53,%54,%55,%56,%57,%58,%59,%60,%61,%62,%63}, [%80];\n\t"
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%64,%65,%66,%67,%68,%69,%70,%71,%72,%73,%74,%75,%76,%77,%78,%79}, [%81];\n\t"
+        "tcgen05.wait::ld.sync.aligned;"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31]), "=r"(r[32]), "=r"(r[33]), "=r"(r[34]), "=r"(r[35]), "=r"(r[36]), "=r"(r[37]), "=r"(r[38]), "=r"(r[39]), "=r"(r[40]), "=r"(r[41]), "=r"(r[42]), "=r"(r[43]), "=r"(r[44]), "=r"(r[45]), "=r"(r[46]), "=r"(r[47]), "=r"(r[48]), "=r"(r[49]), "=r"(r[50]), "=r"(r[51]), "=r"(r[52]), "=r"(r[53]), "=r"(r[54]), "=r"(r[55]), "=r"(r[56]), "=r"(r[57]), "=r"(r[58]), "=r"(r[59]), "=r"(r[60]), "=r"(r[61]), "=r"(r[62]), "=r"(r[63]), "=r"(r[64]), "=r"(r[65]), "=r"(r[66]), "=r"(r[67]), "=r"(r[68]), "=r"(r[69]), "=r"(r[70]), "=r"(r[71]), "=r"(r[72]), "=r"(r[73]), "=r"(r[74]), "=r"(r[75]), "=r"(r[76]), "=r"(r[77]), "=r"(r[78]), "=r"(r[79])
+        : "r"(t0), "r"(t1)
+        : "memory");
+#pragma unroll
+    for (int i = 0; i < 80; ++i) v[i] = __uint_as_float(r[i]);
+}
+__device__ __forceinline__ void tmem_ld_6x8(uint32_t t0, uint32_t t1, uint32_t t2, uint32_t t3, uint32_t t4, uint32_t t5, float* v)
+{
+    uint32_t r[48];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%48];\n\t"
+        "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%8,%9,%10,%11,%12,%13,%14,%15}, [%49];\n\t"
+        "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%16,%17,%18,%19,%20,%21,%22,%23}, [%50];\n\t"
+        "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%24,%25,%26,%27,%28,%29,%30,%31}, [%51];\n\t"
+        "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%32,%33,%34,%35,%36,%37,%38,%39}, [%52];\n\t"
+        "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%40,%41,%42,%43,%44,%45,%46,%47}, [%53];\n\t"
+        "tcgen05.wait::ld.sync.aligned;"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31]), "=r"(r[32]), "=r"(r[33]), "=r"(r[34]), "=r"(r[35]), "=r"(r[36]), "=r"(r[37]), "=r"(r[38]), "=r"(r[39]), "=r"(r[40]), "=r"(r[41]), "=r"(r[42]), "=r"(r[43]), "=r"(r[44]), "=r"(r[45]), "=r"(r[46]), "=r"(r[47])
+        : "r"(t0), "r"(t1), "r"(t2), "r"(t3), "r"(t4), "r"(t5)
+        : "memory");
+#pragma unroll
+    for (int i = 0; i < 48; ++i) v[i] = __uint_as_float(r[i]);
+}
+__device__ __forceinline__ void tmem_ld_2x32(uint32_t t0, uint32_t t1, float* v)
+{
+    uint32_t r[64];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%64];\n\t"
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%32,%33,%34,%35,%36,%37,%38,%39,%40,%41,%42,%43,%44,%45,%46,%47,%48,%49,%50,%51,%52,%53,%54,%55,%56,%57,%58,%59,%60,%61,%62,%63}, [%65];\n\t"
+        "tcgen05.wait::ld.sync.aligned;"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31]), "=r"(r[32]), "=r"(r[33]), "=r"(r[34]), "=r"(r[35]), "=r"(r[36]), "=r"(r[37]), "=r"(r[38]), "=r"(r[39]), "=r"(r[40]), "=r"(r[41]), "=r"(r[42]), "=r"(r[43]), "=r"(r[44]), "=r"(r[45]), "=r"(r[46]), "=r"(r[47]), "=r"(r[48]), "=r"(r[49]), "=r"(r[50]), "=r"(r[51]), "=r"(r[52]), "=r"(r[53]), "=r"(r[54]), "=r"(r[55]), "=r"(r[56]), "=r"(r[57]), "=r"(r[58]), "=r"(r[59]), "=r"(r[60]), "=r"(r[61]), "=r"(r[62]), "=r"(r[63])
+        : "r"(t0), "r"(t1)
+        : "memory");
+#pragma unroll
+    for (int i = 0; i < 64; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// Store 8 columns of this thread's lane (completion: tcgen05.wait::st).
+__device__ __forceinline__ void tmem_st8(uint32_t taddr, const float* v)
+{
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};"
+                 ::"r"(taddr), "r"(__float_as_uint(v[0])), "r"(__float_as_uint(v[1])),
+                   "r"(__float_as_uint(v[2])), "r"(__float_as_uint(v[3])), "r"(__float_as_uint(v[4])),
+                   "r"(__float_as_uint(v[5])), "r"(__float_as_uint(v[6])), "r"(__float_as_uint(v[7]))
+                 : "memory");
+}
+__device__ __forceinline__ void tmem_wait_st()
+{
+    asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+}
+
+// The NCH * 16 columns of one plane of D1 in this thread's lane, one wait.
+template <int NCH>
+__device__ __forceinline__ void tmem_ld_plane(uint32_t taddr, float* v)
+{
+    if constexpr (NCH == 2) tmem_ld32(taddr, v);
+    else if constexpr (NCH == 3) tmem_ld_48(taddr, taddr + 32, v);
+    else if constexpr (NCH == 4) tmem_ld_64(taddr, v);
+    else tmem_ld_80(taddr, taddr + 64, v);
+}
+
 __device__ __forceinline__ void tmem_ld4x8(uint32_t t0, uint32_t t1, uint32_t t2, uint32_t t3,
                                            float* a, float* b, float* c, float* d)
 {
@@ -476,9 +572,16 @@ __global__ void __launch_bounds__(NT, 1) k_fwd_tc(FwdArgs a, long long spin_limi
                          ? __fmul_rn(__fsub_rn(__ldg(a.f + (size_t)gy * a.f_pitch + gx), c0), inv_c0)
                          : 0.f;
         }
-        float num[TW], den[TW];
+        // num / den of my row in TMEM columns tND .. tND + 63 (32 each)
+        const uint32_t tND = tbase + 4 * RWp + 4 * TW + tl;
+        {
+            float z[8];
 #pragma unroll
-        for (int x = 0; x < TW; ++x) num[x] = den[x] = 0.f;
+            for (int e = 0; e < 8; ++e) z[e] = 0.f;
+#pragma unroll
+            for (int q8 = 0; q8 < 8; ++q8) tmem_st8(tND + 8 * q8, z);
+            tmem_wait_st();
+        }
         bool ok = true;
         for (int k = 0; k < K && ok; ++k) {
             float wc = 0.f, Wk = hd.w0;
@@ -493,19 +596,11 @@ __global__ void __launch_bounds__(NT, 1) k_fwd_tc(FwdArgs a, long long spin_limi
             unsigned char* a2row = smem + G.offA2 + (m / 8) * G.sboA2 + (m % 8) * 16;
 #pragma unroll
             for (int pl = 0; pl < 4; ++pl) {
+                float v[NCH * 16];
+                tmem_ld_plane<NCH>(tD1 + tl + pl * RWp, v);
+                unsigned char* dst = a2row + pl * G.planeA2;
 #pragma unroll
-                for (int c = 0; c < NCH; c += 2) {
-                    float v[32];
-                    if (c + 1 < NCH) tmem_ld32(tD1 + tl + pl * RWp + 16 * c, v);
-                    else tmem_ld16(tD1 + tl + pl * RWp + 16 * c, v);
-                    unsigned char* dst = a2row + pl * G.planeA2 + (2 * c) * 128;
-                    store_row8<kBF16>(dst, v);
-                    store_row8<kBF16>(dst + 128, v + 8);
-                    if (c + 1 < NCH) {
-                        store_row8<kBF16>(dst + 256, v + 16);
-                        store_row8<kBF16>(dst + 384, v + 24);
-                    }
-                }
+                for (int b8 = 0; b8 < 2 * NCH; ++b8) store_row8<kBF16>(dst + b8 * 128, v + 8 * b8);
                 fence_async_smem();
                 fence_before();
                 mbar_arrive(bar(kBarA2Full + pl));
@@ -515,20 +610,37 @@ __global__ void __launch_bounds__(NT, 1) k_fwd_tc(FwdArgs a, long long spin_limi
             fence_after();
 #pragma unroll
             for (int cb = 0; cb < TW / 8; ++cb) {
-                float fa[8], fb[8], fc[8], fd[8];
-                tmem_ld4x8(tD2 + tl + 0 * TW + 8 * cb, tD2 + tl + 1 * TW + 8 * cb,
-                           tD2 + tl + 2 * TW + 8 * cb, tD2 + tl + 3 * TW + 8 * cb, fa, fb, fc, fd);
+                float v[48];
+                tmem_ld_6x8(tD2 + tl + 0 * TW + 8 * cb, tD2 + tl + 1 * TW + 8 * cb,
+                            tD2 + tl + 2 * TW + 8 * cb, tD2 + tl + 3 * TW + 8 * cb,
+                            tND + 8 * cb, tND + TW + 8 * cb, v);
+                float nn[8], dd[8];
 #pragma unroll
                 for (int e = 0; e < 8; ++e) {
                     const int x = TW - 1 - (8 * cb + e);
                     float s, c;
                     __sincosf(__fmul_rn(wc, pno[x]), &s, &c);
-                    num[x] = fmaf(Wk, fmaf(c, fa[e], s * fb[e]), num[x]);
-                    den[x] = fmaf(Wk, fmaf(c, fc[e], s * fd[e]), den[x]);
+                    nn[e] = fmaf(Wk, fmaf(c, v[e], s * v[8 + e]), v[32 + e]);
+                    dd[e] = fmaf(Wk, fmaf(c, v[16 + e], s * v[24 + e]), v[40 + e]);
                 }
+                tmem_st8(tND + 8 * cb, nn);
+                tmem_st8(tND + TW + 8 * cb, dd);
             }
+            tmem_wait_st();
             fence_before();
             mbar_arrive(bar(kBarD2Free));
+        }
+        tmem_wait_st();
+        float num[TW], den[TW];
+        {
+            float nd[2 * TW];
+            tmem_ld_2x32(tND, tND + TW, nd);
+            // TMEM column 8 cb + e holds output x = 31 - (8 cb + e)
+#pragma unroll
+            for (int n = 0; n < TW; ++n) {
+                num[TW - 1 - n] = nd[n];
+                den[TW - 1 - n] = nd[TW + n];
+            }
         }
         if (ok && gy < a.H) {
             // normalise with the guard (FP32 clipped Gaussian mass) and store
