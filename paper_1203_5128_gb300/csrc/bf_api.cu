@@ -9,6 +9,7 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <algorithm>
 #include <new>
 
 #include "bf_internal.cuh"
@@ -70,6 +71,13 @@ void free_plan(bf_plan_s* p)
         for (int i = 0; i < 4 * kMaxTimed; ++i)
             if (p->ev[i]) cudaEventDestroy(p->ev[i]);
         free(p->ev);
+    }
+    for (int i = 0; i < 4; ++i)
+        if (p->hst[i]) cudaStreamDestroy(p->hst[i]);
+    if (p->hev) {
+        for (int i = 0; i < p->n_hev; ++i)
+            if (p->hev[i]) cudaEventDestroy(p->hev[i]);
+        free(p->hev);
     }
     free(p);
 }
@@ -188,6 +196,112 @@ cudaError_t enqueue_params(bf_plan_s* p, const float* f, size_t fp, cudaStream_t
     e = launch_params(params_args(p), s);
     if (e != cudaSuccess) return e;
     return mark(p, 2, s);
+}
+
+// ---- host-to-host execution in row bands ---------------------------------
+//
+// With exact T per T-tile every quantity of a band of output rows depends on
+// the input rows within R of it only: the T-tiles of the band (K1: windows of
+// R around each pixel), their parameter sets (K2) and the band's output tiles
+// (K3).  So the image is copied in, filtered and copied out in bands of
+// kHostBandRows rows (a multiple of the T-tile), and the copy of band b + 2
+// in, the filter of band b and the copy of band b - 1 out overlap: band b
+// starts once band b + 1 (its lower halo) is on the device.  Two compute
+// streams alternate so that one band's last wave of tiles overlaps the next
+// band's first.  Same kernels, same arithmetic per pixel as bf_execute.
+constexpr int kHostBandRows = 512;
+
+int host_band_rows(const bf_plan_s* p)
+{
+    const int t = p->set_tile > 0 ? p->set_tile : 128;
+    return (std::max(kHostBandRows, t) + t - 1) / t * t;
+}
+
+bool host_banded(const bf_plan_s* p)
+{
+    int th = 0, tw = 0;
+    fwd_tc_tile(&th, &tw);
+    return p->opt.filter != BF_FILTER_YVV && p->opt.plane_dtype != BF_PLANES_FP32 &&
+           p->opt.t_mode == BF_T_TILE && p->set_tile % th == 0 && p->R < host_band_rows(p) &&
+           p->H >= 2 * host_band_rows(p);
+}
+
+bf_status execute_host_banded(bf_plan_s* p, const float* fh, float* oh, cudaStream_t s)
+{
+    const int H = p->H, W = p->W, B = host_band_rows(p);
+    const int nb = (H + B - 1) / B;
+    int th = 0, tw = 0;
+    fwd_tc_tile(&th, &tw);
+    const int need = 3 + 2 * nb;
+    if (!p->hst[0]) {
+        for (int i = 0; i < 4; ++i)
+            BF_CUDA(cudaStreamCreateWithFlags(&p->hst[i], cudaStreamNonBlocking));
+    }
+    if (p->n_hev < need) {
+        if (p->hev) {
+            for (int i = 0; i < p->n_hev; ++i)
+                if (p->hev[i]) cudaEventDestroy(p->hev[i]);
+            free(p->hev);
+        }
+        p->hev = (cudaEvent_t*)calloc(need, sizeof(cudaEvent_t));
+        p->n_hev = 0;
+        if (!p->hev) return BF_ERR_ALLOC;
+        for (int i = 0; i < need; ++i)
+            BF_CUDA(cudaEventCreateWithFlags(&p->hev[i], cudaEventDisableTiming));
+        p->n_hev = need;
+    }
+    cudaEvent_t ev_fork = p->hev[0], ev_clear = p->hev[1], ev_join = p->hev[2];
+    cudaEvent_t* ev_in = p->hev + 3;
+    cudaEvent_t* ev_done = p->hev + 3 + nb;
+    cudaStream_t s_in = p->hst[0], s_out = p->hst[3];
+    BF_CUDA(cudaEventRecord(ev_fork, s));
+    for (int i = 0; i < 4; ++i) BF_CUDA(cudaStreamWaitEvent(p->hst[i], ev_fork, 0));
+    // T words and the guard counter start at zero for every band's kernels
+    BF_CUDA(cudaMemsetAsync(p->d_T, 0, sizeof(unsigned) * p->n_sets, p->hst[1]));
+    BF_CUDA(cudaMemsetAsync(p->d_nguard, 0, sizeof(unsigned long long), p->hst[1]));
+    BF_CUDA(cudaEventRecord(ev_clear, p->hst[1]));
+    BF_CUDA(cudaStreamWaitEvent(p->hst[2], ev_clear, 0));
+    const size_t row_bytes = sizeof(float) * (size_t)W;
+    for (int b = 0; b < nb; ++b) {
+        const size_t r0 = (size_t)b * B, rows = std::min(H - (int)r0, B);
+        BF_CUDA(cudaMemcpyAsync(p->d_hin + r0 * W, fh + r0 * W, rows * row_bytes,
+                                cudaMemcpyHostToDevice, s_in));
+        BF_CUDA(cudaEventRecord(ev_in[b], s_in));
+    }
+    const int tiles_per_band = B / th, sets_per_band = B / p->set_tile;
+    for (int b = 0; b < nb; ++b) {
+        cudaStream_t cs = p->hst[1 + (b & 1)];
+        const int r0 = b * B, rows = std::min(H - r0, B);
+        BF_CUDA(cudaStreamWaitEvent(cs, ev_in[std::min(b + 1, nb - 1)], 0));
+        BF_CUDA(launch_local_range(p->d_hin, W, H, W, p->R, p->set_tile, p->sets_x, p->d_T, cs,
+                                   r0 / range_tile(), (rows + range_tile() - 1) / range_tile()));
+        ParamsArgs pa = params_args(p);
+        pa.set0 = b * sets_per_band * p->sets_x;
+        BF_CUDA(launch_params(pa, cs, (rows + p->set_tile - 1) / p->set_tile * p->sets_x));
+        FwdArgs fa = forward_args(p, p->d_hin, W, p->d_hout, W);
+        fa.y_tile0 = b * tiles_per_band;
+        fa.y_tiles = (rows + th - 1) / th;
+        BF_CUDA(launch_fwd_tc(fa, p->opt.plane_dtype == BF_PLANES_BF16, p->opt.spin_limit,
+                              p->d_status, cs));
+        BF_CUDA(cudaEventRecord(ev_done[b], cs));
+    }
+    for (int b = 0; b < nb; ++b) {
+        const size_t r0 = (size_t)b * B, rows = std::min(H - (int)r0, B);
+        BF_CUDA(cudaStreamWaitEvent(s_out, ev_done[b], 0));
+        BF_CUDA(cudaMemcpyAsync(oh + r0 * W, p->d_hout + r0 * W, rows * row_bytes,
+                                cudaMemcpyDeviceToHost, s_out));
+    }
+    // join every side stream into the caller's stream
+    BF_CUDA(cudaEventRecord(ev_join, s_out));
+    BF_CUDA(cudaStreamWaitEvent(s, ev_join, 0));
+    BF_CUDA(cudaEventRecord(ev_clear, p->hst[2]));
+    BF_CUDA(cudaStreamWaitEvent(s, ev_clear, 0));
+    BF_CUDA(cudaEventRecord(ev_fork, s_in));
+    BF_CUDA(cudaStreamWaitEvent(s, ev_fork, 0));
+    BF_CUDA(cudaStreamSynchronize(s));
+    p->executed = 1;
+    p->last = s;
+    return BF_OK;
 }
 
 }  // namespace bf
@@ -441,6 +555,7 @@ bf_status bf_execute_host(bf_plan_t p, const float* fh, float* oh, void* stream)
         if (cudaMalloc(&p->d_hin, bytes) != cudaSuccess) return BF_ERR_ALLOC;
         if (cudaMalloc(&p->d_hout, bytes) != cudaSuccess) return BF_ERR_ALLOC;
     }
+    if (host_banded(p)) return execute_host_banded(p, fh, oh, s);
     BF_CUDA(cudaMemcpyAsync(p->d_hin, fh, bytes, cudaMemcpyHostToDevice, s));
     bf_status st = bf_execute(p, p->d_hin, p->W, p->d_hout, p->W, stream);
     if (st != BF_OK) return st;

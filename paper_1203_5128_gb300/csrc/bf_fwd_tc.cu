@@ -182,22 +182,6 @@ __device__ __forceinline__ bool mbar_wait_warp(uint32_t mbar, uint32_t parity, l
 
 // TMEM loads of this thread's lane; the wait is in the same statement, so no
 // use of the outputs can be scheduled before it.
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v)
-{
-    uint32_t r[16];
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
-        "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];\n\t"
-        "tcgen05.wait::ld.sync.aligned;"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
-          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
-          "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-        : "r"(taddr)
-        : "memory");
-#pragma unroll
-    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
-}
-
 __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v)
 {
     uint32_t r[32];
@@ -314,32 +298,6 @@ __device__ __forceinline__ void tmem_ld_plane(uint32_t taddr, float* v)
     else tmem_ld_80(taddr, taddr + 64, v);
 }
 
-__device__ __forceinline__ void tmem_ld4x8(uint32_t t0, uint32_t t1, uint32_t t2, uint32_t t3,
-                                           float* a, float* b, float* c, float* d)
-{
-    uint32_t r[32];
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%32];\n\t"
-        "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%8,%9,%10,%11,%12,%13,%14,%15}, [%33];\n\t"
-        "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%16,%17,%18,%19,%20,%21,%22,%23}, [%34];\n\t"
-        "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%24,%25,%26,%27,%28,%29,%30,%31}, [%35];\n\t"
-        "tcgen05.wait::ld.sync.aligned;"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
-          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
-          "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]),
-          "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
-          "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]),
-          "=r"(r[31])
-        : "r"(t0), "r"(t1), "r"(t2), "r"(t3)
-        : "memory");
-#pragma unroll
-    for (int i = 0; i < 8; ++i) {
-        a[i] = __uint_as_float(r[i]);
-        b[i] = __uint_as_float(r[8 + i]);
-        c[i] = __uint_as_float(r[16 + i]);
-        d[i] = __uint_as_float(r[24 + i]);
-    }
-}
 
 // ---- geometry -------------------------------------------------------------
 
@@ -382,7 +340,7 @@ __global__ void __launch_bounds__(NT, 1) k_fwd_tc(FwdArgs a, long long spin_limi
     const TcGeo G(a.R);
     const int R = a.R;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int by = blockIdx.y * TH, bx = blockIdx.x * TW;
+    const int by = (blockIdx.y + a.y_tile0) * TH, bx = blockIdx.x * TW;
     const int gy0 = by - R, gx0 = bx - R;
     const uint32_t sbase = smem_u32(smem);
     const uint32_t bar0 = sbase + G.offBar;
@@ -680,7 +638,7 @@ cudaError_t launch_t(const FwdArgs& a, long long spin, unsigned* status, cudaStr
     cudaError_t e = cudaFuncSetAttribute(k_fwd_tc<kBF16, NCH>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G.bytes);
     if (e != cudaSuccess) return e;
-    dim3 grid((a.W + TW - 1) / TW, (a.H + TH - 1) / TH);
+    dim3 grid((a.W + TW - 1) / TW, a.y_tiles > 0 ? a.y_tiles : (a.H + TH - 1) / TH);
     k_fwd_tc<kBF16, NCH><<<grid, NT, G.bytes, s>>>(a, spin, status);
     return cudaGetLastError();
 }

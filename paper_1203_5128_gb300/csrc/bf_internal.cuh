@@ -46,6 +46,9 @@ struct bf_plan_s {
     int timing;              // record events around the kernels
     int n_timed;
     cudaEvent_t* ev;         // 4 per recorded execute
+    cudaStream_t hst[4];     // banded host path: copy in, compute (2), copy out
+    cudaEvent_t* hev;        // banded host path: fork, clear, join, then per band in / done
+    int n_hev;
 };
 
 namespace bf {
@@ -99,8 +102,10 @@ constexpr float kGuard = 1e-6f;
 // K1: local range r(x) = max(M(x) - f(x), f(x) - m(x)) reduced to one
 // non-negative float per T-set (atomicMax on the bit pattern).  Tbits must be
 // zeroed first.  set_tile == 0: one set for the whole image.
+// by0 / nby: the 64-row block rows of the launch (nby = 0: all).
 cudaError_t launch_local_range(const float* f, size_t pitch, int H, int W, int R,
-                               int set_tile, int sets_x, unsigned* Tbits, cudaStream_t s);
+                               int set_tile, int sets_x, unsigned* Tbits, cudaStream_t s,
+                               int by0 = 0, int nby = 0);
 
 // Largest R whose K1 staging fits in shared memory.
 int range_max_radius();
@@ -122,11 +127,15 @@ struct ParamsArgs {
     SetHdr* hdr;
     Pair* pairs;
     unsigned* status;
+    int set0 = 0;          // first set of the launch (block b takes set set0 + b)
 };
-cudaError_t launch_params(const ParamsArgs& a, cudaStream_t s);
+// K2 over sets set0 .. set0 + n - 1 (n = 0: all sets).
+cudaError_t launch_params(const ParamsArgs& a, cudaStream_t s, int n = 0);
 
 // K3 (FP32 planes, FIR): fused modulate / filter / demodulate / normalise.
 struct FwdArgs {
+    int y_tile0 = 0;        // first row of output tiles of the launch
+    int y_tiles = 0;        // rows of output tiles (0: the whole image)
     const float* f;
     size_t f_pitch;
     float* out;

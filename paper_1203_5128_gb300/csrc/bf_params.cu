@@ -122,7 +122,7 @@ __device__ void params_body(const ParamsArgs& a, int set)
     }
 }
 
-__global__ void __launch_bounds__(kThreads) k_params(ParamsArgs a) { params_body(a, blockIdx.x); }
+__global__ void __launch_bounds__(kThreads) k_params(ParamsArgs a) { params_body(a, a.set0 + blockIdx.x); }
 
 // Batched: block b computes set block_set[b] of image block_img[b].
 __global__ void __launch_bounds__(kThreads)
@@ -135,10 +135,10 @@ k_params_batch(const ParamsArgs* __restrict__ imgs, const int* __restrict__ bloc
 
 }  // namespace
 
-cudaError_t launch_params(const ParamsArgs& a, cudaStream_t s)
+cudaError_t launch_params(const ParamsArgs& a, cudaStream_t s, int n)
 {
     if (a.n_cap > kMaxTail) return cudaErrorInvalidValue;
-    k_params<<<a.n_sets, kThreads, 0, s>>>(a);
+    k_params<<<n > 0 ? n : a.n_sets, kThreads, 0, s>>>(a);
     return cudaGetLastError();
 }
 

@@ -204,12 +204,12 @@ template <bool kMin, bool kImages>
 __global__ void __launch_bounds__(kThreads)
 k_local_range(const float* __restrict__ f, size_t pitch, int H, int W, int R, int set_tile,
               int sets_x, unsigned* __restrict__ Tbits, float* __restrict__ Mx,
-              float* __restrict__ mn)
+              float* __restrict__ mn, int by0)
 {
     extern __shared__ float sm[];
     __shared__ float red[kThreads / 32];
     range_body<kMin, kImages>(f, pitch, H, W, R, set_tile, sets_x, Tbits, Mx, mn,
-                              blockIdx.y * kT, blockIdx.x * kT, sm, red);
+                              (by0 + (int)blockIdx.y) * kT, blockIdx.x * kT, sm, red);
 }
 
 // Batched: CTAs stride over (image, block row, block column) items; the min
@@ -243,15 +243,15 @@ size_t range_smem(int R, bool with_min)
 
 template <bool kMin, bool kImages>
 cudaError_t launch(const float* f, size_t pitch, int H, int W, int R, int set_tile, int sets_x,
-                   unsigned* Tbits, float* Mx, float* mn, cudaStream_t s)
+                   unsigned* Tbits, float* Mx, float* mn, cudaStream_t s, int by0 = 0, int nby = 0)
 {
     const size_t smem = range_smem(R, kMin);
     cudaError_t e = cudaFuncSetAttribute(k_local_range<kMin, kImages>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    dim3 grid((W + kT - 1) / kT, (H + kT - 1) / kT);
+    dim3 grid((W + kT - 1) / kT, nby > 0 ? nby : (H + kT - 1) / kT);
     k_local_range<kMin, kImages><<<grid, kThreads, smem, s>>>(f, pitch, H, W, R, set_tile, sets_x,
-                                                              Tbits, Mx, mn);
+                                                              Tbits, Mx, mn, by0);
     return cudaGetLastError();
 }
 
@@ -280,11 +280,12 @@ int range_max_radius()
 }
 
 cudaError_t launch_local_range(const float* f, size_t pitch, int H, int W, int R, int set_tile,
-                               int sets_x, unsigned* Tbits, cudaStream_t s)
+                               int sets_x, unsigned* Tbits, cudaStream_t s, int by0, int nby)
 {
     // per-tile T needs the min filter too; the image-wide T does not (Prop. 2.1)
     if (set_tile)
-        return launch<true, false>(f, pitch, H, W, R, set_tile, sets_x, Tbits, nullptr, nullptr, s);
+        return launch<true, false>(f, pitch, H, W, R, set_tile, sets_x, Tbits, nullptr, nullptr, s,
+                                   by0, nby);
     return launch<false, false>(f, pitch, H, W, R, 0, 1, Tbits, nullptr, nullptr, s);
 }
 

@@ -153,6 +153,31 @@ def test_host_entry_point_matches_device(bf):
     assert torch.equal(dev, host)
 
 
+@pytest.mark.parametrize("H,W,planes,tile", [(1100, 300, "fp16", 128), (1536, 256, "bf16", 256),
+                                             (2048, 160, "fp16", 128)])
+def test_host_entry_point_banded(bf, H, W, planes, tile):
+    """Per-tile T with 16-bit planes: the host entry point copies, filters
+    and copies back in row bands that overlap one another; its output, the
+    T, N, M of every T-tile and the guard count equal one bf_execute on the
+    device (ragged last band, two band sizes)."""
+    import torch
+    f = synth.g8(H, W, seed=H + W)
+    plan = bf.bf_plan(H, W, 8.0, 10.0, 0.01, t_mode="tile", t_tile=tile, plane_dtype=planes)
+    dev = bf.bf_execute(plan, to_dev(f)).cpu()
+    T0, N0, M0 = bf.bf_get_sets(plan)
+    g0 = bf.bf_get_info(plan).n_guarded
+    host = bf.bf_execute_host(plan, torch.from_numpy(f).pin_memory())
+    T1, N1, M1 = bf.bf_get_sets(plan)
+    assert torch.equal(dev, host)
+    assert np.array_equal(T0, T1) and np.array_equal(N0, N1) and np.array_equal(M0, M1)
+    assert bf.bf_get_info(plan).n_guarded == g0
+    # a second call through the same plan (streams and events reused)
+    f2 = synth.g8(H, W, seed=H + W + 1)
+    host2 = bf.bf_execute_host(plan, torch.from_numpy(f2).pin_memory())
+    dev2 = bf.bf_execute(plan, to_dev(f2)).cpu()
+    assert torch.equal(dev2, host2)
+
+
 def test_constant_image(bf):
     """A constant image is a fixed point; T = 0 and N = 1 (Sec. 2, Sec. 1.3)."""
     import torch
