@@ -39,9 +39,9 @@ TUNED_YVV = dict(t_mode="global", trunc_rule="alg2", plane_dtype="fp32", filter=
 PLAIN = dict(t_mode="fixed", t_fixed=255.0, trunc_rule="alg2", plane_dtype="fp32", filter="fir")
 SM_COUNT_NOMINAL = 152
 # DRAM bytes of one k_fwd_tc launch on the tuned 4096^2 workload, read + write,
-# from an ncu capture of the kernel as built (67.78 MB + 24.07 MB); set to None
+# from an ncu capture of the kernel as built (67.77 MB + 23.50 MB); set to None
 # whenever the kernel changes until it is captured again
-K3TC_DRAM_BYTES = 67784704 + 24071424
+K3TC_DRAM_BYTES = 67768576 + 23501824
 FP32_LANES_PER_SM = 128
 
 
