@@ -11,6 +11,7 @@
 
 #include <algorithm>
 #include <new>
+#include <vector>
 
 #include "bf_internal.cuh"
 
@@ -203,12 +204,14 @@ cudaError_t enqueue_params(bf_plan_s* p, const float* f, size_t fp, cudaStream_t
 // With exact T per T-tile every quantity of a band of output rows depends on
 // the input rows within R of it only: the T-tiles of the band (K1: windows of
 // R around each pixel), their parameter sets (K2) and the band's output tiles
-// (K3).  So the image is copied in, filtered and copied out in bands of
-// kHostBandRows rows (a multiple of the T-tile), and the copy of band b + 2
-// in, the filter of band b and the copy of band b - 1 out overlap: band b
-// starts once band b + 1 (its lower halo) is on the device.  Two compute
-// streams alternate so that one band's last wave of tiles overlaps the next
-// band's first.  Same kernels, same arithmetic per pixel as bf_execute.
+// (K3).  So the image is copied in (in chunks of one T-tile row, each with an
+// event), filtered and copied out in bands of kHostBandRows rows, half that
+// for the first and the last band so that the pipeline fills and drains
+// sooner: band b is filtered once the chunk holding its last halo row is on
+// the device, while later chunks are copied in and earlier bands out.  Two
+// compute streams alternate so that one band's last wave of tiles overlaps
+// the next band's first.  Same kernels, same arithmetic per pixel as
+// bf_execute.
 constexpr int kHostBandRows = 512;
 
 int host_band_rows(const bf_plan_s* p)
@@ -222,17 +225,30 @@ bool host_banded(const bf_plan_s* p)
     int th = 0, tw = 0;
     fwd_tc_tile(&th, &tw);
     return p->opt.filter != BF_FILTER_YVV && p->opt.plane_dtype != BF_PLANES_FP32 &&
-           p->opt.t_mode == BF_T_TILE && p->set_tile % th == 0 && p->R < host_band_rows(p) &&
+           p->opt.t_mode == BF_T_TILE && p->set_tile % th == 0 && p->R < p->set_tile &&
            p->H >= 2 * host_band_rows(p);
 }
 
 bf_status execute_host_banded(bf_plan_s* p, const float* fh, float* oh, cudaStream_t s)
 {
-    const int H = p->H, W = p->W, B = host_band_rows(p);
-    const int nb = (H + B - 1) / B;
+    const int H = p->H, W = p->W, B = host_band_rows(p), C = p->set_tile;
     int th = 0, tw = 0;
     fwd_tc_tile(&th, &tw);
-    const int need = 3 + 2 * nb;
+    // band boundaries (multiples of the T-tile): a half band first, full
+    // bands, then what is left (at most a full band) last
+    std::vector<int> cut{0};
+    const int half = std::max(C, B / 2 / C * C);
+    cut.push_back(std::min(H, half));
+    while (cut.back() < H) cut.push_back(std::min(H, cut.back() + B));
+    if (cut.size() > 3 && H - cut[cut.size() - 2] > half) {
+        // split the last full band so that the last band is a half band too
+        const int last0 = cut[cut.size() - 2];
+        cut.back() = std::min(H, last0 + (H - last0 - half + C - 1) / C * C);
+        if (cut.back() < H) cut.push_back(H);
+    }
+    const int nb = (int)cut.size() - 1;
+    const int nc = (H + C - 1) / C;                  // copy chunks of one T-tile row
+    const int need = 3 + nc + nb;
     if (!p->hst[0]) {
         for (int i = 0; i < 4; ++i)
             BF_CUDA(cudaStreamCreateWithFlags(&p->hst[i], cudaStreamNonBlocking));
@@ -251,8 +267,8 @@ bf_status execute_host_banded(bf_plan_s* p, const float* fh, float* oh, cudaStre
         p->n_hev = need;
     }
     cudaEvent_t ev_fork = p->hev[0], ev_clear = p->hev[1], ev_join = p->hev[2];
-    cudaEvent_t* ev_in = p->hev + 3;
-    cudaEvent_t* ev_done = p->hev + 3 + nb;
+    cudaEvent_t* ev_in = p->hev + 3;                 // per chunk
+    cudaEvent_t* ev_done = p->hev + 3 + nc;          // per band
     cudaStream_t s_in = p->hst[0], s_out = p->hst[3];
     BF_CUDA(cudaEventRecord(ev_fork, s));
     for (int i = 0; i < 4; ++i) BF_CUDA(cudaStreamWaitEvent(p->hst[i], ev_fork, 0));
@@ -262,34 +278,34 @@ bf_status execute_host_banded(bf_plan_s* p, const float* fh, float* oh, cudaStre
     BF_CUDA(cudaEventRecord(ev_clear, p->hst[1]));
     BF_CUDA(cudaStreamWaitEvent(p->hst[2], ev_clear, 0));
     const size_t row_bytes = sizeof(float) * (size_t)W;
+    int copied = 0;                                  // chunks enqueued so far
     for (int b = 0; b < nb; ++b) {
-        const size_t r0 = (size_t)b * B, rows = std::min(H - (int)r0, B);
-        BF_CUDA(cudaMemcpyAsync(p->d_hin + r0 * W, fh + r0 * W, rows * row_bytes,
-                                cudaMemcpyHostToDevice, s_in));
-        BF_CUDA(cudaEventRecord(ev_in[b], s_in));
-    }
-    const int tiles_per_band = B / th, sets_per_band = B / p->set_tile;
-    for (int b = 0; b < nb; ++b) {
+        const int r0 = cut[b], r1 = cut[b + 1];
+        // chunks up to the one holding input row r1 - 1 + R
+        const int last_chunk = std::min(nc - 1, (std::min(H - 1, r1 - 1 + p->R)) / C);
+        for (; copied <= last_chunk; ++copied) {
+            const size_t c0 = (size_t)copied * C, rows = std::min(H - (int)c0, C);
+            BF_CUDA(cudaMemcpyAsync(p->d_hin + c0 * W, fh + c0 * W, rows * row_bytes,
+                                    cudaMemcpyHostToDevice, s_in));
+            BF_CUDA(cudaEventRecord(ev_in[copied], s_in));
+        }
         cudaStream_t cs = p->hst[1 + (b & 1)];
-        const int r0 = b * B, rows = std::min(H - r0, B);
-        BF_CUDA(cudaStreamWaitEvent(cs, ev_in[std::min(b + 1, nb - 1)], 0));
+        const int rows = r1 - r0;
+        BF_CUDA(cudaStreamWaitEvent(cs, ev_in[last_chunk], 0));
         BF_CUDA(launch_local_range(p->d_hin, W, H, W, p->R, p->set_tile, p->sets_x, p->d_T, cs,
                                    r0 / range_tile(), (rows + range_tile() - 1) / range_tile()));
         ParamsArgs pa = params_args(p);
-        pa.set0 = b * sets_per_band * p->sets_x;
-        BF_CUDA(launch_params(pa, cs, (rows + p->set_tile - 1) / p->set_tile * p->sets_x));
+        pa.set0 = r0 / C * p->sets_x;
+        BF_CUDA(launch_params(pa, cs, (rows + C - 1) / C * p->sets_x));
         FwdArgs fa = forward_args(p, p->d_hin, W, p->d_hout, W);
-        fa.y_tile0 = b * tiles_per_band;
+        fa.y_tile0 = r0 / th;
         fa.y_tiles = (rows + th - 1) / th;
         BF_CUDA(launch_fwd_tc(fa, p->opt.plane_dtype == BF_PLANES_BF16, p->opt.spin_limit,
                               p->d_status, cs));
         BF_CUDA(cudaEventRecord(ev_done[b], cs));
-    }
-    for (int b = 0; b < nb; ++b) {
-        const size_t r0 = (size_t)b * B, rows = std::min(H - (int)r0, B);
         BF_CUDA(cudaStreamWaitEvent(s_out, ev_done[b], 0));
-        BF_CUDA(cudaMemcpyAsync(oh + r0 * W, p->d_hout + r0 * W, rows * row_bytes,
-                                cudaMemcpyDeviceToHost, s_out));
+        BF_CUDA(cudaMemcpyAsync(oh + (size_t)r0 * W, p->d_hout + (size_t)r0 * W,
+                                (size_t)rows * row_bytes, cudaMemcpyDeviceToHost, s_out));
     }
     // join every side stream into the caller's stream
     BF_CUDA(cudaEventRecord(ev_join, s_out));
