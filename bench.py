@@ -233,6 +233,17 @@ def yvv_instr_per_px(N, M):
     return F * 71 + z * 34 + 3
 
 
+def yvv_bytes_per_px(N, M):
+    """HBM bytes per output pixel of the recursive filter's two-pass design:
+    per kept term (pair or zero frequency) the four row-filtered planes are
+    written once (16 B) and read by the down and the up column sweeps (32 B),
+    and the anti-causal row states are written and read back (6 + 6 B); plus
+    the image in and the output out (8 B)."""
+    F = (N - M) - N // 2
+    z = 1 if N % 2 == 0 else 0
+    return (F + z) * 60 + 8
+
+
 def per_set_total(fn, plan_info, N, M, t_tile):
     """Sum over the plan's parameter sets of fn(N_s, M_s) x the pixels the
     set covers (the whole image for one set; T-tiles clipped at the
@@ -478,6 +489,12 @@ def main():
               "launch_ms": kyv_ms,
               "peak_source": "%d SMs x %d FP32 lanes x %.0f MHz (%s sm_max_mhz)" % (
                   sms, FP32_LANES_PER_SM, mhz, pk_kind)}
+    byv = yvv_bytes_per_px(info_yv.N, info_yv.M) * px
+    peak_hbm = float(pk.get("hbm_gbs", 6800.0))
+    roofyv_hbm = {"bound": "hbm", "achieved": byv / (kyv_ms * 1e-3) / 1e9, "peak": peak_hbm,
+                  "unit": "GB/s", "frac": byv / (kyv_ms * 1e-3) / 1e9 / peak_hbm,
+                  "bytes_per_execute": byv,
+                  "peak_source": "%s hbm_gbs" % pk_kind}
     p_k3 = p_kms[2] / max(p_cnt, 1)
     p_instr = fp32_instr_per_px(info_p.N, info_p.M, info_p.R) * px
 
@@ -509,6 +526,7 @@ def main():
                   "fp32_frac": p_instr / (p_k3 * 1e-3) / 1e12 / peak_tinst},
         "tuned_fp32": {"value": t32_value, "ms_per_step": t32_ms / s32, "roofline": roof32},
         "tuned_yvv": {"value": yv_value, "ms_per_step": yv_ms / s32, "roofline": roofyv,
+                      "roofline_hbm": roofyv_hbm,
                       "note": "Young-van Vliet recursion in place of the FIR: approximates "
                               "the Gaussian; parity is against the oracle's recursive mode"},
         "speedup_vs_plain": value / plain_value,
