@@ -106,7 +106,12 @@ typedef struct bf_options {
     int filter;          /* BF_FILTER_*; default AUTO (= FIR)                     */
     int plane_dtype;     /* BF_PLANES_*; default FP32                             */
     int n_max;           /* cap on N; default 4096                                */
-    int t_tile;          /* T-tile side for BF_T_TILE; default 64 (multiple of 64) */
+    int t_tile;          /* T-tile side for BF_T_TILE; default 64 (multiple of 64).
+                            16-bit planes need a multiple of 128 (the height of
+                            the tensor-core tile, which must lie in one
+                            T-tile), else bf_plan returns BF_ERR_INVALID_ARG;
+                            FP32 planes use 128-row tiles for multiples of 128
+                            and 64-row tiles otherwise.                           */
     long long spin_limit;/* iteration bound of device waits; default 1<<22        */
     int reserved[8];     /* must be zero                                          */
 } bf_options;
