@@ -44,10 +44,15 @@ def bf_options_init(**kw) -> nat.bf_options:
     o = nat.bf_options()
     nat.lib().bf_options_init(ctypes.byref(o))
     table = {"t_mode": T_MODES, "trunc_rule": RULES, "filter": FILTERS, "plane_dtype": PLANES}
+    fields = {name for name, _ in nat.bf_options._fields_ if name != "reserved"}
     for k, v in kw.items():
+        if k not in fields:
+            raise TypeError("unknown bf_options field %r (known: %s)" % (k, ", ".join(sorted(fields))))
         if v is None:
             continue
         if k in table and isinstance(v, str):
+            if v not in table[k]:
+                raise ValueError("%s=%r: expected one of %s" % (k, v, ", ".join(sorted(table[k]))))
             v = table[k][v]
         setattr(o, k, v)
     return o
