@@ -112,7 +112,8 @@ typedef struct bf_options {
                             T-tile), else bf_plan returns BF_ERR_INVALID_ARG;
                             FP32 planes use 128-row tiles for multiples of 128
                             and 64-row tiles otherwise.                           */
-    long long spin_limit;/* iteration bound of device waits; default 1<<22        */
+    long long spin_limit;/* iteration bound of device waits; default 1<<22,
+                            at least 1<<16 (smaller values are raised)            */
     int reserved[8];     /* must be zero                                          */
 } bf_options;
 

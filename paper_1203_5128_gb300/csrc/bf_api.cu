@@ -213,6 +213,7 @@ cudaError_t enqueue_params(bf_plan_s* p, const float* f, size_t fp, cudaStream_t
 // the next band's first.  Same kernels, same arithmetic per pixel as
 // bf_execute.
 constexpr int kHostBandRows = 512;
+constexpr long long kMinSpinLimit = 1ll << 16;   // polls; see bf_plan
 
 int host_band_rows(const bf_plan_s* p)
 {
@@ -390,6 +391,9 @@ bf_status bf_plan(int H, int W, double sigma_s, double sigma_r, double eps, cons
         return BF_ERR_INVALID_ARG;
     if (o.t_mode == BF_T_FIXED && !(o.t_fixed > 0.f)) o.t_fixed = o.value_range;
     if (o.spin_limit <= 0) o.spin_limit = 1ll << 22;
+    // the same bound limits the wait that lets issued MMAs finish before a
+    // stopping CTA frees its TMEM: keep it far above their completion time
+    if (o.spin_limit < kMinSpinLimit) o.spin_limit = kMinSpinLimit;
 
     const double Rr = ceil(3.0 * sigma_s);
     if (Rr > 1000.0) return BF_ERR_NOT_SUPPORTED;
