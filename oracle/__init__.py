@@ -20,7 +20,11 @@ Parity status: every function here is pinned by ``tests/test_oracle_pins.py``
 values the paper prints).  The Young-van Vliet mode (``spatial="yvv"``) is
 pinned by ``tests/test_oracle_yvv.py`` against the recursion's closed-form
 frequency response, brute-force convolution with its impulse response and
-the direct form; the paper prints no value for it.
+the direct form; the paper prints no value for it.  The box mode
+(``spatial="box"``: the constant spatial filter of radius sigma_s that
+Sec. 4 uses against BF2) is pinned by ``tests/test_oracle_box.py`` against
+running sums of an integral image, pure-Python brute force and the direct
+form.
 """
 from __future__ import annotations
 
@@ -121,6 +125,27 @@ def taps(sigma_s: float, R: int | None = None) -> np.ndarray:
     g = np.empty(2 * R + 1)
     _load().orc_gauss_taps(float(sigma_s), R, _p(g))
     return g
+
+
+def box_radius(sigma_s: float) -> int:
+    """Radius of the constant (box) spatial filter.  In the comparison with
+    BF2 (Sec. 4, Figs. 7-10) sigma_s names the radius of the box, so it must
+    be a positive integer; the window is the (2 sigma_s + 1)^2 square."""
+    r = float(sigma_s)
+    if not (r >= 1.0 and r == int(r)):
+        raise ValueError("box radius sigma_s must be a positive integer, got %r" % sigma_s)
+    return int(r)
+
+
+def spatial_taps(sigma_s: float, R: int, spatial: str) -> np.ndarray:
+    """One-dimensional taps of the separable spatial filter: the truncated
+    Gaussian ("fir") or the constant filter ("box"), whose 2-D kernel is
+    the product of the two lines'."""
+    if spatial == "fir":
+        return taps(sigma_s, R)
+    if spatial == "box":
+        return np.ones(2 * R + 1)
+    raise ValueError(spatial)
 
 
 # ---------------------------------------------------------------- max / min
@@ -234,11 +259,13 @@ class Params:
 def resolve(f, sigma_s: float, sigma_r: float, eps: float = 0.0, *,
             t_mode: str = T_GLOBAL, rule: str = RULE_ALG2,
             value_range: float = 255.0, t_fixed: float | None = None,
-            t_tile: int = 64) -> Params:
-    """Algorithm 2, steps 1-4: R, T, N and M (per T-tile in ``tile`` mode)."""
+            t_tile: int = 64, spatial: str = "fir") -> Params:
+    """Algorithm 2, steps 1-4: R, T, N and M (per T-tile in ``tile`` mode).
+    R is ceil(3 sigma_s) for the Gaussian (and its recursive form) and
+    sigma_s itself for the box filter (``spatial="box"``)."""
     f = _f64(f)
     H, W = f.shape
-    R = radius(sigma_s)
+    R = box_radius(sigma_s) if spatial == "box" else radius(sigma_s)
     if t_mode == T_FIXED:
         T = np.array([[np.float32(value_range if t_fixed is None else t_fixed)]], np.float32)
         th = tw = WHOLE
@@ -299,7 +326,8 @@ def shiftable(f, sigma_s: float, sigma_r: float, params: Params, *, return_parts
     """SHIFTABLE-BF (Sec. 1.2) with phi_eps per T-tile.  Returns out (and
     num, den, number of guarded pixels when return_parts).  ``spatial``
     "yvv" filters the planes with the Young-van Vliet recursion instead of
-    the truncated Gaussian (single kernel only)."""
+    the truncated Gaussian (single kernel only); "box" with the constant
+    filter of radius params.R (Sec. 4)."""
     f = _f64(f)
     H, W = f.shape
     if spatial == "yvv":
@@ -311,9 +339,7 @@ def shiftable(f, sigma_s: float, sigma_r: float, params: Params, *, return_parts
         if return_parts:
             return out, num, den, nfb
         return out
-    if spatial != "fir":
-        raise ValueError(spatial)
-    g = taps(sigma_s, params.R)
+    g = spatial_taps(sigma_s, params.R, spatial)
     out = np.empty_like(f)
     num = np.empty_like(f)
     den = np.empty_like(f)
@@ -340,7 +366,7 @@ def direct(f, sigma_s: float, sigma_r: float, params: Params | None = None, *,
     when ``gauss``.  Returns values in the order of ``points`` (or an image).
     ``spatial`` "yvv" weighs neighbours by the product of the recursion's
     one-dimensional impulse responses over the whole image instead of the
-    truncated Gaussian."""
+    truncated Gaussian; "box" weighs the (2 sigma_s + 1)^2 square equally."""
     f = _f64(f)
     H, W = f.shape
     if points is None:
@@ -353,9 +379,12 @@ def direct(f, sigma_s: float, sigma_r: float, params: Params | None = None, *,
     if spatial == "yvv":
         R = max(H, W)
         g = yvv_impulse(sigma_s, R)
-    elif spatial == "fir":
-        R = radius(sigma_s) if params is None else params.R
-        g = taps(sigma_s, R)
+    elif spatial in ("fir", "box"):
+        if params is not None:
+            R = params.R
+        else:
+            R = box_radius(sigma_s) if spatial == "box" else radius(sigma_s)
+        g = spatial_taps(sigma_s, R, spatial)
     else:
         raise ValueError(spatial)
     if gauss:
@@ -385,13 +414,15 @@ def direct(f, sigma_s: float, sigma_r: float, params: Params | None = None, *,
     return out
 
 
-def grad_shiftable(f, u, sigma_s: float, sigma_r: float, params: Params):
+def grad_shiftable(f, u, sigma_s: float, sigma_r: float, params: Params, *,
+                   spatial: str = "fir"):
     """d/df of L = sum u * out, T, N, M held fixed (shiftable form)."""
     f = _f64(f)
     u = _f64(u)
     H, W = f.shape
-    out, num, den, _ = shiftable(f, sigma_s, sigma_r, params, return_parts=True)
-    g = taps(sigma_s, params.R)
+    out, num, den, _ = shiftable(f, sigma_s, sigma_r, params, return_parts=True,
+                                 spatial=spatial)
+    g = spatial_taps(sigma_s, params.R, spatial)
     guarded = ~(den > 1e-6 * _mass(g, params.R, H, W))
     a = np.where(guarded, 0.0, u / np.where(guarded, 1.0, den))
     b = -a * out
@@ -407,14 +438,15 @@ def grad_shiftable(f, u, sigma_s: float, sigma_r: float, params: Params):
     return grad
 
 
-def grad_direct(f, u, sigma_s: float, sigma_r: float, params: Params, points=None):
+def grad_direct(f, u, sigma_s: float, sigma_r: float, params: Params, points=None, *,
+                spatial: str = "fir"):
     """Same gradient from the direct form (single kernel only)."""
     assert params.T.size == 1, "direct gradient takes one (N, M)"
     f = _f64(f)
     u = _f64(u)
     H, W = f.shape
-    out, num, den, _ = direct(f, sigma_s, sigma_r, params, return_parts=True)
-    g = taps(sigma_s, params.R)
+    out, num, den, _ = direct(f, sigma_s, sigma_r, params, return_parts=True, spatial=spatial)
+    g = spatial_taps(sigma_s, params.R, spatial)
     guarded = ~(den > 1e-6 * _mass(g, params.R, H, W))
     a = np.ascontiguousarray(np.where(guarded, 0.0, u / np.where(guarded, 1.0, den)))
     b = np.ascontiguousarray(-a * out)
