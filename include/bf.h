@@ -31,7 +31,8 @@
  *     that ran out) are recorded in the plan's device status word and read
  *     with bf_get_device_status.
  *   - Borders: sums run over in-image pixels only (clipped windows), the
- *     window is the (2R+1)^2 square with R = ceil(3 sigma_s).
+ *     window is the (2R+1)^2 square with R = ceil(3 sigma_s) (R = sigma_s
+ *     for the box spatial filter, BF_SPATIAL_BOX).
  */
 #ifndef BF_H
 #define BF_H
@@ -86,6 +87,17 @@ enum {
  * other. */
 enum { BF_FILTER_AUTO = 0, BF_FILTER_FIR = 1, BF_FILTER_YVV = 2 };
 
+/* Spatial kernel g_s of eq. (BF).  GAUSS: exp(-k^2 / (2 sigma_s^2)) per
+ * axis, R = ceil(3 sigma_s).  BOX: the constant filter that Sec. 4 uses to
+ * compare SHIFTABLE-BF with BF2 (whose integral histograms work only for
+ * box filters); there sigma_s is the radius of the box, so it must be an
+ * integer >= 1 (else BF_ERR_INVALID_ARG), R = sigma_s, and every pixel of
+ * the clipped (2R+1)^2 square weighs 1.  T (Algorithm 1) is taken over the
+ * same square.  The box runs through the FIR, tensor-core, batch and
+ * adjoint kernels with unit taps (cost per pixel as the Gaussian's of the
+ * same R); BOX with filter = YVV is BF_ERR_NOT_SUPPORTED. */
+enum { BF_SPATIAL_GAUSS = 0, BF_SPATIAL_BOX = 1 };
+
 /* Storage / multiply type of the modulated planes. */
 enum { BF_PLANES_FP32 = 0, BF_PLANES_BF16 = 1, BF_PLANES_FP16 = 2 };
 
@@ -114,7 +126,8 @@ typedef struct bf_options {
                             and 64-row tiles otherwise.                           */
     long long spin_limit;/* iteration bound of device waits; default 1<<22,
                             at least 1<<16 (smaller values are raised)            */
-    int reserved[8];     /* must be zero                                          */
+    int spatial;         /* BF_SPATIAL_*; default GAUSS                           */
+    int reserved[7];     /* must be zero                                          */
 } bf_options;
 
 /* Fills *opt with the defaults listed above. */

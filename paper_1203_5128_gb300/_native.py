@@ -26,6 +26,7 @@ BF_T_FIXED, BF_T_GLOBAL, BF_T_TILE = 0, 1, 2
 BF_RULE_ALG2, BF_RULE_TRUNC, BF_RULE_CHERNOFF = 0, 1, 2
 BF_FILTER_AUTO, BF_FILTER_FIR, BF_FILTER_YVV = 0, 1, 2
 BF_PLANES_FP32, BF_PLANES_BF16, BF_PLANES_FP16 = 0, 1, 2
+BF_SPATIAL_GAUSS, BF_SPATIAL_BOX = 0, 1
 BF_DEV_ORDER_TOO_LARGE, BF_DEV_TIMEOUT, BF_DEV_BAD_WORK = 1, 2, 4
 
 
@@ -40,7 +41,8 @@ class bf_options(ctypes.Structure):
         ("n_max", ctypes.c_int),
         ("t_tile", ctypes.c_int),
         ("spin_limit", ctypes.c_longlong),
-        ("reserved", ctypes.c_int * 8),
+        ("spatial", ctypes.c_int),
+        ("reserved", ctypes.c_int * 7),
     ]
 
 

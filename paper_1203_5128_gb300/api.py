@@ -17,6 +17,7 @@ T_MODES = {"fixed": nat.BF_T_FIXED, "global": nat.BF_T_GLOBAL, "tile": nat.BF_T_
 RULES = {"alg2": nat.BF_RULE_ALG2, "trunc": nat.BF_RULE_TRUNC, "chernoff": nat.BF_RULE_CHERNOFF}
 FILTERS = {"auto": nat.BF_FILTER_AUTO, "fir": nat.BF_FILTER_FIR, "yvv": nat.BF_FILTER_YVV}
 PLANES = {"fp32": nat.BF_PLANES_FP32, "bf16": nat.BF_PLANES_BF16, "fp16": nat.BF_PLANES_FP16}
+SPATIALS = {"gauss": nat.BF_SPATIAL_GAUSS, "box": nat.BF_SPATIAL_BOX}
 
 
 def _stream_ptr(stream=None) -> int:
@@ -40,10 +41,11 @@ def bf_status_string(code: int) -> str:
 def bf_options_init(**kw) -> nat.bf_options:
     """bf_options with the library defaults, then keyword overrides
     (t_mode, t_fixed, value_range, trunc_rule, filter, plane_dtype, n_max,
-    t_tile, spin_limit; enum fields accept their lower-case names)."""
+    t_tile, spin_limit, spatial; enum fields accept their lower-case names)."""
     o = nat.bf_options()
     nat.lib().bf_options_init(ctypes.byref(o))
-    table = {"t_mode": T_MODES, "trunc_rule": RULES, "filter": FILTERS, "plane_dtype": PLANES}
+    table = {"t_mode": T_MODES, "trunc_rule": RULES, "filter": FILTERS, "plane_dtype": PLANES,
+             "spatial": SPATIALS}
     fields = {name for name, _ in nat.bf_options._fields_ if name != "reserved"}
     for k, v in kw.items():
         if k not in fields:

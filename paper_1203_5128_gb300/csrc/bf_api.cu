@@ -338,6 +338,7 @@ void bf_options_init(bf_options* o)
     o->n_max = 4096;
     o->t_tile = 64;
     o->spin_limit = 1ll << 22;
+    o->spatial = BF_SPATIAL_GAUSS;
 }
 
 const char* bf_status_string(bf_status s)
@@ -373,8 +374,13 @@ bf_status bf_plan(int H, int W, double sigma_s, double sigma_r, double eps, cons
     if (!(o.value_range > 0.f) || !isfinite(o.value_range)) return BF_ERR_INVALID_ARG;
     if (o.n_max < 1) return BF_ERR_INVALID_ARG;
     if (o.n_max > 4096) return BF_ERR_NOT_SUPPORTED;
-    for (int i = 0; i < 8; ++i)
+    for (int i = 0; i < (int)(sizeof(o.reserved) / sizeof(o.reserved[0])); ++i)
         if (o.reserved[i]) return BF_ERR_INVALID_ARG;
+    // the box filter (Sec. 4): sigma_s is its radius, a whole number of pixels
+    const bool box = o.spatial == BF_SPATIAL_BOX;
+    if (o.spatial != BF_SPATIAL_GAUSS && !box) return BF_ERR_INVALID_ARG;
+    if (box && (sigma_s < 1.0 || sigma_s != floor(sigma_s))) return BF_ERR_INVALID_ARG;
+    if (box && o.filter == BF_FILTER_YVV) return BF_ERR_NOT_SUPPORTED;
     if (o.filter == BF_FILTER_AUTO) o.filter = BF_FILTER_FIR;
     if (o.filter != BF_FILTER_FIR && o.filter != BF_FILTER_YVV) return BF_ERR_INVALID_ARG;
     if (o.plane_dtype < BF_PLANES_FP32 || o.plane_dtype > BF_PLANES_FP16) return BF_ERR_INVALID_ARG;
@@ -395,7 +401,7 @@ bf_status bf_plan(int H, int W, double sigma_s, double sigma_r, double eps, cons
     // stopping CTA frees its TMEM: keep it far above their completion time
     if (o.spin_limit < kMinSpinLimit) o.spin_limit = kMinSpinLimit;
 
-    const double Rr = ceil(3.0 * sigma_s);
+    const double Rr = box ? sigma_s : ceil(3.0 * sigma_s);
     if (Rr > 1000.0) return BF_ERR_NOT_SUPPORTED;
     const int R = (int)Rr;
     if (o.t_mode != BF_T_FIXED && R > range_max_radius()) return BF_ERR_NOT_SUPPORTED;
@@ -464,7 +470,8 @@ bf_status bf_plan(int H, int W, double sigma_s, double sigma_r, double eps, cons
         free_plan(p);
         return BF_ERR_ALLOC;
     }
-    // spatial taps g(k) = exp(-k^2 / (2 sigma_s^2)) and the log(k!) table
+    // spatial taps g(k) = exp(-k^2 / (2 sigma_s^2)) (1 for the box) and the
+    // log(k!) table
     float* taps = (float*)malloc(sizeof(float) * (2 * R + 1));
     double* lf = (double*)malloc(sizeof(double) * (n_cap + 1));
     if (!taps || !lf) {
@@ -474,7 +481,7 @@ bf_status bf_plan(int H, int W, double sigma_s, double sigma_r, double eps, cons
         return BF_ERR_ALLOC;
     }
     for (int k = -R; k <= R; ++k)
-        taps[k + R] = (float)exp(-(double)k * (double)k / (2.0 * sigma_s * sigma_s));
+        taps[k + R] = box ? 1.f : (float)exp(-(double)k * (double)k / (2.0 * sigma_s * sigma_s));
     for (int k = 0; k <= n_cap; ++k) lf[k] = lgamma((double)k + 1.0);
     ok &= cudaMemcpy(p->d_taps, taps, sizeof(float) * (2 * R + 1), cudaMemcpyHostToDevice) ==
           cudaSuccess;

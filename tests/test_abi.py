@@ -53,7 +53,7 @@ def test_options_defaults(lib):
     lib.bf_options_init(ctypes.byref(o))
     assert o.t_mode == nat.BF_T_GLOBAL and o.value_range == 255.0
     assert o.trunc_rule == nat.BF_RULE_ALG2 and o.n_max == 4096 and o.t_tile == 64
-    assert o.plane_dtype == nat.BF_PLANES_FP32
+    assert o.plane_dtype == nat.BF_PLANES_FP32 and o.spatial == nat.BF_SPATIAL_GAUSS
 
 
 @pytest.mark.parametrize("args", [
@@ -94,6 +94,27 @@ def test_plan_rejects_bad_options(lib):
     o.t_tile = 64
     assert lib.bf_plan(64, 64, 1.0, 10.0, 0.0, ctypes.byref(o), ctypes.byref(h)) == \
         nat.BF_ERR_INVALID_ARG
+
+
+def test_plan_rejects_bad_box_options(lib):
+    """The box filter of Sec. 4 takes sigma_s as its radius: a whole number
+    >= 1.  It has no recursive form, and unknown spatial kinds are errors."""
+    from paper_1203_5128_gb300 import _native as nat
+    h = ctypes.c_void_p()
+    for sigma_s, spatial, filt, code in [(2.5, nat.BF_SPATIAL_BOX, nat.BF_FILTER_AUTO,
+                                          nat.BF_ERR_INVALID_ARG),
+                                         (0.5, nat.BF_SPATIAL_BOX, nat.BF_FILTER_FIR,
+                                          nat.BF_ERR_INVALID_ARG),
+                                         (3.0, nat.BF_SPATIAL_BOX, nat.BF_FILTER_YVV,
+                                          nat.BF_ERR_NOT_SUPPORTED),
+                                         (3.0, 2, nat.BF_FILTER_AUTO, nat.BF_ERR_INVALID_ARG),
+                                         (3.0, -1, nat.BF_FILTER_AUTO, nat.BF_ERR_INVALID_ARG)]:
+        o = nat.bf_options()
+        lib.bf_options_init(ctypes.byref(o))
+        o.spatial = spatial
+        o.filter = filt
+        assert lib.bf_plan(64, 64, sigma_s, 10.0, 0.0, ctypes.byref(o), ctypes.byref(h)) == code
+        assert not h.value
 
 
 def test_calls_reject_null_plan(lib):

@@ -21,6 +21,8 @@ def test_options_by_name():
     assert o.trunc_rule == api.RULES["chernoff"]
     d = api.bf_options_init()
     assert (d.t_mode, d.t_tile, d.n_max) == (api.T_MODES["global"], 64, 4096)
+    assert d.spatial == api.SPATIALS["gauss"]
+    assert api.bf_options_init(spatial="box").spatial == api.SPATIALS["box"]
 
 
 def test_unknown_option_name_is_an_error():
@@ -35,6 +37,8 @@ def test_unknown_enum_name_is_an_error():
         api.bf_options_init(t_mode="tiles")
     with pytest.raises(ValueError):
         api.bf_options_init(plane_dtype="fp8")
+    with pytest.raises(ValueError):
+        api.bf_options_init(spatial="disk")
 
 
 @pytest.mark.parametrize("bad", [

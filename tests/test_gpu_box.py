@@ -1,0 +1,219 @@
+"""GPU parity of the box spatial filter (BF_SPATIAL_BOX: the constant filter
+of radius sigma_s with which Sec. 4 compares SHIFTABLE-BF and BF2) against
+the oracle's box mode, through the C ABI.
+
+The box runs through the same kernels as the Gaussian with unit taps, so the
+bars are the Gaussian's: T, N, M bit-exact; FP32 planes within 1e-3 gray
+levels of the oracle with the same (T, N, M), plus FP32 roundoff times the
+pixel's condition number mass / den where den is a small part of the
+window's mass (every pixel of the window weighs 1, so the mass is the
+clipped window's pixel count); the adjoint within 1e-3 of max |grad|; the
+batch bitwise equal to separate calls.
+
+16-bit planes: within 0.5 gray level (FP16) or 2 (BF16) wherever den is
+more than 5 % of the window's mass, and everywhere within that plus the
+rounding bound of the stored planes.  Each plane value (at most 1 in
+magnitude after centring and scaling by c0 = value_range / 2) is rounded to
+16 bits twice, once as modulated and once after the first of the two
+separable passes, so each filtered plane is off by at most 2 u mass (u the
+unit roundoff, 2^-11 for FP16 and 2^-8 for BF16); num and den, sums over
+the kept terms with weights of total at most 1, are off by at most 4 u c0
+mass and 4 u mass, and out = num / den by at most 8 u c0 mass / den.  At a
+pixel unlike its whole window den is a tiny part of the mass (0.1 % in the
+radius-20, sigma_r = 5 setting) and the 16-bit result there can exceed the
+0.5 bar; the FP32 planes stay within theirs.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1203_5128_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+TOL8 = 1e-3
+TOL_LOWP = {"fp16": 0.5, "bf16": 2.0}
+U16 = {"fp16": 2.0 ** -11, "bf16": 2.0 ** -8}     # unit roundoff of the stored planes
+C0 = 127.5                                        # centring constant of 8-bit images
+
+
+def check_lowp(err, den, mass, planes, what):
+    """The 16-bit bar: TOL_LOWP where den > 5 % of the mass, and everywhere
+    TOL_LOWP plus the rounding bound 8 u c0 mass / den."""
+    well = den > 0.05 * mass
+    bound = TOL_LOWP[planes] + 8 * U16[planes] * C0 * mass / np.maximum(den, 1e-300)
+    print("box %s %s: max-abs %.3g gray levels, %.3g where den > 5%% of the window, "
+          "%d of %d outputs above %g, largest share of the rounding bound %.3g" % (
+              planes, what, err.max(), err[well].max() if well.any() else 0.0,
+              int(np.sum(err > TOL_LOWP[planes])), err.size, TOL_LOWP[planes],
+              float(np.max(err / bound))))
+    if well.any():
+        assert np.max(err[well]) <= TOL_LOWP[planes]
+    assert np.all(err <= bound)
+
+
+@pytest.fixture(scope="module")
+def bf():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need CUDA"
+    from paper_1203_5128_gb300 import build
+    build.build()
+    import paper_1203_5128_gb300 as m
+    return m
+
+
+def to_dev(a):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).cuda()
+
+
+def run(bf, f, R, sr, eps, mode="global", rule="alg2", tile=64, planes="fp32", t_fixed=None):
+    import torch
+    H, W = f.shape
+    kw = dict(t_mode=mode, trunc_rule=rule, t_tile=tile, plane_dtype=planes, spatial="box")
+    if t_fixed is not None:
+        kw["t_fixed"] = t_fixed
+    plan = bf.bf_plan(H, W, float(R), sr, eps, **kw)
+    out = bf.bf_execute(plan, to_dev(f))
+    torch.cuda.synchronize()
+    assert bf.bf_get_device_status(plan) == 0
+    assert bf.bf_get_info(plan).R == R
+    p = oracle.resolve(f, float(R), sr, eps, t_mode=mode, rule=rule, t_tile=tile,
+                       t_fixed=t_fixed, spatial="box")
+    T, N, M = bf.bf_get_sets(plan)
+    assert np.array_equal(T, p.T.ravel())
+    assert np.array_equal(N, p.N.ravel().astype(np.int32))
+    assert np.array_equal(M, p.M.ravel().astype(np.int32))
+    return plan, out.cpu().numpy().astype(np.float64), p
+
+
+def box_count(R, ys, xs, H, W):
+    """Pixels of the (2R+1)^2 square clipped to the image."""
+    ny = np.minimum(ys + R, H - 1) - np.maximum(ys - R, 0) + 1
+    nx = np.minimum(xs + R, W - 1) - np.maximum(xs - R, 0) + 1
+    return (ny * nx).astype(np.float64)
+
+
+def tol_fp32(den, mass, T):
+    return 1e-3 + 2.0 ** -24 * (mass / np.maximum(den, 1e-300)) * T
+
+
+def sample_points(H, W, n, seed, R, tile=128):
+    rng = np.random.default_rng(seed)
+    ys = list(rng.integers(0, H, n))
+    xs = list(rng.integers(0, W, n))
+    for y, x in [(0, 0), (H - 1, W - 1), (0, W - 1), (H - 1, 0), (tile - 1, tile),
+                 (tile, tile - 1), (H // 2, 0), (0, W // 2), (R, R), (H - 1 - R, W - 1 - R)]:
+        ys.append(min(max(y, 0), H - 1))
+        xs.append(min(max(x, 0), W - 1))
+    return np.array(ys), np.array(xs)
+
+
+FP32_CASES = [
+    # H, W, R, sigma_r, eps, mode, rule, tile
+    (120, 90, 3, 20.0, 0.01, "global", "alg2", 64),      # fused tall tile
+    (100, 77, 6, 15.0, 0.01, "tile", "trunc", 64),       # per-tile T, ragged
+    (70, 130, 12, 30.0, 0.0, "fixed", "alg2", 64),       # T = 255, no truncation
+    (300, 140, 20, 5.0, 0.01, "tile", "alg2", 128),      # the paper's radius 20, sigma_r = 5
+    (1, 200, 4, 20.0, 0.01, "global", "alg2", 64),       # one row
+    (64, 150, 30, 25.0, 0.01, "global", "alg2", 64),     # R = 30: two passes through HBM
+]
+
+
+@pytest.mark.parametrize("case", FP32_CASES, ids=lambda c: "%dx%d_R%d_r%g_%s" % (c[0], c[1], c[2], c[3], c[5]))
+def test_box_fp32_matches_oracle(bf, case):
+    H, W, R, sr, eps, mode, rule, tile = case
+    f = synth.g8(H, W, seed=H + 5 * W + R)
+    _, out, p = run(bf, f, R, sr, eps, mode, rule, tile,
+                    t_fixed=255.0 if mode == "fixed" else None)
+    ref, _, den, _ = oracle.shiftable(f, float(R), sr, p, return_parts=True, spatial="box")
+    yy, xx = np.mgrid[0:H, 0:W]
+    mass = box_count(R, yy, xx, H, W)
+    err = np.abs(out - ref)
+    well = den > 0.05 * mass
+    print("box FP32 %s: max-abs %.3g gray levels (%.3g where den > 5%% of the window)"
+          % (case, err.max(), err[well].max() if well.any() else 0.0))
+    assert np.all(err <= tol_fp32(den, mass, float(p.T.max())))
+    if well.any():
+        assert np.max(err[well]) <= TOL8
+
+
+@pytest.mark.parametrize("planes", ["fp16", "bf16"])
+@pytest.mark.parametrize("H,W,R,sr,mode", [(256, 160, 8, 10.0, "tile"), (200, 150, 20, 5.0, "global"),
+                                           (130, 33, 24, 20.0, "global")])
+def test_box_lowp_matches_oracle(bf, planes, H, W, R, sr, mode):
+    """16-bit planes on the tensor cores: the banded products take unit taps."""
+    f = synth.g8(H, W, seed=H + W + R)
+    _, out, p = run(bf, f, R, sr, 0.01, mode, "alg2", 128, planes)
+    ref, _, den, _ = oracle.shiftable(f, float(R), sr, p, return_parts=True, spatial="box")
+    yy, xx = np.mgrid[0:H, 0:W]
+    check_lowp(np.abs(out - ref), den, box_count(R, yy, xx, H, W), planes,
+               "%dx%d R=%d sigma_r=%g %s" % (H, W, R, sr, mode))
+
+
+@pytest.mark.parametrize("planes", ["fp32", "fp16"])
+def test_box_1024_sampled(bf, planes):
+    """1024^2 G8 in the paper's box setting (radius 20, sigma_r = 5,
+    eps = 1e-2) with exact T per 128 x 128 T-tile, sampled against the
+    oracle's direct form."""
+    f = synth.g8(1024, 1024, seed=1)
+    _, out, p = run(bf, f, 20, 5.0, 0.01, "tile", "alg2", 128, planes)
+    ys, xs = sample_points(1024, 1024, 80, seed=9, R=20)
+    ref, _, den, _ = oracle.direct(f, 20.0, 5.0, p, points=(ys, xs), return_parts=True,
+                                   spatial="box")
+    err = np.abs(out[ys, xs] - ref)
+    mass = box_count(20, ys, xs, 1024, 1024)
+    if planes == "fp32":
+        print("box 1024^2 fp32: max-abs %.3g gray levels at sampled outputs" % err.max())
+        assert np.all(err <= tol_fp32(den, mass, float(p.T.max())))
+    else:
+        check_lowp(err, den, mass, planes, "1024^2 sampled")
+
+
+def test_box_4096_bench_workload_sampled(bf):
+    """The bench's box workload (4096^2 G8, radius 20, sigma_r = 5,
+    eps = 1e-2, exact T per 128 x 128 T-tile, FP16 planes), sampled."""
+    f = synth.g8(4096, 4096, seed=5)
+    _, out, p = run(bf, f, 20, 5.0, 0.01, "tile", "alg2", 128, "fp16")
+    ys, xs = sample_points(4096, 4096, 40, seed=13, R=20)
+    ref, _, den, _ = oracle.direct(f, 20.0, 5.0, p, points=(ys, xs), return_parts=True,
+                                   spatial="box")
+    check_lowp(np.abs(out[ys, xs] - ref), den, box_count(20, ys, xs, 4096, 4096), "fp16",
+               "4096^2 sampled")
+
+
+@pytest.mark.parametrize("H,W,R,sr,mode", [(64, 80, 4, 25.0, "global"), (130, 96, 6, 30.0, "tile")])
+def test_box_backward_matches_oracle(bf, H, W, R, sr, mode):
+    """The adjoint with unit taps (the box is symmetric, so it is its own
+    adjoint) against the oracle's box gradient."""
+    import torch
+    f = synth.g8(H, W, seed=H * W + R)
+    u = synth.weights_normal((H, W), seed=R)
+    plan = bf.bf_plan(H, W, float(R), sr, 0.01, t_mode=mode, spatial="box")
+    fd = to_dev(f)
+    bf.bf_execute(plan, fd)
+    g = bf.bf_backward(plan, fd, to_dev(u))
+    torch.cuda.synchronize()
+    p = oracle.resolve(f, float(R), sr, 0.01, t_mode=mode, spatial="box")
+    ref = oracle.grad_shiftable(f, u.astype(np.float64), float(R), sr, p, spatial="box")
+    rel = float(np.max(np.abs(g.cpu().numpy() - ref)) / np.max(np.abs(ref)))
+    print("box adjoint %dx%d R=%d: %.3g of max |grad|" % (H, W, R, rel))
+    assert rel <= 1e-3
+
+
+def test_box_batch_bitwise(bf):
+    """Box and Gaussian plans in one batch reproduce separate calls bit for bit."""
+    import torch
+    specs = [(150, 90, 3.0, 20.0, "box"), (90, 200, 2.0, 30.0, "gauss"),
+             (64, 64, 10.0, 15.0, "box"), (200, 120, 1.5, 25.0, "gauss")]
+    plans, fs = [], []
+    for k, (H, W, ss, sr, sp) in enumerate(specs):
+        plans.append(bf.bf_plan(H, W, ss, sr, 0.01, spatial=sp))
+        fs.append(to_dev(synth.g8(H, W, seed=300 + k)))
+    ref = [bf.bf_execute(p, f) for p, f in zip(plans, fs)]
+    torch.cuda.synchronize()
+    ref = [r.cpu().numpy() for r in ref]
+    outs = bf.bf_execute_batch(plans, fs)
+    torch.cuda.synchronize()
+    for o, r in zip(outs, ref):
+        assert np.array_equal(o.cpu().numpy(), r)
