@@ -107,6 +107,53 @@ def test_tuned_metric_workload_sampled(bf, mode, tile):
     assert err <= 0.5
 
 
+def test_tuned_metric_workload_every_pixel_top_half(bf):
+    """Every output of the top half (rows 0..2047) of the tuned 4096^2
+    workload (exact T per 128 x 128 T-tile, FP16 planes) against the oracle
+    run on rows 0..2071: each output and each T of those T-tiles depends
+    only on rows within R = 24 of it, so the crop gives the image's values.
+
+    Bar: 0.5 gray level wherever den is more than 5 % of the window's
+    Gaussian mass, and everywhere 0.5 plus the rounding bound of the 16-bit
+    planes, 8 u c0 mass / den (u = 2^-11; each plane value, at most 1 in
+    magnitude after centring, is rounded to 16 bits as modulated and again
+    after the vertical pass, and num and den sum the kept terms with weights
+    of total at most 1).  At the few pixels unlike their whole window (den
+    under 0.5 % of the mass) the FP16 result can exceed 0.5."""
+    import torch
+    f = synth.g8(4096, 4096, seed=5)
+    plan = bf.bf_plan(4096, 4096, 8.0, 10.0, 0.01, t_mode="tile", t_tile=128, trunc_rule="alg2",
+                      plane_dtype="fp16")
+    out = bf.bf_execute(plan, to_dev(f))
+    torch.cuda.synchronize()
+    assert bf.bf_get_device_status(plan) == 0
+    out = out[:2048].cpu().numpy().astype(np.float64)
+    T, N, M = bf.bf_get_sets(plan)
+    R = 24
+    crop = f[:2048 + R]
+    p = oracle.resolve(crop, 8.0, 10.0, 0.01, t_mode="tile", t_tile=128, rule="alg2")
+    assert np.array_equal(T.reshape(32, 32)[:16], p.T[:16])
+    assert np.array_equal(N.reshape(32, 32)[:16], p.N[:16].astype(np.int32))
+    assert np.array_equal(M.reshape(32, 32)[:16], p.M[:16].astype(np.int32))
+    ref, _, den, _ = oracle.shiftable(crop, 8.0, 10.0, p, return_parts=True)
+    ref, den = ref[:2048], den[:2048]
+    g = oracle.taps(8.0, R)
+
+    def line(i, n):
+        return g[max(0, i - R) - i + R: min(n - 1, i + R) - i + R + 1].sum()
+
+    mass = np.outer([line(y, 4096) for y in range(2048)], [line(x, 4096) for x in range(4096)])
+    err = np.abs(out - ref)
+    well = den > 0.05 * mass
+    bound = 0.5 + 8 * 2.0 ** -11 * 127.5 * mass / den
+    print("tuned fp16 4096^2, top half: max-abs %.4g gray levels, %.4g where den > 5%% of the "
+          "window, %d of %d outputs above 0.5, largest share of the rounding bound %.3g" % (
+              err.max(), err[well].max(), int(np.sum(err > 0.5)), err.size,
+              float(np.max(err / bound))))
+    assert np.max(err[well]) <= 0.5
+    assert np.all(err <= bound)
+
+
 @pytest.mark.parametrize("planes", ["fp16", "bf16"])
 def test_order_cap_passes_image_through(bf, planes):
     """A set whose N exceeds the plan's cap passes its pixels through (and
