@@ -17,7 +17,11 @@ strings the steps together in the order of Algorithm 2:
 
 Parity status: every function here is pinned by ``tests/test_oracle_pins.py``
 (closed forms, invariants, brute force, exact rational arithmetic and the
-values the paper prints).  The Young-van Vliet mode (``spatial="yvv"``) is
+values the paper prints).  The denominator guard (where den <= 1e-6 of the
+clipped spatial mass the output is f(x); the paper is silent) and the
+clipped mass it uses are pinned by ``tests/test_oracle_guard.py`` against
+den, num and mass computed in plain Python at outliers tuned to either
+side of the threshold at the image border.  The Young-van Vliet mode (``spatial="yvv"``) is
 pinned by ``tests/test_oracle_yvv.py`` against the recursion's closed-form
 frequency response, brute-force convolution with its impulse response and
 the direct form; the paper prints no value for it.  The box mode
