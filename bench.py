@@ -5,7 +5,9 @@ Workload (the headline metric): one 4096 x 4096 8-bit-range image (seeded
 G8 generator), sigma_s = 8 (R = 24), sigma_r = 10.
   * tuned: Algorithm 2 of the paper -- exact T (Algorithm 1), eps = 1e-2
     truncation by the sigma_r <= 10 rule (Chernoff) -- with FP16 planes
-    filtered on the tensor cores (FP32 phases, demodulation and accumulation);
+    filtered on the tensor cores (FP32 phases, demodulation and accumulation),
+    and the FP32 recheck of the outputs whose denominator is under 5 % of
+    their window's mass (so that max-abs <= 0.5 holds at every pixel);
   * plain: the unaccelerated method, T = 255, no truncation, FP32 planes.
 A step is one bf_execute (T, N/M/weights, fused filter) of one image with its
 input resident in HBM; the L2 is flushed (256 MB write) before every timed
@@ -44,9 +46,9 @@ BOX_TUNED = dict(TUNED, spatial="box")
 BOX_FP32 = dict(TUNED_FP32, spatial="box")
 SM_COUNT_NOMINAL = 152
 # DRAM bytes of one k_fwd_tc launch on the tuned 4096^2 workload, read + write,
-# from an ncu capture of the kernel as built (67.77 MB + 23.50 MB); set to None
-# whenever the kernel changes until it is captured again
-K3TC_DRAM_BYTES = 67768576 + 23501824
+# from an ncu capture of the kernel as built; None whenever the kernel has
+# changed since the last capture
+K3TC_DRAM_BYTES = None
 FP32_LANES_PER_SM = 128
 
 
@@ -58,7 +60,9 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--plain-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--oracle-rows", type=int, default=H,
+                    help="output rows the CPU oracle computes (timed baseline and every-pixel "
+                         "parity of the tuned output); default the whole image")
     return ap.parse_args()
 
 
@@ -152,26 +156,22 @@ def oracle_crop(f64, p, y0, side):
     return time.perf_counter() - t0
 
 
-def cpu_oracle_run(f_np, seconds_target: float):
-    """Times the FP64 oracle (SHIFTABLE-BF with the tuned form's Algorithm 2
-    parameters, from the oracle itself) on a centred crop of the image,
-    sized to take about `seconds_target`.  Returns (Mpx/s, crop side,
-    seconds, threads)."""
+def cpu_oracle_rows(f_np, rows):
+    """The FP64 oracle (SHIFTABLE-BF with the tuned form's Algorithm 2
+    parameters, from the oracle itself) on output rows 0 .. rows-1 (the whole
+    image when rows >= H), timed.  Each output, and the T of each 128-row
+    T-tile, depends only on the input rows within R of it, so the oracle runs
+    on the rows + R first rows.  Returns (Mpx/s, seconds, threads, output)."""
     import numpy as np
     import oracle
-    p = oracle_tuned_params(f_np)
-    f64 = np.ascontiguousarray(f_np, dtype=np.float64)
-
-    def run(side):
-        return oracle_crop(f64, p, (H - side) // 2, side)
-
-    side = 32
-    dt = run(side)
-    # cost ~ side^2: grow the crop (up to the whole image) to the time target
-    while dt < seconds_target / 3 and side < min(H, W):
-        side = min(2 * side, min(H, W))
-        dt = run(side)
-    return side * side / dt / 1e6, side, dt, oracle.num_threads()
+    R = oracle.radius(SIGMA_S)
+    rows = min(rows, H)
+    crop = np.ascontiguousarray(f_np[:min(H, rows + R)], dtype=np.float64)
+    t0 = time.perf_counter()
+    p = oracle_tuned_params(crop)
+    ref = oracle.shiftable(crop, SIGMA_S, SIGMA_R, p)[:rows]
+    dt = time.perf_counter() - t0
+    return rows * W / dt / 1e6, dt, oracle.num_threads(), ref
 
 
 def reference_arm(args, rank: int):
@@ -273,6 +273,113 @@ def fir_flops_per_px(N, M, R):
     return (F + z) * 4 * 2 * (2 * R + 1) * 2
 
 
+# the precision workload: 4096^2 G16 (16-bit range), sigma_s = 8, sigma_r =
+# 2000, exact T of the image, no truncation, FP32 / BF16 / FP16 planes
+PREC = dict(sigma_s=8.0, sigma_r=2000.0, eps=0.0, value_range=65535.0, seed=2)
+# the accelerations' sweep: 1024^2 G8, sigma_s in {5, 10} x sigma_r in {10, 20}
+C1_SIDE, C1_SEED = 1024, 1
+
+
+def sample_pixels(n, seed, side_h=H, side_w=W, tile=128):
+    """Random pixels plus corners, borders and T-tile seams."""
+    import numpy as np
+    rng = np.random.default_rng(seed)
+    ys = list(rng.integers(0, side_h, n))
+    xs = list(rng.integers(0, side_w, n))
+    for y, x in [(0, 0), (side_h - 1, side_w - 1), (0, side_w - 1), (side_h - 1, 0),
+                 (tile - 1, tile), (tile, tile - 1), (side_h // 2, 0), (0, side_w // 2)]:
+        ys.append(y)
+        xs.append(x)
+    return np.array(ys), np.array(xs)
+
+
+def precision_leg(bf, timed_on, steps, world, max_over_ranks):
+    """The precision workload with each plane type: Mpixel/s and the max-abs
+    error (16-bit gray levels) against the FP64 oracle's direct form with
+    the same T, N, M at sampled pixels."""
+    import numpy as np
+    import torch
+    import oracle
+    from paper_1203_5128_gb300 import synth
+    f_np = synth.g16(H, W, seed=PREC["seed"])
+    f = torch.from_numpy(f_np).cuda()
+    out = torch.empty_like(f)
+    p = oracle.resolve(f_np, PREC["sigma_s"], PREC["sigma_r"], PREC["eps"], t_mode="global",
+                       rule="alg2", value_range=PREC["value_range"])
+    ys, xs = sample_pixels(48, seed=17)
+    ref = oracle.direct(f_np, PREC["sigma_s"], PREC["sigma_r"], p, points=(ys, xs))
+    res = {"workload": "4096x4096 G16 16-bit image, sigma_s=8 (R=24), sigma_r=2000, exact T of "
+                       "the image, eps=0 (K = N+1 terms)",
+           "T": float(p.T[0, 0]), "N": int(p.N[0, 0]),
+           "error_unit": "16-bit gray levels, at %d sampled pixels vs the FP64 oracle (direct "
+                         "form, same T, N, M)" % ys.size}
+    for planes in ("fp32", "bf16", "fp16"):
+        plan = bf.bf_plan(H, W, PREC["sigma_s"], PREC["sigma_r"], PREC["eps"], t_mode="global",
+                          trunc_rule="alg2", value_range=PREC["value_range"], plane_dtype=planes)
+        ms, kms, cnt = timed_on(plan, f, out, steps, 1)
+        ms = max_over_ranks(ms)
+        o = out.cpu().numpy().astype(np.float64)
+        info = bf.bf_get_info(plan)
+        res[planes] = {"value": world * H * W * steps / (ms * 1e3), "unit": "Mpixel/s",
+                       "ms_per_step": ms / steps, "forward_ms": kms[2] / max(cnt, 1),
+                       "recheck_ms": kms[3] / max(cnt, 1), "rechecked": info.n_rechecked,
+                       "max_abs": float(np.max(np.abs(o[ys, xs] - ref)))}
+        plan.close()
+    return res
+
+
+def config1_leg(bf, timed_on, steps, world, max_over_ranks):
+    """The accelerations' sweep at 1024^2 (FP32 planes): Algorithm 2 (eps =
+    1e-2) with exact T of the image and per 128 x 128 T-tile, against the
+    plain method (T = 255, eps = 0), per (sigma_s, sigma_r) cell."""
+    import torch
+    from paper_1203_5128_gb300 import synth
+    f = torch.from_numpy(synth.g8(C1_SIDE, C1_SIDE, seed=C1_SEED)).cuda()
+    out = torch.empty_like(f)
+    px = C1_SIDE * C1_SIDE
+    cells = []
+    for ss in (5.0, 10.0):
+        for sr in (10.0, 20.0):
+            cell = {"sigma_s": ss, "sigma_r": sr}
+            for name, eps, opts in (("plain", 0.0, PLAIN),
+                                    ("accel_global", EPS, dict(TUNED_FP32, t_mode="global")),
+                                    ("accel_tile", EPS, TUNED_FP32)):
+                plan = bf.bf_plan(C1_SIDE, C1_SIDE, ss, sr, eps, **opts)
+                ms, _, _ = timed_on(plan, f, out, steps, 1)
+                ms = max_over_ranks(ms)
+                info = bf.bf_get_info(plan)
+                cell[name] = {"value": world * px * steps / (ms * 1e3), "ms": ms / steps,
+                              "max_K": info.K, "terms_total": info.terms_total}
+                plan.close()
+            cell["speedup_global"] = cell["accel_global"]["value"] / cell["plain"]["value"]
+            cell["speedup_tile"] = cell["accel_tile"]["value"] / cell["plain"]["value"]
+            cells.append(cell)
+    return {"workload": "1024x1024 G8, FP32 planes; accel = Algorithm 2 (eps=1e-2) with exact T "
+                        "(image or 128x128 T-tile), plain = T=255, eps=0", "unit": "Mpixel/s",
+            "cells": cells}
+
+
+def divergence(f_np, tuned_out, n=300, seed=23):
+    """Deviation of the tuned output from the direct Gaussian bilateral filter
+    (eq. (BF), Gaussian range kernel) and from the plain-parameter method
+    (T = 255, eps = 0), at sampled pixels: max-abs and MSE in gray levels
+    (the paper's Table 6 reports 10 log10 MSE against the direct filter)."""
+    import numpy as np
+    import oracle
+    ys, xs = sample_pixels(n, seed)
+    got = tuned_out[ys, xs].astype(np.float64)
+    gauss = oracle.direct(f_np, SIGMA_S, SIGMA_R, points=(ys, xs), gauss=True)
+    pp = oracle.resolve(f_np, SIGMA_S, SIGMA_R, 0.0, t_mode="fixed", t_fixed=255.0)
+    plain = oracle.direct(f_np, SIGMA_S, SIGMA_R, pp, points=(ys, xs))
+    res = {"pixels": int(ys.size)}
+    for name, ref in (("vs_direct_gaussian", gauss), ("vs_plain_parameters", plain)):
+        d = got - ref
+        mse = float(np.mean(d * d))
+        res[name] = {"max_abs": float(np.max(np.abs(d))), "mse": mse,
+                     "10log10_mse": float(10 * np.log10(mse)) if mse > 0 else None}
+    return res
+
+
 def box_leg(bf, timed, steps, world, max_over_ranks):
     """The box spatial filter on the bench image: radius BOX_R, sigma_r =
     BOX_SIGMA_R, eps = EPS, exact T per 128 x 128 T-tile, with FP16 planes on
@@ -339,9 +446,9 @@ def main():
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     stream = torch.cuda.current_stream()
 
-    def timed(plan, steps, warmup):
+    def timed_on(plan, f_in, f_out, steps, warmup):
         for _ in range(warmup):
-            bf.bf_execute(plan, f, out)
+            bf.bf_execute(plan, f_in, f_out)
         barrier()
         bf.bf_set_timing(plan, True)
         evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
@@ -349,13 +456,16 @@ def main():
         for a, b in evs:
             flush.zero_()
             a.record(stream)
-            bf.bf_execute(plan, f, out)
+            bf.bf_execute(plan, f_in, f_out)
             b.record(stream)
         barrier()
         total = sum(a.elapsed_time(b) for a, b in evs)
         kms, cnt = bf.bf_get_timing(plan)
         bf.bf_set_timing(plan, False)
         return total, kms, cnt
+
+    def timed(plan, steps, warmup):
+        return timed_on(plan, f, out, steps, warmup)
 
     # ---- tuned (the headline)
     tuned = bf.bf_plan(H, W, SIGMA_S, SIGMA_R, EPS, **TUNED)
@@ -370,7 +480,10 @@ def main():
     total_ms = max_over_ranks(total_ms)
     px = H * W
     value = world * px * args.steps / (total_ms * 1e3)
-    launches_per_step = 3 if TUNED["t_mode"] != "fixed" else 2
+    # K1 (T), K2 (N, M, weights), K3-tc and the FP32 recheck
+    launches_per_step = 4 if TUNED["t_mode"] != "fixed" else 3
+    tuned_out = out.cpu().numpy()
+    info_t = bf.bf_get_info(tuned)
 
     # ---- the same Algorithm 2 with FP32 planes (the fused FP32 path)
     t32 = bf.bf_plan(H, W, SIGMA_S, SIGMA_R, EPS, **TUNED_FP32)
@@ -467,6 +580,13 @@ def main():
     # ---- the box spatial filter (Sec. 4's setting), tuned form
     box = box_leg(bf, timed, max(1, min(args.plain_steps, args.steps)), world, max_over_ranks)
 
+    # ---- the precision workload (16-bit image, large N) with each plane type
+    small_steps = max(1, min(args.plain_steps, args.steps))
+    precision = precision_leg(bf, timed_on, small_steps, world, max_over_ranks)
+
+    # ---- the accelerations' sweep at 1024^2 (accel vs plain per cell)
+    config1 = config1_leg(bf, timed_on, small_steps, world, max_over_ranks)
+
     # ---- plain FP32 (context for the metric's ratio)
     plain = bf.bf_plan(H, W, SIGMA_S, SIGMA_R, 0.0, **PLAIN)
     bf.bf_execute(plain, f, out)
@@ -542,11 +662,20 @@ def main():
     p_instr = fp32_instr_per_px(info_p.N, info_p.M, info_p.R) * px
 
     cpu = None
+    every_pixel = None
+    div = None
     if not args.no_cpu_baseline and world == 1:
-        v, side, dt, thr = cpu_oracle_run(f_np, args.cpu_seconds)
+        rows = min(args.oracle_rows, H)
+        v, dt, thr, ref = cpu_oracle_rows(f_np, rows)
         cpu = {"value": v, "unit": "Mpixel/s", "cores": thr, "kind": "oracle",
-               "sample": "centred %dx%d crop of the tuned workload (FP64 shiftable oracle with the "
-                         "tuned form's per-tile T, N, M; %.1f s)" % (side, side, dt)}
+               "sample": "output rows 0..%d of the 4096x4096 tuned workload (FP64 shiftable "
+                         "oracle with the tuned form's per-tile T, N, M, found by the oracle; "
+                         "%.1f s)" % (rows - 1, dt)}
+        err = np.abs(tuned_out[:rows].astype(np.float64) - ref)
+        every_pixel = {"max_abs": float(err.max()), "outputs": int(err.size),
+                       "above_0.5": int(np.sum(err > 0.5)),
+                       "vs": "FP64 oracle, same per-tile T, N, M, every output"}
+        div = divergence(f_np, tuned_out)
 
     line = {
         "metric": METRIC, "value": value, "unit": "Mpixel/s", "n_gpus": world,
@@ -563,11 +692,12 @@ def main():
                   "mean_terms": float(np.mean([(int(n) - int(m)) - int(n) // 2 + (1 - int(n) % 2)
                                                for n, m in zip(N_, M_)])),
                   "kernel_ms": {"range": kms[0] / max(cnt, 1), "params": kms[1] / max(cnt, 1),
-                                "forward": k3_ms},
-                  "parity": "vs the FP64 oracle with the same per-tile T, N, M (tests): <= 0.5 "
-                            "gray level wherever den > 5% of the window mass; at pixels unlike "
-                            "their whole window the FP16 rounding is amplified by mass/den (18 of "
-                            "8.4M outputs of the top half above 0.5, max 1.24)"},
+                                "forward": k3_ms, "recheck": kms[3] / max(cnt, 1)},
+                  "rechecked": info_t.n_rechecked, "guarded": info_t.n_guarded,
+                  "every_pixel": every_pixel,
+                  "parity": "every output vs the FP64 oracle with the same per-tile T, N, M: "
+                            "see every_pixel (outputs whose den is under 5% of the window mass "
+                            "are recomputed in FP32 by the recheck kernel)"},
         "plain": {"value": plain_value, "ms_per_step": p_ms / p_steps, "N": info_p.N,
                   "K": info_p.K, "forward_ms": p_k3,
                   "fp32_frac": p_instr / (p_k3 * 1e-3) / 1e12 / peak_tinst},
@@ -590,6 +720,9 @@ def main():
                      "value": world * 16 * 512 * 512 / (d_ms * 1e3), "unit": "Mpixel/s",
                      "ms": d_ms},
         "box": box,
+        "precision": precision,
+        "config1": config1,
+        "divergence": div,
     }
     print(json.dumps(line), flush=True)
     reps.close()

@@ -127,7 +127,16 @@ typedef struct bf_options {
     long long spin_limit;/* iteration bound of device waits; default 1<<22,
                             at least 1<<16 (smaller values are raised)            */
     int spatial;         /* BF_SPATIAL_*; default GAUSS                           */
-    int reserved[7];     /* must be zero                                          */
+    float lowp_recheck;  /* 16-bit planes only: an output whose denominator is
+                            below lowp_recheck x its clipped spatial mass
+                            (g * 1_Omega)(x) is recomputed in FP32 after the
+                            tensor-core pass, by the direct sum of eq. (BF)
+                            with phi_eps over its window (bf_info.n_rechecked
+                            counts them).  At such pixels (unlike most of
+                            their window) the 16-bit rounding of the planes
+                            is amplified by mass / den.  Default 0.05; 0
+                            turns the recheck off; must lie in [0, 1).     */
+    int reserved[6];     /* must be zero                                          */
 } bf_options;
 
 /* Fills *opt with the defaults listed above. */
@@ -190,6 +199,7 @@ typedef struct bf_info {
     unsigned device_status; /* BF_DEV_* bits (not cleared)                      */
     int filter, plane_dtype, t_mode;
     int tile_h, tile_w;     /* output tile of the forward kernel                */
+    long long n_rechecked;  /* outputs recomputed in FP32 (lowp_recheck)        */
 } bf_info;
 
 /* Synchronises the plan's last stream and reports the parameters the last
@@ -213,13 +223,15 @@ const char *bf_status_string(bf_status s);
 /* ---- device timing of the plan's own launches -------------------------- */
 
 /* on != 0: every later bf_execute of this plan records CUDA events on its
- * stream around K1 (range/T), K2 (N, M, weights) and K3 (fused filter), up
- * to 4096 executes.  Costs four event records per execute. */
+ * stream around K1 (range/T), K2 (N, M, weights), K3 (fused filter) and
+ * the FP32 recheck of 16-bit plans (lowp_recheck), up to 4096 executes.
+ * Costs five event records per execute. */
 bf_status bf_set_timing(bf_plan_t plan, int on);
 
 /* Synchronises and returns, summed over the executes recorded since the
- * last call, the device milliseconds of ms[0] = K1, ms[1] = K2, ms[2] = K3
- * and their number in *count; then forgets them. */
+ * last call, the device milliseconds of ms[0] = K1, ms[1] = K2, ms[2] = K3,
+ * ms[3] = the recheck (0 when none runs; ms must hold 4 doubles) and their
+ * number in *count; then forgets them. */
 bf_status bf_get_timing(bf_plan_t plan, double *ms, int *count);
 
 /* ---- allocation-free variant ------------------------------------------- */
@@ -240,7 +252,10 @@ bf_status bf_get_timing(bf_plan_t plan, double *ms, int *count);
  * for an image within [0, value_range], ceil(4 value_range^2 / (pi^2
  * sigma_r^2)), <= 1024 (else BF_ERR_ORDER_TOO_LARGE); pixels outside
  * [0, value_range] may push N past the table, and then the output is a copy
- * of the input.  The first call on a device looks up the array's device
+ * of the input and the call still returns BF_OK: the status bit that
+ * records it is read with bf_noalloc_device_status.  Radii above 24 run on
+ * the fused kernel's small tiles (there is no two-pass workspace), so they
+ * cost far more per pixel than a plan's two-pass path.  The first call on a device looks up the array's device
  * address (cudaGetSymbolAddress) with that device current; make that first
  * call before any stream capture.  Every call reuses the same array and
  * clears what must start at zero, so calls whose work overlaps on the GPU
@@ -249,6 +264,15 @@ bf_status bf_get_timing(bf_plan_t plan, double *ms, int *count);
 bf_status bf_execute_noalloc(const float *f_dev, size_t f_pitch, float *out_dev,
                              size_t out_pitch, int H, int W, double sigma_s,
                              double sigma_r, double eps, float value_range, void *stream);
+
+/* Device status of bf_execute_noalloc calls on the current device: waits
+ * for `stream`, copies the static scratch's status word (BF_DEV_* bits) to
+ * *bits (may be NULL), clears it on `stream` and returns
+ * BF_ERR_DEVICE_STATUS if any bit was set.  BF_DEV_ORDER_TOO_LARGE means an
+ * image had pixels outside [0, value_range] whose local range needed an
+ * order above the table: that call's output was a copy of its input.
+ * Allocates nothing. */
+bf_status bf_noalloc_device_status(void *stream, unsigned *bits);
 
 /* ---- single steps of the path (tests and profiling) ------------------- */
 

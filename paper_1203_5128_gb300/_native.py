@@ -42,7 +42,8 @@ class bf_options(ctypes.Structure):
         ("t_tile", ctypes.c_int),
         ("spin_limit", ctypes.c_longlong),
         ("spatial", ctypes.c_int),
-        ("reserved", ctypes.c_int * 7),
+        ("lowp_recheck", ctypes.c_float),
+        ("reserved", ctypes.c_int * 6),
     ]
 
 
@@ -57,6 +58,7 @@ class bf_info(ctypes.Structure):
         ("device_status", ctypes.c_uint),
         ("filter", ctypes.c_int), ("plane_dtype", ctypes.c_int), ("t_mode", ctypes.c_int),
         ("tile_h", ctypes.c_int), ("tile_w", ctypes.c_int),
+        ("n_rechecked", ctypes.c_longlong),
     ]
 
 
@@ -78,6 +80,7 @@ PROTOTYPES = {
     "bf_maxmin": (_I, [_P, _I, _I, _Z, _I, _P, _P, _P]),
     "bf_set_timing": (_I, [_P, _I]),
     "bf_execute_noalloc": (_I, [_P, _Z, _P, _Z, _I, _I, _D, _D, _D, ctypes.c_float, _P]),
+    "bf_noalloc_device_status": (_I, [_P, ctypes.POINTER(ctypes.c_uint)]),
     "bf_get_timing": (_I, [_P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(_I)]),
 }
 

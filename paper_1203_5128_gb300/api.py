@@ -41,7 +41,8 @@ def bf_status_string(code: int) -> str:
 def bf_options_init(**kw) -> nat.bf_options:
     """bf_options with the library defaults, then keyword overrides
     (t_mode, t_fixed, value_range, trunc_rule, filter, plane_dtype, n_max,
-    t_tile, spin_limit, spatial; enum fields accept their lower-case names)."""
+    t_tile, spin_limit, spatial, lowp_recheck; enum fields accept their
+    lower-case names)."""
     o = nat.bf_options()
     nat.lib().bf_options_init(ctypes.byref(o))
     table = {"t_mode": T_MODES, "trunc_rule": RULES, "filter": FILTERS, "plane_dtype": PLANES,
@@ -78,6 +79,7 @@ class Info:
     t_mode: int
     tile_h: int
     tile_w: int
+    n_rechecked: int
 
 
 class Plan:
@@ -203,11 +205,12 @@ def bf_set_timing(plan: Plan, on: bool = True):
 
 
 def bf_get_timing(plan: Plan):
-    """(ms_K1, ms_K2, ms_K3) summed over the timed executes, and their count."""
-    ms = (ctypes.c_double * 3)()
+    """(ms_K1, ms_K2, ms_K3, ms_recheck) summed over the timed executes, and
+    their count."""
+    ms = (ctypes.c_double * 4)()
     n = ctypes.c_int()
     nat.check(nat.lib().bf_get_timing(plan.handle, ms, ctypes.byref(n)), "bf_get_timing")
-    return (ms[0], ms[1], ms[2]), n.value
+    return (ms[0], ms[1], ms[2], ms[3]), n.value
 
 
 def bf_destroy(plan: Plan):

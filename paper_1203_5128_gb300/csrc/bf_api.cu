@@ -29,6 +29,7 @@ namespace {
 
 constexpr double kPi = 3.14159265358979323846;
 constexpr int kMaxTimed = 4096;
+constexpr int kEvPerExec = 5;     // before K1, after K1, K2, K3, recheck
 
 int order_of(double T, double sigma_r)
 {
@@ -68,8 +69,10 @@ void free_plan(bf_plan_s* p)
     cudaFree(p->d_sep_P);
     cudaFree(p->d_sep_nd);
     cudaFree(p->d_bwd);
+    cudaFree(p->d_fix);
+    cudaFree(p->d_fixcnt);
     if (p->ev) {
-        for (int i = 0; i < 4 * kMaxTimed; ++i)
+        for (int i = 0; i < kEvPerExec * kMaxTimed; ++i)
             if (p->ev[i]) cudaEventDestroy(p->ev[i]);
         free(p->ev);
     }
@@ -162,14 +165,43 @@ FwdArgs forward_args(bf_plan_s* p, const float* f, size_t fp, float* out, size_t
     a.sep_nk = p->sep_nk;
     a.sep_Wp = p->sep_Wp;
     a.sep_cap_terms = p->cap_pairs + 1;
+    if (p->d_fix) {
+        a.fix_list = p->d_fix;
+        a.fix_count = p->d_fixcnt;
+        a.fix_kappa = p->opt.lowp_recheck;
+    }
     return a;
+}
+
+// The FP32 recheck of what a 16-bit forward with these arguments listed.
+FixArgs fixup_args(bf_plan_s* p, const FwdArgs& fa)
+{
+    FixArgs x;
+    x.f = fa.f;
+    x.f_pitch = fa.f_pitch;
+    x.out = fa.out;
+    x.out_pitch = fa.out_pitch;
+    x.H = p->H;
+    x.W = p->W;
+    x.R = p->R;
+    x.taps = p->d_taps;
+    x.hdr = p->d_hdr;
+    x.pairs = p->d_pairs;
+    x.cap_pairs = p->cap_pairs;
+    x.set_tile = fa.set_tile;
+    x.sets_x = p->sets_x;
+    x.sigma_r = p->sigma_r;
+    x.list = fa.fix_list;
+    x.count = fa.fix_count;
+    x.n_guarded = p->d_nguard;
+    return x;
 }
 
 // Event k (0..3) of the current timed execute, or null when not timing.
 static cudaEvent_t timing_event(bf_plan_s* p, int k)
 {
     if (!p->timing || p->n_timed >= kMaxTimed) return nullptr;
-    return p->ev[4 * p->n_timed + k];
+    return p->ev[kEvPerExec * p->n_timed + k];
 }
 
 static cudaError_t mark(bf_plan_s* p, int k, cudaStream_t s)
@@ -192,6 +224,10 @@ cudaError_t enqueue_params(bf_plan_s* p, const float* f, size_t fp, cudaStream_t
     }
     e = cudaMemsetAsync(p->d_nguard, 0, sizeof(unsigned long long), s);
     if (e != cudaSuccess) return e;
+    if (p->d_fixcnt) {
+        e = cudaMemsetAsync(p->d_fixcnt, 0, sizeof(unsigned) * p->n_fixcnt, s);
+        if (e != cudaSuccess) return e;
+    }
     e = mark(p, 1, s);
     if (e != cudaSuccess) return e;
     e = launch_params(params_args(p), s);
@@ -248,6 +284,7 @@ bf_status execute_host_banded(bf_plan_s* p, const float* fh, float* oh, cudaStre
         if (cut.back() < H) cut.push_back(H);
     }
     const int nb = (int)cut.size() - 1;
+    if (p->d_fix && nb > p->n_fixcnt) return BF_ERR_NOT_SUPPORTED;
     const int nc = (H + C - 1) / C;                  // copy chunks of one T-tile row
     const int need = 3 + nc + nb;
     if (!p->hst[0]) {
@@ -276,6 +313,8 @@ bf_status execute_host_banded(bf_plan_s* p, const float* fh, float* oh, cudaStre
     // T words and the guard counter start at zero for every band's kernels
     BF_CUDA(cudaMemsetAsync(p->d_T, 0, sizeof(unsigned) * p->n_sets, p->hst[1]));
     BF_CUDA(cudaMemsetAsync(p->d_nguard, 0, sizeof(unsigned long long), p->hst[1]));
+    if (p->d_fixcnt)
+        BF_CUDA(cudaMemsetAsync(p->d_fixcnt, 0, sizeof(unsigned) * p->n_fixcnt, p->hst[1]));
     BF_CUDA(cudaEventRecord(ev_clear, p->hst[1]));
     BF_CUDA(cudaStreamWaitEvent(p->hst[2], ev_clear, 0));
     const size_t row_bytes = sizeof(float) * (size_t)W;
@@ -301,8 +340,13 @@ bf_status execute_host_banded(bf_plan_s* p, const float* fh, float* oh, cudaStre
         FwdArgs fa = forward_args(p, p->d_hin, W, p->d_hout, W);
         fa.y_tile0 = r0 / th;
         fa.y_tiles = (rows + th - 1) / th;
+        if (p->d_fix) {                          // each band lists into its own rows
+            fa.fix_list = p->d_fix + (size_t)r0 * W;
+            fa.fix_count = p->d_fixcnt + b;
+        }
         BF_CUDA(launch_fwd_tc(fa, p->opt.plane_dtype == BF_PLANES_BF16, p->opt.spin_limit,
                               p->d_status, cs));
+        if (p->d_fix) BF_CUDA(launch_fixup(fixup_args(p, fa), cs));
         BF_CUDA(cudaEventRecord(ev_done[b], cs));
         BF_CUDA(cudaStreamWaitEvent(s_out, ev_done[b], 0));
         BF_CUDA(cudaMemcpyAsync(oh + (size_t)r0 * W, p->d_hout + (size_t)r0 * W,
@@ -339,6 +383,7 @@ void bf_options_init(bf_options* o)
     o->t_tile = 64;
     o->spin_limit = 1ll << 22;
     o->spatial = BF_SPATIAL_GAUSS;
+    o->lowp_recheck = 0.05f;
 }
 
 const char* bf_status_string(bf_status s)
@@ -373,6 +418,7 @@ bf_status bf_plan(int H, int W, double sigma_s, double sigma_r, double eps, cons
     if (o.trunc_rule < BF_RULE_ALG2 || o.trunc_rule > BF_RULE_CHERNOFF) return BF_ERR_INVALID_ARG;
     if (!(o.value_range > 0.f) || !isfinite(o.value_range)) return BF_ERR_INVALID_ARG;
     if (o.n_max < 1) return BF_ERR_INVALID_ARG;
+    if (!(o.lowp_recheck >= 0.f) || !(o.lowp_recheck < 1.f)) return BF_ERR_INVALID_ARG;
     if (o.n_max > 4096) return BF_ERR_NOT_SUPPORTED;
     for (int i = 0; i < (int)(sizeof(o.reserved) / sizeof(o.reserved[0])); ++i)
         if (o.reserved[i]) return BF_ERR_INVALID_ARG;
@@ -495,6 +541,18 @@ bf_status bf_plan(int H, int W, double sigma_s, double sigma_r, double eps, cons
         float T = o.t_fixed;
         ok &= cudaMemcpy(p->d_T, &T, sizeof(float), cudaMemcpyHostToDevice) == cudaSuccess;
     }
+    if (ok && o.plane_dtype != BF_PLANES_FP32 && o.lowp_recheck > 0.f) {
+        // the recheck list (one slot per pixel, so it cannot overflow) and
+        // one list length per row band of the host path
+        p->n_fixcnt = H / 64 + 4;
+        if (cudaMalloc(&p->d_fix, sizeof(unsigned) * (size_t)H * W) != cudaSuccess ||
+            cudaMalloc(&p->d_fixcnt, sizeof(unsigned) * p->n_fixcnt) != cudaSuccess) {
+            cudaGetLastError();
+            free_plan(p);
+            return BF_ERR_ALLOC;
+        }
+        ok &= cudaMemset(p->d_fixcnt, 0, sizeof(unsigned) * p->n_fixcnt) == cudaSuccess;
+    }
     if (ok && use_sep) {
         // row-filtered planes of sep_nk terms at a time (up to 2 GiB), and
         // the (num, den) partial carried between chunks of terms
@@ -566,6 +624,9 @@ bf_status bf_execute(bf_plan_t p, const float* f, size_t fp, float* out, size_t 
                               p->opt.plane_dtype == BF_PLANES_BF16, p->opt.spin_limit,
                               p->d_status, s));
     BF_CUDA(mark(p, 3, s));
+    if (p->d_fix && p->opt.filter != BF_FILTER_YVV && p->opt.plane_dtype != BF_PLANES_FP32)
+        BF_CUDA(launch_fixup(fixup_args(p, forward_args(p, f, fp, out, op)), s));
+    BF_CUDA(mark(p, 4, s));
     if (p->timing && p->n_timed < kMaxTimed) ++p->n_timed;
     p->executed = 1;
     p->last = s;
@@ -628,14 +689,19 @@ bf_status bf_get_info(bf_plan_t p, bf_info* info)
     if (!h) return BF_ERR_ALLOC;
     unsigned long long ng = 0;
     unsigned st = 0;
+    std::vector<unsigned> fc(p->n_fixcnt);
     bool ok = cudaMemcpy(h, p->d_hdr, sizeof(SetHdr) * p->n_sets, cudaMemcpyDeviceToHost) ==
               cudaSuccess;
     ok &= cudaMemcpy(&ng, p->d_nguard, sizeof(ng), cudaMemcpyDeviceToHost) == cudaSuccess;
     ok &= cudaMemcpy(&st, p->d_status, sizeof(st), cudaMemcpyDeviceToHost) == cudaSuccess;
+    if (p->n_fixcnt)
+        ok &= cudaMemcpy(fc.data(), p->d_fixcnt, sizeof(unsigned) * p->n_fixcnt,
+                         cudaMemcpyDeviceToHost) == cudaSuccess;
     if (!ok) {
         free(h);
         return BF_ERR_CUDA;
     }
+    for (unsigned v : fc) info->n_rechecked += v;
     int best = 0;
     long long terms = 0;
     float Tm = 0.f;
@@ -702,9 +768,9 @@ bf_status bf_set_timing(bf_plan_t p, int on)
     if (!p) return BF_ERR_INVALID_ARG;
     BF_CUDA(cudaSetDevice(p->device));
     if (on && !p->ev) {
-        p->ev = (cudaEvent_t*)calloc(4 * kMaxTimed, sizeof(cudaEvent_t));
+        p->ev = (cudaEvent_t*)calloc(kEvPerExec * kMaxTimed, sizeof(cudaEvent_t));
         if (!p->ev) return BF_ERR_ALLOC;
-        for (int i = 0; i < 4 * kMaxTimed; ++i) BF_CUDA(cudaEventCreate(&p->ev[i]));
+        for (int i = 0; i < kEvPerExec * kMaxTimed; ++i) BF_CUDA(cudaEventCreate(&p->ev[i]));
     }
     p->timing = on ? 1 : 0;
     p->n_timed = 0;
@@ -716,11 +782,12 @@ bf_status bf_get_timing(bf_plan_t p, double* ms, int* count)
     if (!p || !ms) return BF_ERR_INVALID_ARG;
     BF_CUDA(cudaSetDevice(p->device));
     BF_CUDA(cudaStreamSynchronize(p->last));
-    ms[0] = ms[1] = ms[2] = 0.0;
+    ms[0] = ms[1] = ms[2] = ms[3] = 0.0;
     for (int i = 0; i < p->n_timed; ++i) {
         float t;
-        for (int k = 0; k < 3; ++k) {
-            BF_CUDA(cudaEventElapsedTime(&t, p->ev[4 * i + k], p->ev[4 * i + k + 1]));
+        for (int k = 0; k < kEvPerExec - 1; ++k) {
+            BF_CUDA(cudaEventElapsedTime(&t, p->ev[kEvPerExec * i + k],
+                                         p->ev[kEvPerExec * i + k + 1]));
             ms[k] += t;
         }
     }

@@ -610,7 +610,12 @@ __global__ void __launch_bounds__(NT, 1) k_fwd_tc(FwdArgs a, long long spin_limi
                 if (gx >= a.W) continue;
                 const float cmass = clipped_mass(a.taps, R, gx, a.W, full);
                 float v;
-                if (den[x] > kGuard * rmass * cmass) {
+                if (a.fix_list && den[x] < a.fix_kappa * rmass * cmass) {
+                    // the 16-bit rounding is amplified by mass / den here: the
+                    // FP32 recheck writes this output (and applies the guard)
+                    v = a.f[(size_t)gy * a.f_pitch + gx];
+                    a.fix_list[atomicAdd(a.fix_count, 1u)] = (unsigned)gy * (unsigned)a.W + gx;
+                } else if (den[x] > kGuard * rmass * cmass) {
                     v = __fdiv_rn(num[x], den[x]) * c0 + c0;
                 } else {
                     v = a.f[(size_t)gy * a.f_pitch + gx];

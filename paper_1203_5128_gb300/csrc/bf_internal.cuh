@@ -46,6 +46,9 @@ struct bf_plan_s {
     int timing;              // record events around the kernels
     int n_timed;
     cudaEvent_t* ev;         // 4 per recorded execute
+    unsigned* d_fix;         // 16-bit recheck: listed pixels (y * W + x), H * W slots
+    unsigned* d_fixcnt;      // 16-bit recheck: list lengths, one per row band
+    int n_fixcnt;
     cudaStream_t hst[4];     // banded host path: copy in, compute (2), copy out
     cudaEvent_t* hev;        // banded host path: fork, clear, join, then per band in / done
     int n_hev;
@@ -156,7 +159,33 @@ struct FwdArgs {
     float* sep_P;           // [nk][4][H][sep_Wp] row-filtered planes
     float2* sep_nd;         // [H][W] (num, den) partial
     int sep_nk, sep_Wp, sep_cap_terms;
+    // 16-bit planes: outputs with den < fix_kappa * mass are appended to
+    // fix_list (y * W + x) for the FP32 recheck instead of being final
+    unsigned* fix_list = nullptr;
+    unsigned* fix_count = nullptr;
+    float fix_kappa = 0.f;
 };
+
+// FP32 recheck of listed outputs of a 16-bit-plane forward: the direct sum
+// of eq. (BF) with phi_eps of the pixel's own parameter set.
+struct FixArgs {
+    const float* f;
+    size_t f_pitch;
+    float* out;
+    size_t out_pitch;
+    int H, W, R;
+    const float* taps;      // 2R+1 device taps
+    const SetHdr* hdr;
+    const Pair* pairs;
+    int cap_pairs;
+    int set_tile;           // 0: single set; else T-tile side
+    int sets_x;
+    double sigma_r;
+    const unsigned* list;   // pixels y * W + x
+    const unsigned* count;  // list length (device)
+    unsigned long long* n_guarded;
+};
+cudaError_t launch_fixup(const FixArgs& a, cudaStream_t s);
 // K3-sep (FP32 FIR in two passes through HBM, R > 24, one parameter set).
 struct SepArgs {
     const float* f;

@@ -13,11 +13,15 @@
 // array of fixed size, kNoAllocBytes, that every GPU loading the library
 // holds until the process exits.
 //
-// The scratch is filled by a small set-up kernel at the start of every call
-// (taps and log(k!) computed on the device; T, status and counters cleared),
-// so no host-to-device copy is needed either.  Calls share the array: two
-// calls whose work overlaps on the GPU (different streams, or different host
-// threads without ordering) race on it and must be serialised by the caller.
+// The scratch is filled by a small set-up kernel at the start of every call:
+// the spatial taps and the log(k!) table are computed on the host, with the
+// same host exp and lgamma as bf_plan, and reach the device as that kernel's
+// parameters (no host-to-device copy, no staging buffer), so N, M and the
+// weights equal a plan's; T and the counters are cleared.  The status word
+// is cleared by bf_noalloc_device_status, which reads it.  Calls share the
+// array: two calls whose work overlaps on the GPU (different streams, or
+// different host threads without ordering) race on it and must be
+// serialised by the caller.
 #include <math.h>
 #include <mutex>
 
@@ -69,18 +73,22 @@ cudaError_t scratch_on_current_device(NoAllocScratch** out)
     return cudaSuccess;
 }
 
-__global__ void k_noalloc_setup(NoAllocScratch* s, double sigma_s, int R, int n_cap)
+// Host-computed tables for one call, passed by value as the set-up kernel's
+// parameter (about 8.6 KB, within the 32 KB parameter space of sm_70 and up).
+struct NoAllocTables {
+    float taps[2 * kNoAllocMaxR + 1 + 3];
+    double logfact[kNoAllocMaxN + 1];
+};
+
+__global__ void k_noalloc_setup(NoAllocScratch* s, const __grid_constant__ NoAllocTables t, int R,
+                                int n_cap)
 {
     if (threadIdx.x == 0) {
         s->Tbits = 0u;
-        s->status = 0u;
         s->n_guarded = 0ull;
     }
-    for (int k = threadIdx.x; k <= 2 * R; k += blockDim.x) {
-        const double d = (double)(k - R);
-        s->taps[k] = (float)exp(-d * d / (2.0 * sigma_s * sigma_s));
-    }
-    for (int k = threadIdx.x; k <= n_cap; k += blockDim.x) s->logfact[k] = lgamma((double)k + 1.0);
+    for (int k = threadIdx.x; k <= 2 * R; k += blockDim.x) s->taps[k] = t.taps[k];
+    for (int k = threadIdx.x; k <= n_cap; k += blockDim.x) s->logfact[k] = t.logfact[k];
 }
 
 int order_bound(double T, double sigma_r)
@@ -121,7 +129,12 @@ extern "C" bf_status bf_execute_noalloc(const float* f, size_t f_pitch, float* o
     if (scratch_on_current_device(&s) != cudaSuccess) return BF_ERR_CUDA;
     cudaStream_t st = (cudaStream_t)stream;
 
-    k_noalloc_setup<<<1, 256, 0, st>>>(s, sigma_s, R, n_cap);
+    // taps g(k) = exp(-k^2 / (2 sigma_s^2)) and log(k!) as bf_plan makes them
+    NoAllocTables tab;
+    for (int k = -R; k <= R; ++k)
+        tab.taps[k + R] = (float)exp(-(double)k * (double)k / (2.0 * sigma_s * sigma_s));
+    for (int k = 0; k <= n_cap; ++k) tab.logfact[k] = lgamma((double)k + 1.0);
+    k_noalloc_setup<<<1, 256, 0, st>>>(s, tab, R, n_cap);
     if (cudaGetLastError() != cudaSuccess) return BF_ERR_CUDA;
     if (launch_local_range(f, f_pitch, H, W, R, 0, 1, &s->Tbits, st) != cudaSuccess)
         return BF_ERR_CUDA;
@@ -159,13 +172,26 @@ extern "C" bf_status bf_execute_noalloc(const float* f, size_t f_pitch, float* o
     fa.den_out = nullptr;
     fa.den_pitch = 0;
     // the same taps on the host, for the kernels that take them as a parameter
-    float h_taps[2 * kNoAllocMaxR + 1];
-    for (int k = -R; k <= R; ++k)
-        h_taps[k + R] = (float)exp(-(double)k * (double)k / (2.0 * sigma_s * sigma_s));
-    fa.h_taps = h_taps;
+    fa.h_taps = tab.taps;
     fa.sep_P = nullptr;             // no workspace: the fused tiles serve every radius
     fa.sep_nd = nullptr;
     fa.sep_nk = fa.sep_Wp = fa.sep_cap_terms = 0;
     if (launch_fwd32(fa, st) != cudaSuccess) return BF_ERR_CUDA;
     return BF_OK;
+}
+
+// Reads, then clears, the status word the calls on `stream`'s device have
+// left in the static scratch (BF_DEV_* bits), after synchronising `stream`.
+extern "C" bf_status bf_noalloc_device_status(void* stream, unsigned* bits)
+{
+    NoAllocScratch* s = nullptr;
+    if (scratch_on_current_device(&s) != cudaSuccess) return BF_ERR_CUDA;
+    cudaStream_t st = (cudaStream_t)stream;
+    unsigned v = 0;
+    if (cudaMemcpyAsync(&v, &s->status, sizeof(v), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
+        return BF_ERR_CUDA;
+    if (cudaMemsetAsync(&s->status, 0, sizeof(unsigned), st) != cudaSuccess) return BF_ERR_CUDA;
+    if (bits) *bits = v;
+    return v ? BF_ERR_DEVICE_STATUS : BF_OK;
 }

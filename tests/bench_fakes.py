@@ -2,7 +2,7 @@
 streams and the process group replaced by fakes, so that the shape of the
 JSON line bench.py prints can be checked without a GPU.  The numbers are
 the fakes' (every timed region reads 2 ms, every kernel-timing hook 0.2 /
-0.01 / 1.9 ms); the CPU oracle baseline is real.
+0.01 / 1.9 / 0.05 ms); the CPU oracle baseline is real.
 
 Run as a separate process (it patches torch): python tests/bench_fakes.py
 [bench arguments...].
@@ -22,7 +22,7 @@ import paper_1203_5128_gb300 as bf  # noqa: E402
 import paper_1203_5128_gb300.replicas as replicas  # noqa: E402
 
 EVENT_MS = 2.0
-KERNEL_MS = [0.2, 0.01, 1.9]
+KERNEL_MS = [0.2, 0.01, 1.9, 0.05]
 
 
 class FakeEvent:
@@ -92,7 +92,8 @@ def install():
     bf.bf_set_timing = lambda *a: None
     bf.bf_get_timing = lambda plan: (list(KERNEL_MS), 1)
     bf.bf_get_info = lambda p: types.SimpleNamespace(R=p.R, N=264, M=94, K=77, H=p.H, W=p.W,
-                                                     n_sets=p.n_sets)
+                                                     n_sets=p.n_sets, n_rechecked=0,
+                                                     n_guarded=0, terms_total=77)
     bf.bf_get_sets = lambda p: (np.full(p.n_sets, 200.0, np.float32),
                                 np.full(p.n_sets, 200, np.int32), np.full(p.n_sets, 60, np.int32))
 

@@ -54,6 +54,9 @@ def test_options_defaults(lib):
     assert o.t_mode == nat.BF_T_GLOBAL and o.value_range == 255.0
     assert o.trunc_rule == nat.BF_RULE_ALG2 and o.n_max == 4096 and o.t_tile == 64
     assert o.plane_dtype == nat.BF_PLANES_FP32 and o.spatial == nat.BF_SPATIAL_GAUSS
+    assert abs(o.lowp_recheck - 0.05) < 1e-7
+    # the struct has the size the header gives it (reserved words included)
+    assert ctypes.sizeof(nat.bf_options) == 4 * 8 + 8 + 4 + 4 + 4 * 6
 
 
 @pytest.mark.parametrize("args", [
@@ -79,6 +82,8 @@ def test_plan_rejects_bad_options(lib):
                              ("trunc_rule", 5, nat.BF_ERR_INVALID_ARG),
                              ("value_range", 0.0, nat.BF_ERR_INVALID_ARG),
                              ("n_max", 0, nat.BF_ERR_INVALID_ARG),
+                             ("lowp_recheck", -0.1, nat.BF_ERR_INVALID_ARG),
+                             ("lowp_recheck", 1.0, nat.BF_ERR_INVALID_ARG),
                              ("n_max", 100000, nat.BF_ERR_NOT_SUPPORTED)]:
         o = nat.bf_options()
         lib.bf_options_init(ctypes.byref(o))

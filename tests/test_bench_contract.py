@@ -22,7 +22,7 @@ def line():
     from paper_1203_5128_gb300 import build
     build.build()
     r = subprocess.run([sys.executable, os.path.join(ROOT, "tests", "bench_fakes.py"),
-                        "--steps", "2", "--warmup", "3", "--cpu-seconds", "1"],
+                        "--steps", "2", "--warmup", "3", "--oracle-rows", "128"],
                        capture_output=True, text=True, timeout=600, cwd=ROOT)
     assert r.returncode == 0, r.stderr[-3000:]
     lines = [x for x in r.stdout.splitlines() if x.startswith("{")]
@@ -44,7 +44,7 @@ def test_top_level_keys(line):
 def test_value_and_step_time(line):
     assert line["ms_per_step"] == pytest.approx(EVENT_MS)
     assert line["value"] == pytest.approx(H * W / (EVENT_MS * 1e3))
-    assert line["gpu_launches"] == 3 * 2
+    assert line["gpu_launches"] == 4 * 2
 
 
 def test_roofline(line):
@@ -59,7 +59,7 @@ def test_roofline(line):
 def test_cpu_baseline_and_e2e(line):
     c = line["cpu_baseline"]
     assert c["kind"] == "oracle" and c["unit"] == "Mpixel/s" and c["cores"] >= 1
-    assert c["value"] > 0 and "crop" in c["sample"]
+    assert c["value"] > 0 and "rows 0..127" in c["sample"]
     e = line["e2e"]
     assert e["unit"] == "Mpixel/s" and e["value"] > 0
     assert e["h2d_bytes_per_step"] == 4 * H * W and e["d2h_bytes_per_step"] == 4 * H * W
@@ -73,3 +73,20 @@ def test_extra_legs(line):
         assert b["value"] == pytest.approx(H * W / (EVENT_MS * 1e3))
     assert line["tuned_fp32"]["roofline"]["bound"] == "alu"
     assert line["tuned_yvv"]["roofline_hbm"]["bound"] == "hbm"
+
+
+def test_parity_and_sweep_legs(line):
+    t = line["tuned"]
+    assert t["every_pixel"]["outputs"] == 128 * W and t["every_pixel"]["max_abs"] >= 0
+    assert "recheck" in t["kernel_ms"]
+    for planes in ["fp32", "bf16", "fp16"]:
+        e = line["precision"][planes]
+        assert e["value"] == pytest.approx(H * W / (EVENT_MS * 1e3)) and e["max_abs"] >= 0
+    cells = line["config1"]["cells"]
+    assert sorted((c["sigma_s"], c["sigma_r"]) for c in cells) == \
+        [(5.0, 10.0), (5.0, 20.0), (10.0, 10.0), (10.0, 20.0)]
+    for c in cells:
+        assert c["speedup_tile"] == pytest.approx(c["accel_tile"]["value"] / c["plain"]["value"])
+    d = line["divergence"]
+    for k in ["vs_direct_gaussian", "vs_plain_parameters"]:
+        assert d[k]["max_abs"] >= 0 and d[k]["mse"] >= 0

@@ -10,9 +10,11 @@ window's mass (every pixel of the window weighs 1, so the mass is the
 clipped window's pixel count); the adjoint within 1e-3 of max |grad|; the
 batch bitwise equal to separate calls.
 
-16-bit planes: within 0.5 gray level (FP16) or 2 (BF16) wherever den is
-more than 5 % of the window's mass, and everywhere within that plus the
-rounding bound of the stored planes.  Each plane value (at most 1 in
+16-bit planes: within 0.5 gray level (FP16) or 2 (BF16) at every output,
+with the library's default FP32 recheck of the outputs whose den is under
+5 % of the window's mass.  Without the recheck the bar would hold only where
+den is a large part of the mass, by the rounding bound of the stored
+planes.  Each plane value (at most 1 in
 magnitude after centring and scaling by c0 = value_range / 2) is rounded to
 16 bits twice, once as modulated and once after the first of the two
 separable passes, so each filtered plane is off by at most 2 u mass (u the
@@ -21,7 +23,7 @@ the kept terms with weights of total at most 1, are off by at most 4 u c0
 mass and 4 u mass, and out = num / den by at most 8 u c0 mass / den.  At a
 pixel unlike its whole window den is a tiny part of the mass (0.1 % in the
 radius-20, sigma_r = 5 setting) and the 16-bit result there can exceed the
-0.5 bar; the FP32 planes stay within theirs.
+0.5 bar; the recheck recomputes those outputs in FP32.
 """
 import numpy as np
 import pytest
@@ -38,8 +40,8 @@ C0 = 127.5                                        # centring constant of 8-bit i
 
 
 def check_lowp(err, den, mass, planes, what):
-    """The 16-bit bar: TOL_LOWP where den > 5 % of the mass, and everywhere
-    TOL_LOWP plus the rounding bound 8 u c0 mass / den."""
+    """The 16-bit bar: TOL_LOWP at every output (the recheck is on).  The
+    share of the 16-bit rounding bound 8 u c0 mass / den is printed."""
     well = den > 0.05 * mass
     bound = TOL_LOWP[planes] + 8 * U16[planes] * C0 * mass / np.maximum(den, 1e-300)
     print("box %s %s: max-abs %.3g gray levels, %.3g where den > 5%% of the window, "
@@ -47,9 +49,7 @@ def check_lowp(err, den, mass, planes, what):
               planes, what, err.max(), err[well].max() if well.any() else 0.0,
               int(np.sum(err > TOL_LOWP[planes])), err.size, TOL_LOWP[planes],
               float(np.max(err / bound))))
-    if well.any():
-        assert np.max(err[well]) <= TOL_LOWP[planes]
-    assert np.all(err <= bound)
+    assert np.max(err) <= TOL_LOWP[planes]
 
 
 @pytest.fixture(scope="module")
@@ -168,6 +168,25 @@ def test_box_1024_sampled(bf, planes):
         assert np.all(err <= tol_fp32(den, mass, float(p.T.max())))
     else:
         check_lowp(err, den, mass, planes, "1024^2 sampled")
+
+
+@pytest.mark.parametrize("planes", ["fp16", "bf16"])
+def test_box_1024_every_output(bf, planes):
+    """Every output of 1024^2 G8 in the paper's box setting (radius 20,
+    sigma_r = 5, eps = 1e-2, exact T per 128 x 128 T-tile) with 16-bit
+    planes, against the oracle's shiftable box mode: the flat bar holds at
+    every pixel, including those unlike their whole window (den about 0.1 %
+    of the mass), which the FP32 recheck recomputes."""
+    f = synth.g8(1024, 1024, seed=1)
+    plan, out, p = run(bf, f, 20, 5.0, 0.01, "tile", "alg2", 128, planes)
+    ref, _, den, nfb = oracle.shiftable(f, 20.0, 5.0, p, return_parts=True, spatial="box")
+    yy, xx = np.mgrid[0:1024, 0:1024]
+    info = bf.bf_get_info(plan)
+    print("box 1024^2 %s: %d outputs rechecked in FP32, %d guarded (oracle %d)" % (
+        planes, info.n_rechecked, info.n_guarded, nfb))
+    assert info.n_rechecked > 0 and info.n_guarded == nfb
+    check_lowp(np.abs(out - ref), den, box_count(20, yy, xx, 1024, 1024), planes,
+               "1024^2 every output")
 
 
 def test_box_4096_bench_workload_sampled(bf):

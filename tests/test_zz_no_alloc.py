@@ -42,10 +42,20 @@ def noalloc(lib, f, out, sigma_s, sigma_r, eps, value_range=255.0):
     assert code == nat.BF_OK, lib.bf_status_string(code)
 
 
+def device_status(lib):
+    import torch
+    bits = ctypes.c_uint()
+    lib.bf_noalloc_device_status(torch.cuda.current_stream().cuda_stream, ctypes.byref(bits))
+    return bits.value
+
+
 def test_noalloc_matches_plan_path_on_two_calls(lib):
     import torch
     import paper_1203_5128_gb300 as bf
-    cases = [(300, 257, 3.0, 20.0, 0.01, 11), (256, 320, 5.0, 10.0, 0.01, 12)]
+    # radii 9 and 15 (tall tiles), 30 and 48 (the fused kernel's small tiles:
+    # there is no two-pass workspace), ragged sizes
+    cases = [(300, 257, 3.0, 20.0, 0.01, 11), (256, 320, 5.0, 10.0, 0.01, 12),
+             (97, 203, 10.0, 20.0, 0.01, 13), (65, 97, 16.0, 25.0, 0.01, 14)]
     for H, W, ss, sr, eps, seed in cases:
         f = torch.from_numpy(synth.g8(H, W, seed=seed)).cuda()
         ref = bf.bf_execute(bf.bf_plan(H, W, ss, sr, eps, t_mode="global", trunc_rule="alg2"), f)
@@ -54,6 +64,28 @@ def test_noalloc_matches_plan_path_on_two_calls(lib):
         torch.cuda.synchronize()
         err = (out - ref).abs().max().item()
         assert np.isfinite(err) and err <= TOL8, "max-abs %.3g gray levels" % err
+        assert device_status(lib) == 0
+
+
+def test_noalloc_reports_order_overflow(lib):
+    """Pixels outside [0, value_range] can need an order above the static
+    table: the output is then a copy of the input, the call still returns
+    BF_OK, and the status bit is read (and cleared) by
+    bf_noalloc_device_status."""
+    import torch
+    from paper_1203_5128_gb300 import _native as nat
+    f_np = synth.g8(64, 96, seed=21)
+    f_np[10:20, 10:20] = 2000.0           # far above value_range = 255
+    f = torch.from_numpy(f_np).cuda()
+    out = torch.full_like(f, float("nan"))
+    noalloc(lib, f, out, 2.0, 10.0, 0.01)
+    torch.cuda.synchronize()
+    assert torch.equal(out, f)
+    bits = ctypes.c_uint()
+    s = torch.cuda.current_stream().cuda_stream
+    assert lib.bf_noalloc_device_status(s, ctypes.byref(bits)) == nat.BF_ERR_DEVICE_STATUS
+    assert bits.value & nat.BF_DEV_ORDER_TOO_LARGE
+    assert lib.bf_noalloc_device_status(s, ctypes.byref(bits)) == nat.BF_OK and bits.value == 0
 
 
 def test_noalloc_rejects_sizes_above_its_scratch(lib):
