@@ -94,6 +94,10 @@ def _load():
         "orc_yvv_2d": (None, [P, P, I, I, D, I]),
         "orc_yvv_impulse": (None, [D, I, P]),
         "orc_shiftable_yvv": (L, [P, I, I, D, I, I, D, P, P, P]),
+        "orc_poly_order": (I, [D, D]),
+        "orc_poly_phi": (None, [P, I, I, D, P]),
+        "orc_range_tiles": (None, [P, I, I, I, I, I, P]),
+        "orc_poly_direct_points": (L, [P, I, I, P, I, P, D, P, P, I, P, P, P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -263,13 +267,20 @@ class Params:
 def resolve(f, sigma_s: float, sigma_r: float, eps: float = 0.0, *,
             t_mode: str = T_GLOBAL, rule: str = RULE_ALG2,
             value_range: float = 255.0, t_fixed: float | None = None,
-            t_tile: int = 64, spatial: str = "fir") -> Params:
+            t_tile: int = 64, spatial: str = "fir", kernel: str = "cos") -> Params:
     """Algorithm 2, steps 1-4: R, T, N and M (per T-tile in ``tile`` mode).
     R is ceil(3 sigma_s) for the Gaussian (and its recursive form) and
-    sigma_s itself for the box filter (``spatial="box"``)."""
+    sigma_s itself for the box filter (``spatial="box"``).  ``kernel="poly"``
+    takes the raised polynomial of eq. (RPconv): N = max(1, ceil(T^2 /
+    (2 sigma_r^2))), no truncation (M = 0), and T the range of f over the
+    image (``global``) or over each T-tile grown by R (``tile``)."""
     f = _f64(f)
     H, W = f.shape
     R = box_radius(sigma_s) if spatial == "box" else radius(sigma_s)
+    if kernel == "poly":
+        return _resolve_poly(f, R, sigma_r, t_mode, value_range, t_fixed, t_tile)
+    if kernel != "cos":
+        raise ValueError(kernel)
     if t_mode == T_FIXED:
         T = np.array([[np.float32(value_range if t_fixed is None else t_fixed)]], np.float32)
         th = tw = WHOLE
@@ -285,6 +296,74 @@ def resolve(f, sigma_s: float, sigma_r: float, eps: float = 0.0, *,
     M = np.vectorize(lambda n: choose_m(int(n), sigma_r, eps, rule, value_range),
                      otypes=[np.int64])(N)
     return Params(R=R, tile_h=th, tile_w=tw, T=T, N=N, M=M)
+
+
+def poly_order(T: float, sigma_r: float) -> int:
+    """N = max(1, ceil(T^2 / (2 sigma_r^2))) (Sec. 1.3, raised polynomial)."""
+    return _load().orc_poly_order(float(T), float(sigma_r))
+
+
+def poly_phi(s, N: int, sigma_r: float) -> np.ndarray:
+    """(1 - s^2 / (2 N sigma_r^2))^N, eq. (RPconv)."""
+    s = _f64(np.atleast_1d(s))
+    out = np.empty_like(s)
+    _load().orc_poly_phi(_p(s), s.size, int(N), float(sigma_r), _p(out))
+    return out
+
+
+def range_tiles(f, R: int, tile_h: int, tile_w: int) -> np.ndarray:
+    """max - min of f over each tile grown by R (clipped), float64."""
+    f = _f64(f)
+    H, W = f.shape
+    ty, tx = -(-H // tile_h), -(-W // tile_w)
+    T = np.empty((ty, tx))
+    _load().orc_range_tiles(_p(f), H, W, int(R), int(tile_h), int(tile_w), _p(T))
+    return T
+
+
+def _resolve_poly(f, R, sigma_r, t_mode, value_range, t_fixed, t_tile) -> Params:
+    H, W = f.shape
+    if t_mode == T_FIXED:
+        T = np.array([[float(value_range if t_fixed is None else t_fixed)]])
+        th = tw = WHOLE
+    elif t_mode == T_GLOBAL:
+        T = range_tiles(f, R, H, W)
+        th = tw = WHOLE
+    elif t_mode == T_TILE:
+        T = range_tiles(f, R, t_tile, t_tile)
+        th, tw = t_tile, t_tile
+    else:
+        raise ValueError(t_mode)
+    N = np.vectorize(lambda t: poly_order(float(t), sigma_r), otypes=[np.int64])(T)
+    return Params(R=R, tile_h=th, tile_w=tw, T=T.astype(np.float32), N=N,
+                  M=np.zeros_like(N))
+
+
+def poly_direct(f, sigma_s: float, sigma_r: float, params: Params, *, points=None,
+                return_parts=False, spatial: str = "fir"):
+    """Direct sum of eq. (BF) with the raised-polynomial range kernel of each
+    point's T-tile order (eq. (RPconv)), at the given points (all pixels if
+    None)."""
+    f = _f64(f)
+    H, W = f.shape
+    if points is None:
+        yy, xx = np.mgrid[0:H, 0:W]
+        ys, xs = yy.ravel(), xx.ravel()
+    else:
+        ys, xs = np.asarray(points[0]), np.asarray(points[1])
+    ys = np.ascontiguousarray(ys, dtype=np.int32)
+    xs = np.ascontiguousarray(xs, dtype=np.int32)
+    g = spatial_taps(sigma_s, params.R, spatial)
+    a, b = _tile_of(params, ys, xs)
+    Ns = np.ascontiguousarray(params.N[a, b], dtype=np.int32)
+    out, num, den = np.empty(ys.size), np.empty(ys.size), np.empty(ys.size)
+    nfb = _load().orc_poly_direct_points(_p(f), H, W, _p(g), params.R, _p(Ns), float(sigma_r),
+                                         _p(ys), _p(xs), ys.size, _p(out), _p(num), _p(den))
+    if points is None:
+        out, num, den = out.reshape(H, W), num.reshape(H, W), den.reshape(H, W)
+    if return_parts:
+        return out, num, den, nfb
+    return out
 
 
 def _blocks(p: Params, H: int, W: int):

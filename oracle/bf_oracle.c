@@ -698,3 +698,80 @@ void orc_grad_direct_points(const double *f, int H, int W, const double *g, int 
     }
     free(lw); free(wk); free(omk);
 }
+
+/* ------------------------------------------------------------------ */
+/* Raised-polynomial range kernel (Sec. 1.3, eqs. (RP) and (RPconv)):  */
+/*   phi(s) = (1 - s^2 / (2 N sigma_r^2))^N,                          */
+/* which tends to exp(-s^2 / (2 sigma_r^2)) as N grows and is positive */
+/* and monotone on [-T, T] when N >= N0 = 0.5 (T / sigma_r)^2.         */
+/* ------------------------------------------------------------------ */
+
+/* N = max(1, ceil(N0)), N0 = T^2 / (2 sigma_r^2). */
+int orc_poly_order(double T, double sigma_r)
+{
+    double n0 = (T * T) / (2.0 * sigma_r * sigma_r);
+    int N = (int)ceil(n0);
+    return N < 1 ? 1 : N;
+}
+
+/* phi(s) at ns points. */
+void orc_poly_phi(const double *s, int ns, int N, double sigma_r, double *out)
+{
+    for (int i = 0; i < ns; ++i)
+        out[i] = pow(1.0 - s[i] * s[i] / (2.0 * (double)N * sigma_r * sigma_r), (double)N);
+}
+
+/* T of the polynomial kernel per tile: the range (max - min) of f over the
+ * tile grown by R on every side and clipped to the image, so that every
+ * pair of values a pixel of the tile meets (and every pair the polynomial
+ * expansion over that region represents) lies within [-T, T].  A single
+ * tile covering the image gives the image's range.  Returned in double
+ * (the difference of two image values is exact). */
+void orc_range_tiles(const double *f, int H, int W, int R, int tile_h, int tile_w, double *T)
+{
+    int ty = (H + tile_h - 1) / tile_h, tx = (W + tile_w - 1) / tile_w;
+    for (int a = 0; a < ty; ++a)
+        for (int b = 0; b < tx; ++b) {
+            int i0 = imax(0, a * tile_h - R), i1 = imin(H, (a + 1) * tile_h + R);
+            int j0 = imax(0, b * tile_w - R), j1 = imin(W, (b + 1) * tile_w + R);
+            double mx = -INFINITY, mn = INFINITY;
+            for (int i = i0; i < i1; ++i)
+                for (int j = j0; j < j1; ++j) {
+                    mx = fmax(mx, f[(size_t)i * W + j]);
+                    mn = fmin(mn, f[(size_t)i * W + j]);
+                }
+            T[a * tx + b] = mx - mn;
+        }
+}
+
+/* Direct filter of eq. (BF) with the raised-polynomial range kernel of
+ * order Ns[p] at the points (ys[p], xs[p]), clipped window, with the same
+ * denominator guard as the cosine kernel.  Returns the guarded count. */
+long orc_poly_direct_points(const double *f, int H, int W, const double *g, int R,
+                            const int *Ns, double sigma_r, const int *ys, const int *xs, int npts,
+                            double *out, double *num_out, double *den_out)
+{
+    long nfb = 0;
+    #pragma omp parallel for schedule(dynamic, 4) reduction(+ : nfb)
+    for (int p = 0; p < npts; ++p) {
+        const int i = ys[p], j = xs[p], N = Ns[p];
+        const double a = 2.0 * (double)N * sigma_r * sigma_r;
+        const double fx = f[(size_t)i * W + j];
+        double num = 0.0, den = 0.0;
+        for (int y = imax(0, i - R); y <= imin(H - 1, i + R); ++y)
+            for (int x = imax(0, j - R); x <= imin(W - 1, j + R); ++x) {
+                const double fy = f[(size_t)y * W + x];
+                const double s = fy - fx;
+                const double phi = pow(1.0 - s * s / a, (double)N);
+                const double wgt = g[y - i + R] * g[x - j + R] * phi;
+                num += wgt * fy;
+                den += wgt;
+            }
+        const double mass = clipped_mass(g, R, H, W, i, j);
+        if (den > 1e-6 * mass) out[p] = num / den;
+        else { out[p] = fx; ++nfb; }
+        if (num_out) num_out[p] = num;
+        if (den_out) den_out[p] = den;
+    }
+    return nfb;
+}
