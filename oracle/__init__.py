@@ -98,6 +98,8 @@ def _load():
         "orc_poly_phi": (None, [P, I, I, D, P]),
         "orc_range_tiles": (None, [P, I, I, I, I, I, P]),
         "orc_poly_direct_points": (L, [P, I, I, P, I, P, D, P, P, I, P, P, P]),
+        "orc_nlm_direct_points": (L, [P, I, I, P, I, I, I, D, I, P, P, I, P, P, I, P, P, P]),
+        "orc_nlm_shiftable": (L, [P, I, I, P, I, I, I, D, P, P, I, P, P, P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -361,6 +363,73 @@ def poly_direct(f, sigma_s: float, sigma_r: float, params: Params, *, points=Non
                                          _p(ys), _p(xs), ys.size, _p(out), _p(num), _p(den))
     if points is None:
         out, num, den = out.reshape(H, W), num.reshape(H, W), den.reshape(H, W)
+    if return_parts:
+        return out, num, den, nfb
+    return out
+
+
+# ---------------------------------------------------------------- non-local means
+
+def patch_offsets(mask: int):
+    """Patch pixels u_1..u_p of the non-local means of Sec. 6 from a 9-bit
+    mask over the 3 x 3 neighbourhood (bit 3 (dy + 1) + (dx + 1)); the centre
+    bit must be set and comes first (u_1 = 0)."""
+    mask = int(mask)
+    if not (mask & (1 << 4)) or mask >> 9:
+        raise ValueError("patch mask must hold the centre (bit 4) and fit 9 bits: %r" % mask)
+    offs = [(0, 0)]
+    for b in range(9):
+        if b != 4 and mask & (1 << b):
+            offs.append((b // 3 - 1, b % 3 - 1))
+    uy = np.ascontiguousarray([o[0] for o in offs], dtype=np.int32)
+    ux = np.ascontiguousarray([o[1] for o in offs], dtype=np.int32)
+    return uy, ux
+
+
+def nlm_direct(f, sigma_s: float, sigma_r: float, params: Params, patch_mask: int, *,
+               points=None, gauss: bool = False, spatial: str = "box", return_parts=False):
+    """Direct sums of eqs. (NL1), (NL2) (Sec. 6): the range kernel is the
+    product over the patch pixels of phi_eps (one (N, M) for the image), or
+    of exact Gaussians when ``gauss``; ``spatial`` "box" weighs the window
+    equally (the paper's sums), "fir" with the Gaussian."""
+    assert params.T.size == 1, "non-local means takes one (N, M)"
+    f = _f64(f)
+    H, W = f.shape
+    if points is None:
+        yy, xx = np.mgrid[0:H, 0:W]
+        ys, xs = yy.ravel(), xx.ravel()
+    else:
+        ys, xs = np.asarray(points[0]), np.asarray(points[1])
+    ys = np.ascontiguousarray(ys, dtype=np.int32)
+    xs = np.ascontiguousarray(xs, dtype=np.int32)
+    uy, ux = patch_offsets(patch_mask)
+    g = spatial_taps(sigma_s, params.R, spatial)
+    out, num, den = np.empty(ys.size), np.empty(ys.size), np.empty(ys.size)
+    nfb = _load().orc_nlm_direct_points(_p(f), H, W, _p(g), params.R, int(params.N[0, 0]),
+                                        int(params.M[0, 0]), float(sigma_r), int(gauss),
+                                        _p(uy), _p(ux), uy.size, _p(ys), _p(xs), ys.size,
+                                        _p(out), _p(num), _p(den))
+    if points is None:
+        out, num, den = out.reshape(H, W), num.reshape(H, W), den.reshape(H, W)
+    if return_parts:
+        return out, num, den, nfb
+    return out
+
+
+def nlm_shiftable(f, sigma_s: float, sigma_r: float, params: Params, patch_mask: int, *,
+                  spatial: str = "box", return_parts=False):
+    """The O(1) shiftable form of the same sums: one pair of modulated
+    planes per multi-index of the product expansion (every multi-index,
+    no folding)."""
+    assert params.T.size == 1, "non-local means takes one (N, M)"
+    f = _f64(f)
+    H, W = f.shape
+    uy, ux = patch_offsets(patch_mask)
+    g = spatial_taps(sigma_s, params.R, spatial)
+    out, num, den = np.empty_like(f), np.empty_like(f), np.empty_like(f)
+    nfb = _load().orc_nlm_shiftable(_p(f), H, W, _p(g), params.R, int(params.N[0, 0]),
+                                    int(params.M[0, 0]), float(sigma_r), _p(uy), _p(ux), uy.size,
+                                    _p(out), _p(num), _p(den))
     if return_parts:
         return out, num, den, nfb
     return out

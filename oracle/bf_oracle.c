@@ -775,3 +775,134 @@ long orc_poly_direct_points(const double *f, int H, int W, const double *g, int 
     }
     return nfb;
 }
+
+/* ------------------------------------------------------------------ */
+/* Non-local means with a small patch (Sec. 6, eqs. (NL1), (NL2)):     */
+/*   NL1(x) = sum_y s(y) f(x-y) g(f(x+u_1) - f(x-y+u_1), ...,           */
+/*                              f(x+u_p) - f(x-y+u_p)),                 */
+/*   NL2(x) = the same without f(x-y),   out = NL1 / NL2,               */
+/* g a product of one-dimensional Gaussians of width sigma_r, each      */
+/* approximated by phi_eps (eq. (approx)) with the N, M of T (eq.       */
+/* (bound)).  s is the spatial weight (the box of the paper's sums, or  */
+/* the Gaussian), y over the clipped window.  Patch values f(z + u_i)   */
+/* outside the image are taken at the nearest in-image pixel.           */
+/* ------------------------------------------------------------------ */
+
+static double f_clamped(const double *f, int H, int W, int y, int x)
+{
+    y = imin(imax(y, 0), H - 1);
+    x = imin(imax(x, 0), W - 1);
+    return f[(size_t)y * W + x];
+}
+
+/* Direct sums at npts points.  uy, ux: the p patch offsets (u_1 = 0 first).
+ * gauss != 0: the range kernel is the product of exact Gaussians. */
+long orc_nlm_direct_points(const double *f, int H, int W, const double *g, int R,
+                           int N, int M, double sigma_r, int gauss,
+                           const int *uy, const int *ux, int p,
+                           const int *ys, const int *xs, int npts,
+                           double *out, double *num_out, double *den_out)
+{
+    long nfb = 0;
+    int nk = N - 2 * M + 1;
+    double *lw = (double *)malloc(sizeof(double) * (size_t)(N + 1));
+    double *wk = (double *)malloc(sizeof(double) * (size_t)nk);
+    double *omk = (double *)malloc(sizeof(double) * (size_t)nk);
+    orc_log_weights(N, lw);
+    for (int n = M; n <= N - M; ++n) {
+        wk[n - M] = exp(lw[n]);
+        omk[n - M] = (double)(2 * n - N) / (sqrt((double)N) * sigma_r);
+    }
+    #pragma omp parallel for schedule(dynamic, 4) reduction(+ : nfb)
+    for (int q = 0; q < npts; ++q) {
+        const int i = ys[q], j = xs[q];
+        double num = 0.0, den = 0.0;
+        for (int a = imax(0, i - R); a <= imin(H - 1, i + R); ++a)
+            for (int b = imax(0, j - R); b <= imin(W - 1, j + R); ++b) {
+                double kern = 1.0;
+                for (int c = 0; c < p; ++c) {
+                    const double s = f_clamped(f, H, W, i + uy[c], j + ux[c]) -
+                                     f_clamped(f, H, W, a + uy[c], b + ux[c]);
+                    double phi = 0.0;
+                    if (gauss) phi = exp(-s * s / (2.0 * sigma_r * sigma_r));
+                    else
+                        for (int k = 0; k < nk; ++k) phi += wk[k] * cos(omk[k] * s);
+                    kern *= phi;
+                }
+                const double wgt = g[a - i + R] * g[b - j + R] * kern;
+                num += wgt * f[(size_t)a * W + b];
+                den += wgt;
+            }
+        const double mass = clipped_mass(g, R, H, W, i, j);
+        if (den > 1e-6 * mass) out[q] = num / den;
+        else { out[q] = f[(size_t)i * W + j]; ++nfb; }
+        if (num_out) num_out[q] = num;
+        if (den_out) den_out[q] = den;
+    }
+    free(lw); free(wk); free(omk);
+    return nfb;
+}
+
+/* The shiftable form of the same sums (the O(1) algorithm of the paper's
+ * Sec. 6): expanding every phi_eps(s_i) = sum_n w_n exp(j omega_n s_i)
+ * gives, for each multi-index nu = (n_1, ..., n_p) in [M, N-M]^p, the
+ * weight w_nu = prod_i w_{n_i} and the phase image theta_nu(z) = sum_i
+ * omega_{n_i} f(z + u_i); then
+ *   NL2(x) = sum_nu w_nu [cos theta_nu(x) (s * cos theta_nu)(x)
+ *                        + sin theta_nu(x) (s * sin theta_nu)(x)],
+ * and NL1 likewise with the planes f cos theta_nu, f sin theta_nu (f at the
+ * window pixel).  Every multi-index is visited (no folding). */
+long orc_nlm_shiftable(const double *f, int H, int W, const double *g, int R,
+                       int N, int M, double sigma_r, const int *uy, const int *ux, int p,
+                       double *out, double *num_out, double *den_out)
+{
+    const size_t HW = (size_t)H * W;
+    int nk = N - 2 * M + 1;
+    double *lw = (double *)malloc(sizeof(double) * (size_t)(N + 1));
+    orc_log_weights(N, lw);
+    double *buf = (double *)malloc(sizeof(double) * HW * 11);
+    double *th = buf, *P = buf + HW, *Q = buf + 5 * HW, *tmp = buf + 9 * HW;
+    double *num = (double *)calloc(HW, sizeof(double)), *den = (double *)calloc(HW, sizeof(double));
+    int *idx = (int *)calloc((size_t)p, sizeof(int));
+    const double scale = sqrt((double)N) * sigma_r;
+    long total = 1;
+    for (int c = 0; c < p; ++c) total *= nk;
+    for (long t = 0; t < total; ++t) {
+        long r = t;
+        double wnu = 1.0;
+        for (int c = 0; c < p; ++c) {
+            idx[c] = M + (int)(r % nk);
+            r /= nk;
+            wnu *= exp(lw[idx[c]]);
+        }
+        for (int i = 0; i < H; ++i)
+            for (int j = 0; j < W; ++j) {
+                double v = 0.0;
+                for (int c = 0; c < p; ++c)
+                    v += (double)(2 * idx[c] - N) / scale * f_clamped(f, H, W, i + uy[c], j + ux[c]);
+                th[(size_t)i * W + j] = v;
+            }
+        for (size_t k = 0; k < HW; ++k) {
+            const double c = cos(th[k]), s = sin(th[k]);
+            P[k] = f[k] * c; P[HW + k] = f[k] * s; P[2 * HW + k] = c; P[3 * HW + k] = s;
+        }
+        for (int q = 0; q < 4; ++q) sep_filter(P + q * HW, tmp, Q + q * HW, H, W, g, R);
+        for (size_t k = 0; k < HW; ++k) {
+            const double c = cos(th[k]), s = sin(th[k]);
+            num[k] += wnu * (c * Q[k] + s * Q[HW + k]);
+            den[k] += wnu * (c * Q[2 * HW + k] + s * Q[3 * HW + k]);
+        }
+    }
+    long nfb = 0;
+    for (int i = 0; i < H; ++i)
+        for (int j = 0; j < W; ++j) {
+            const size_t k = (size_t)i * W + j;
+            const double mass = clipped_mass(g, R, H, W, i, j);
+            if (den[k] > 1e-6 * mass) out[k] = num[k] / den[k];
+            else { out[k] = f[k]; ++nfb; }
+            if (num_out) num_out[k] = num[k];
+            if (den_out) den_out[k] = den[k];
+        }
+    free(lw); free(buf); free(num); free(den); free(idx);
+    return nfb;
+}
