@@ -359,6 +359,83 @@ def config1_leg(bf, timed_on, steps, world, max_over_ranks):
             "cells": cells}
 
 
+# the raised-polynomial kernel (Sec. 1.3, eq. (RPconv)) against the raised
+# cosine on the bench image: sigma_s = 3, sigma_r = 30, no truncation
+POLY = dict(sigma_s=3.0, sigma_r=30.0)
+# non-local means (Sec. 6): 1024^2 G8, box search window of radius 5,
+# sigma_r = 40 per patch pixel, eps = 5e-2, patch = centre, right, below
+NLM = dict(side=1024, seed=11, radius=5, sigma_r=40.0, eps=0.05, patch=0x10 | 0x20 | 0x80)
+
+
+def poly_leg(bf, f, f_np, timed_on, steps, world, max_over_ranks):
+    """Raised polynomial vs raised cosine (FP32 planes) on the 4096^2 bench
+    image with T fixed at 255 and per 128 x 128 T-tile: Mpixel/s, terms and
+    the polynomial's max-abs error against the FP64 oracle's direct sum at
+    sampled pixels."""
+    import numpy as np
+    import torch
+    import oracle
+    out = torch.empty_like(f)
+    ys, xs = sample_pixels(40, seed=29)
+    res = {"workload": "4096x4096 G8, sigma_s=3 (R=9), sigma_r=30, eps=0, FP32 planes; T = 255 "
+                       "or per 128x128 T-tile (the region range for the polynomial, Algorithm 1 "
+                       "for the cosine)"}
+    for name, kern, mode in (("poly_fixed", "poly", "fixed"), ("poly_tile", "poly", "tile"),
+                             ("cosine_fixed", "cosine", "fixed"), ("cosine_tile", "cosine", "tile")):
+        kw = dict(t_mode=mode, t_tile=128, range_kernel=kern, plane_dtype="fp32")
+        if mode == "fixed":
+            kw["t_fixed"] = 255.0
+        plan = bf.bf_plan(H, W, POLY["sigma_s"], POLY["sigma_r"], 0.0, **kw)
+        ms, kms, cnt = timed_on(plan, f, out, steps, 1)
+        ms = max_over_ranks(ms)
+        info = bf.bf_get_info(plan)
+        e = {"value": world * H * W * steps / (ms * 1e3), "unit": "Mpixel/s",
+             "ms_per_step": ms / steps, "max_N": info.N, "terms_total": info.terms_total}
+        if kern == "poly":
+            p = oracle.resolve(f_np, POLY["sigma_s"], POLY["sigma_r"], t_mode=mode, t_tile=128,
+                               t_fixed=255.0 if mode == "fixed" else None, kernel="poly")
+            ref = oracle.poly_direct(f_np, POLY["sigma_s"], POLY["sigma_r"], p, points=(ys, xs))
+            o = out.cpu().numpy().astype(np.float64)
+            e["max_abs"] = float(np.max(np.abs(o[ys, xs] - ref)))
+        res[name] = e
+        plan.close()
+    return res
+
+
+def nlm_leg(bf, timed_on, steps, world, max_over_ranks):
+    """O(1) non-local means with a 3-pixel patch: Mpixel/s, multi-index terms
+    and the max-abs error against the FP64 oracle's direct sums at sampled
+    pixels."""
+    import numpy as np
+    import torch
+    import oracle
+    from paper_1203_5128_gb300 import synth
+    n = NLM["side"]
+    f_np = synth.g8(n, n, seed=NLM["seed"])
+    f = torch.from_numpy(f_np).cuda()
+    out = torch.empty_like(f)
+    plan = bf.bf_plan(n, n, float(NLM["radius"]), NLM["sigma_r"], NLM["eps"], t_mode="global",
+                      trunc_rule="alg2", spatial="box", patch_mask=NLM["patch"])
+    ms, kms, cnt = timed_on(plan, f, out, steps, 1)
+    ms = max_over_ranks(ms)
+    info = bf.bf_get_info(plan)
+    p = oracle.resolve(f_np, float(NLM["radius"]), NLM["sigma_r"], NLM["eps"], t_mode="global",
+                       spatial="box")
+    ys, xs = sample_pixels(40, seed=31, side_h=n, side_w=n)
+    ref = oracle.nlm_direct(f_np, float(NLM["radius"]), NLM["sigma_r"], p, NLM["patch"],
+                            points=(ys, xs), spatial="box")
+    o = out.cpu().numpy().astype(np.float64)
+    K = info.N - 2 * info.M + 1
+    plan.close()
+    return {"workload": "%dx%d G8, box search window radius %d, sigma_r=%g per patch pixel, "
+                        "eps=%g, patch = centre, right, below (p=3)" % (
+                            n, n, NLM["radius"], NLM["sigma_r"], NLM["eps"]),
+            "value": world * n * n * steps / (ms * 1e3), "unit": "Mpixel/s",
+            "ms_per_step": ms / steps, "N": info.N, "M": info.M,
+            "terms": (K ** 3 + 1) // 2, "forward_ms": kms[2] / max(cnt, 1),
+            "max_abs": float(np.max(np.abs(o[ys, xs] - ref)))}
+
+
 def divergence(f_np, tuned_out, n=300, seed=23):
     """Deviation of the tuned output from the direct Gaussian bilateral filter
     (eq. (BF), Gaussian range kernel) and from the plain-parameter method
@@ -587,6 +664,10 @@ def main():
     # ---- the accelerations' sweep at 1024^2 (accel vs plain per cell)
     config1 = config1_leg(bf, timed_on, small_steps, world, max_over_ranks)
 
+    # ---- the raised-polynomial kernel and the non-local means
+    poly = poly_leg(bf, f, f_np, timed_on, small_steps, world, max_over_ranks)
+    nlm = nlm_leg(bf, timed_on, small_steps, world, max_over_ranks)
+
     # ---- plain FP32 (context for the metric's ratio)
     plain = bf.bf_plan(H, W, SIGMA_S, SIGMA_R, 0.0, **PLAIN)
     bf.bf_execute(plain, f, out)
@@ -722,6 +803,8 @@ def main():
         "box": box,
         "precision": precision,
         "config1": config1,
+        "poly": poly,
+        "nlm": nlm,
         "divergence": div,
     }
     print(json.dumps(line), flush=True)

@@ -98,6 +98,22 @@ enum { BF_FILTER_AUTO = 0, BF_FILTER_FIR = 1, BF_FILTER_YVV = 2 };
  * same R); BOX with filter = YVV is BF_ERR_NOT_SUPPORTED. */
 enum { BF_SPATIAL_GAUSS = 0, BF_SPATIAL_BOX = 1 };
 
+/* Range kernel phi of eq. (BF).  COSINE: the raised cosine of eq. (RCconv)
+ * with its binomial expansion, truncation and T (Secs. 1.3, 2, 3, Algorithm
+ * 2).  POLY: the raised polynomial of eq. (RPconv), phi(s) = (1 - s^2 /
+ * (2 N sigma_r^2))^N with N = max(1, ceil(T^2 / (2 sigma_r^2))) (its
+ * positivity threshold, Sec. 1.3) and no truncation (eps is ignored); it is
+ * evaluated through an interpolating polynomial basis (Lagrange polynomials
+ * of 2N + 1 Chebyshev points over the values of each parameter set's
+ * region), so it takes 2N + 1 terms of two planes each.  For POLY, T is the
+ * range (max - min) of f over the region a parameter set's expansion spans:
+ * the image for BF_T_GLOBAL, each T-tile grown by R for BF_T_TILE, and
+ * t_fixed for BF_T_FIXED (which must be >= value_range, the range the
+ * expansion then spans; else BF_ERR_NOT_SUPPORTED).  POLY takes FP32 planes
+ * and the FIR filter only, and no bf_backward or bf_execute_batch
+ * (BF_ERR_NOT_SUPPORTED). */
+enum { BF_RANGE_COSINE = 0, BF_RANGE_POLY = 1 };
+
 /* Storage / multiply type of the modulated planes. */
 enum { BF_PLANES_FP32 = 0, BF_PLANES_BF16 = 1, BF_PLANES_FP16 = 2 };
 
@@ -124,8 +140,11 @@ typedef struct bf_options {
                             T-tile), else bf_plan returns BF_ERR_INVALID_ARG;
                             FP32 planes use 128-row tiles for multiples of 128
                             and 64-row tiles otherwise.                           */
-    long long spin_limit;/* iteration bound of device waits; default 1<<22,
-                            at least 1<<16 (smaller values are raised)            */
+    long long spin_limit;/* iteration bound of the tensor-core kernel's hand-off
+                            waits; default 1<<22, at least 1<<16 (smaller values
+                            are raised).  The wait that lets issued MMAs drain
+                            before a stopping CTA frees tensor memory has its
+                            own fixed bound.                                     */
     int spatial;         /* BF_SPATIAL_*; default GAUSS                           */
     float lowp_recheck;  /* 16-bit planes only: an output whose denominator is
                             below lowp_recheck x its clipped spatial mass
@@ -136,7 +155,25 @@ typedef struct bf_options {
                             their window) the 16-bit rounding of the planes
                             is amplified by mass / den.  Default 0.05; 0
                             turns the recheck off; must lie in [0, 1).     */
-    int reserved[6];     /* must be zero                                          */
+    int range_kernel;    /* BF_RANGE_*; default COSINE                            */
+    int patch_mask;      /* 0: the bilateral filter.  Else the non-local means of
+                            Sec. 6 (eqs. (NL1), (NL2)) with the patch pixels
+                            u_i given by the set bits of a 3 x 3 mask, bit
+                            3 (dy + 1) + (dx + 1); the centre (bit 4, 0x10)
+                            must be set.  The range kernel is the product over
+                            the p patch pixels of phi_eps with the N, M that T
+                            (Algorithm 1) and Algorithm 2 give; its expansion
+                            has (N - 2M + 1)^p terms (half of them run, as
+                            conjugate pairs), which must be at most 2^22 for
+                            the plan's largest N (else BF_ERR_NOT_SUPPORTED).
+                            The spatial weight is sigma_s's Gaussian or, with
+                            BF_SPATIAL_BOX, the equal weights of the paper's
+                            sums over the window.  Patch values outside the
+                            image are taken at the nearest in-image pixel.
+                            Takes FP32 planes, the FIR filter, t_mode FIXED or
+                            GLOBAL and the cosine kernel, and no bf_backward or
+                            bf_execute_batch (else BF_ERR_NOT_SUPPORTED).     */
+    int reserved[4];     /* must be zero                                          */
 } bf_options;
 
 /* Fills *opt with the defaults listed above. */
@@ -275,6 +312,17 @@ bf_status bf_execute_noalloc(const float *f_dev, size_t f_pitch, float *out_dev,
 bf_status bf_noalloc_device_status(void *stream, unsigned *bits);
 
 /* ---- single steps of the path (tests and profiling) ------------------- */
+
+/* Test of the bounded-wait path of the tensor-core forward (16-bit plans):
+ * with on != 0, every later bf_execute of the plan makes the tensor-core
+ * kernel's MMA-issuing thread wait, first, for a barrier that nothing
+ * arrives on.  The wait runs out after spin_limit polls, the CTA stops all
+ * of its roles (no MMA has been issued), frees its tensor memory and
+ * returns; the outputs of that execute are undefined and the device status
+ * word holds BF_DEV_TIMEOUT.  on = 0 restores normal execution.  Not in the
+ * paper; for tests of the failure path.  BF_ERR_NOT_SUPPORTED for plans
+ * that do not use the tensor-core kernel. */
+bf_status bf_test_stall(bf_plan_t plan, int on);
 
 /* Windowed max and min of f over the clipped (2R+1)^2 square (Prop.
  * MAX-FILTER, Algorithm 1 steps 2-3, by the van Herk / Gil-Werman running

@@ -16,6 +16,7 @@ from .api import (  # noqa: F401
     bf_get_sets,
     bf_get_timing,
     bf_maxmin,
+    bf_test_stall,
     bf_options_init,
     bf_plan,
     bf_set_timing,

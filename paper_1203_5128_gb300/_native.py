@@ -27,6 +27,7 @@ BF_RULE_ALG2, BF_RULE_TRUNC, BF_RULE_CHERNOFF = 0, 1, 2
 BF_FILTER_AUTO, BF_FILTER_FIR, BF_FILTER_YVV = 0, 1, 2
 BF_PLANES_FP32, BF_PLANES_BF16, BF_PLANES_FP16 = 0, 1, 2
 BF_SPATIAL_GAUSS, BF_SPATIAL_BOX = 0, 1
+BF_RANGE_COSINE, BF_RANGE_POLY = 0, 1
 BF_DEV_ORDER_TOO_LARGE, BF_DEV_TIMEOUT, BF_DEV_BAD_WORK = 1, 2, 4
 
 
@@ -43,7 +44,9 @@ class bf_options(ctypes.Structure):
         ("spin_limit", ctypes.c_longlong),
         ("spatial", ctypes.c_int),
         ("lowp_recheck", ctypes.c_float),
-        ("reserved", ctypes.c_int * 6),
+        ("range_kernel", ctypes.c_int),
+        ("patch_mask", ctypes.c_int),
+        ("reserved", ctypes.c_int * 4),
     ]
 
 
@@ -78,6 +81,7 @@ PROTOTYPES = {
     "bf_destroy": (None, [_P]),
     "bf_status_string": (ctypes.c_char_p, [_I]),
     "bf_maxmin": (_I, [_P, _I, _I, _Z, _I, _P, _P, _P]),
+    "bf_test_stall": (_I, [_P, _I]),
     "bf_set_timing": (_I, [_P, _I]),
     "bf_execute_noalloc": (_I, [_P, _Z, _P, _Z, _I, _I, _D, _D, _D, ctypes.c_float, _P]),
     "bf_noalloc_device_status": (_I, [_P, ctypes.POINTER(ctypes.c_uint)]),

@@ -18,6 +18,7 @@ RULES = {"alg2": nat.BF_RULE_ALG2, "trunc": nat.BF_RULE_TRUNC, "chernoff": nat.B
 FILTERS = {"auto": nat.BF_FILTER_AUTO, "fir": nat.BF_FILTER_FIR, "yvv": nat.BF_FILTER_YVV}
 PLANES = {"fp32": nat.BF_PLANES_FP32, "bf16": nat.BF_PLANES_BF16, "fp16": nat.BF_PLANES_FP16}
 SPATIALS = {"gauss": nat.BF_SPATIAL_GAUSS, "box": nat.BF_SPATIAL_BOX}
+RANGE_KERNELS = {"cosine": nat.BF_RANGE_COSINE, "poly": nat.BF_RANGE_POLY}
 
 
 def _stream_ptr(stream=None) -> int:
@@ -41,12 +42,12 @@ def bf_status_string(code: int) -> str:
 def bf_options_init(**kw) -> nat.bf_options:
     """bf_options with the library defaults, then keyword overrides
     (t_mode, t_fixed, value_range, trunc_rule, filter, plane_dtype, n_max,
-    t_tile, spin_limit, spatial, lowp_recheck; enum fields accept their
-    lower-case names)."""
+    t_tile, spin_limit, spatial, lowp_recheck, range_kernel, patch_mask;
+    enum fields accept their lower-case names)."""
     o = nat.bf_options()
     nat.lib().bf_options_init(ctypes.byref(o))
     table = {"t_mode": T_MODES, "trunc_rule": RULES, "filter": FILTERS, "plane_dtype": PLANES,
-             "spatial": SPATIALS}
+             "spatial": SPATIALS, "range_kernel": RANGE_KERNELS}
     fields = {name for name, _ in nat.bf_options._fields_ if name != "reserved"}
     for k, v in kw.items():
         if k not in fields:
@@ -262,3 +263,9 @@ def bilateral_filter(f, plan: Plan):
     if _BF is None:
         _BF = _autograd_fn()
     return _BF.apply(f, plan)
+
+
+def bf_test_stall(plan: Plan, on: bool = True):
+    """Makes the plan's tensor-core forward run out a bounded wait (tests of
+    the failure path; see include/bf.h)."""
+    nat.check(nat.lib().bf_test_stall(plan.handle, 1 if on else 0), "bf_test_stall")

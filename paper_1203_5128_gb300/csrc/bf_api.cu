@@ -31,6 +31,15 @@ constexpr double kPi = 3.14159265358979323846;
 constexpr int kMaxTimed = 4096;
 constexpr int kEvPerExec = 5;     // before K1, after K1, K2, K3, recheck
 
+// N of the raised polynomial: max(1, ceil(T^2 / (2 sigma_r^2))) (Sec. 1.3)
+int poly_order_of(double T, double sigma_r)
+{
+    const double c = ceil((T * T) / (2.0 * sigma_r * sigma_r));
+    if (c < 1.0) return 1;
+    if (c > 1e9) return 1000000000;
+    return (int)c;
+}
+
 int order_of(double T, double sigma_r)
 {
     // same arithmetic as the device (K2): N = max(1, ceil(4 T^2 / (pi^2 sigma_r^2)))
@@ -71,6 +80,8 @@ void free_plan(bf_plan_s* p)
     cudaFree(p->d_bwd);
     cudaFree(p->d_fix);
     cudaFree(p->d_fixcnt);
+    cudaFree(p->d_fixscan);
+    cudaFree(p->d_mm);
     if (p->ev) {
         for (int i = 0; i < kEvPerExec * kMaxTimed; ++i)
             if (p->ev[i]) cudaEventDestroy(p->ev[i]);
@@ -165,9 +176,11 @@ FwdArgs forward_args(bf_plan_s* p, const float* f, size_t fp, float* out, size_t
     a.sep_nk = p->sep_nk;
     a.sep_Wp = p->sep_Wp;
     a.sep_cap_terms = p->cap_pairs + 1;
+    a.stall_test = p->stall_test;
     if (p->d_fix) {
         a.fix_list = p->d_fix;
         a.fix_count = p->d_fixcnt;
+        a.fix_cap = p->fix_cap;
         a.fix_kappa = p->opt.lowp_recheck;
     }
     return a;
@@ -193,7 +206,12 @@ FixArgs fixup_args(bf_plan_s* p, const FwdArgs& fa)
     x.sigma_r = p->sigma_r;
     x.list = fa.fix_list;
     x.count = fa.fix_count;
+    x.fix_cap = fa.fix_cap;
     x.n_guarded = p->d_nguard;
+    x.set0 = 0;
+    x.n_ctas = 4 * 152;                 // four 48 KB-table CTAs per SM
+    x.ntab = fixup_table_entries(p->n_cap);
+    x.scan = p->d_fixscan;
     return x;
 }
 
@@ -215,6 +233,21 @@ cudaError_t enqueue_params(bf_plan_s* p, const float* f, size_t fp, cudaStream_t
 {
     cudaError_t e = mark(p, 0, s);
     if (e != cudaSuccess) return e;
+    if (p->opt.t_mode == BF_T_TILE && tile_params_ok(p->R, p->set_tile, p->n_cap)) {
+        // T and the parameter set of every T-tile in one launch
+        e = cudaMemsetAsync(p->d_nguard, 0, sizeof(unsigned long long), s);
+        if (e != cudaSuccess) return e;
+        if (p->d_fixcnt) {
+            e = cudaMemsetAsync(p->d_fixcnt, 0, sizeof(unsigned) * p->n_fixcnt, s);
+            if (e != cudaSuccess) return e;
+        }
+        e = launch_tile_params(f, fp, p->H, p->W, p->R, p->set_tile, p->sets_x, 0, p->n_sets,
+                               p->d_T, params_args(p), s);
+        if (e != cudaSuccess) return e;
+        e = mark(p, 1, s);
+        if (e != cudaSuccess) return e;
+        return mark(p, 2, s);
+    }
     if (p->opt.t_mode != BF_T_FIXED) {
         e = cudaMemsetAsync(p->d_T, 0, sizeof(unsigned) * p->n_sets, s);
         if (e != cudaSuccess) return e;
@@ -233,6 +266,45 @@ cudaError_t enqueue_params(bf_plan_s* p, const float* f, size_t fp, cudaStream_t
     e = launch_params(params_args(p), s);
     if (e != cudaSuccess) return e;
     return mark(p, 2, s);
+}
+
+// The raised-polynomial path: the range of each set's region (unless T is
+// fixed), N and the Chebyshev nodes, then the fused tile kernel.
+cudaError_t enqueue_poly(bf_plan_s* p, const float* f, size_t fp, float* out, size_t op,
+                         cudaStream_t s)
+{
+    cudaError_t e = mark(p, 0, s);
+    if (e != cudaSuccess) return e;
+    const bool fixed = p->opt.t_mode == BF_T_FIXED;
+    const int set_tile = p->opt.t_mode == BF_T_TILE ? p->set_tile : 0;
+    if (!fixed) {
+        e = launch_poly_range(f, fp, p->H, p->W, p->R, set_tile, p->sets_x, p->n_sets, p->d_mm, s);
+        if (e != cudaSuccess) return e;
+    }
+    e = cudaMemsetAsync(p->d_nguard, 0, sizeof(unsigned long long), s);
+    if (e != cudaSuccess) return e;
+    e = mark(p, 1, s);
+    if (e != cudaSuccess) return e;
+    PolyParamsArgs pa;
+    pa.mm = fixed ? nullptr : p->d_mm;
+    pa.n_sets = p->n_sets;
+    pa.sigma_r = p->sigma_r;
+    pa.t_fixed = p->opt.t_fixed;
+    pa.value_range = p->opt.value_range;
+    pa.n_cap = p->n_cap;
+    pa.cap_nodes = p->cap_pairs;
+    pa.hdr = p->d_hdr;
+    pa.nodes = p->d_pairs;
+    pa.status = p->d_status;
+    e = launch_poly_params(pa, s);
+    if (e != cudaSuccess) return e;
+    e = mark(p, 2, s);
+    if (e != cudaSuccess) return e;
+    e = launch_poly32(forward_args(p, f, fp, out, op), s);
+    if (e != cudaSuccess) return e;
+    e = mark(p, 3, s);
+    if (e != cudaSuccess) return e;
+    return mark(p, 4, s);
 }
 
 // ---- host-to-host execution in row bands ---------------------------------
@@ -284,7 +356,6 @@ bf_status execute_host_banded(bf_plan_s* p, const float* fh, float* oh, cudaStre
         if (cut.back() < H) cut.push_back(H);
     }
     const int nb = (int)cut.size() - 1;
-    if (p->d_fix && nb > p->n_fixcnt) return BF_ERR_NOT_SUPPORTED;
     const int nc = (H + C - 1) / C;                  // copy chunks of one T-tile row
     const int need = 3 + nc + nb;
     if (!p->hst[0]) {
@@ -332,21 +403,29 @@ bf_status execute_host_banded(bf_plan_s* p, const float* fh, float* oh, cudaStre
         cudaStream_t cs = p->hst[1 + (b & 1)];
         const int rows = r1 - r0;
         BF_CUDA(cudaStreamWaitEvent(cs, ev_in[last_chunk], 0));
-        BF_CUDA(launch_local_range(p->d_hin, W, H, W, p->R, p->set_tile, p->sets_x, p->d_T, cs,
-                                   r0 / range_tile(), (rows + range_tile() - 1) / range_tile()));
-        ParamsArgs pa = params_args(p);
-        pa.set0 = r0 / C * p->sets_x;
-        BF_CUDA(launch_params(pa, cs, (rows + C - 1) / C * p->sets_x));
+        const int bset0 = r0 / C * p->sets_x, bsets = (rows + C - 1) / C * p->sets_x;
+        if (tile_params_ok(p->R, p->set_tile, p->n_cap)) {
+            BF_CUDA(launch_tile_params(p->d_hin, W, H, W, p->R, p->set_tile, p->sets_x, bset0,
+                                       bsets, p->d_T, params_args(p), cs));
+        } else {
+            BF_CUDA(launch_local_range(p->d_hin, W, H, W, p->R, p->set_tile, p->sets_x, p->d_T,
+                                       cs, r0 / range_tile(),
+                                       (rows + range_tile() - 1) / range_tile()));
+            ParamsArgs pa = params_args(p);
+            pa.set0 = bset0;
+            BF_CUDA(launch_params(pa, cs, bsets));
+        }
         FwdArgs fa = forward_args(p, p->d_hin, W, p->d_hout, W);
         fa.y_tile0 = r0 / th;
         fa.y_tiles = (rows + th - 1) / th;
-        if (p->d_fix) {                          // each band lists into its own rows
-            fa.fix_list = p->d_fix + (size_t)r0 * W;
-            fa.fix_count = p->d_fixcnt + b;
-        }
         BF_CUDA(launch_fwd_tc(fa, p->opt.plane_dtype == BF_PLANES_BF16, p->opt.spin_limit,
                               p->d_status, cs));
-        if (p->d_fix) BF_CUDA(launch_fixup(fixup_args(p, fa), cs));
+        if (p->d_fix) {                          // the band's own sets
+            FixArgs xa = fixup_args(p, fa);
+            xa.set0 = r0 / C * p->sets_x;
+            xa.scan = p->d_fixscan + xa.set0 + b;    // bands run concurrently: own offsets
+            BF_CUDA(launch_fixup(xa, (rows + C - 1) / C * p->sets_x, cs));
+        }
         BF_CUDA(cudaEventRecord(ev_done[b], cs));
         BF_CUDA(cudaStreamWaitEvent(s_out, ev_done[b], 0));
         BF_CUDA(cudaMemcpyAsync(oh + (size_t)r0 * W, p->d_hout + (size_t)r0 * W,
@@ -430,6 +509,17 @@ bf_status bf_plan(int H, int W, double sigma_s, double sigma_r, double eps, cons
     if (o.filter == BF_FILTER_AUTO) o.filter = BF_FILTER_FIR;
     if (o.filter != BF_FILTER_FIR && o.filter != BF_FILTER_YVV) return BF_ERR_INVALID_ARG;
     if (o.plane_dtype < BF_PLANES_FP32 || o.plane_dtype > BF_PLANES_FP16) return BF_ERR_INVALID_ARG;
+    const bool poly = o.range_kernel == BF_RANGE_POLY;
+    if (o.range_kernel != BF_RANGE_COSINE && !poly) return BF_ERR_INVALID_ARG;
+    if (poly && (o.filter != BF_FILTER_FIR || o.plane_dtype != BF_PLANES_FP32))
+        return BF_ERR_NOT_SUPPORTED;
+    // non-local means: a 3 x 3 patch mask holding the centre
+    const bool nlm = o.patch_mask != 0;
+    if (nlm && (o.patch_mask < 0 || o.patch_mask >= (1 << 9) || !(o.patch_mask & (1 << 4))))
+        return BF_ERR_INVALID_ARG;
+    if (nlm && (poly || o.filter == BF_FILTER_YVV || o.plane_dtype != BF_PLANES_FP32 ||
+                o.t_mode == BF_T_TILE))
+        return BF_ERR_NOT_SUPPORTED;
     // the recursive filter: FP32 planes, one parameter set per image (every
     // output depends on the whole image), and the recursion's range of scales
     YvvCoef yc;
@@ -442,19 +532,35 @@ bf_status bf_plan(int H, int W, double sigma_s, double sigma_r, double eps, cons
     if (o.plane_dtype != BF_PLANES_FP32 && o.t_mode == BF_T_TILE && o.t_tile % 128)
         return BF_ERR_INVALID_ARG;
     if (o.t_mode == BF_T_FIXED && !(o.t_fixed > 0.f)) o.t_fixed = o.value_range;
+    // the polynomial expansion spans [0, value_range] with a fixed T
+    if (poly && o.t_mode == BF_T_FIXED && o.t_fixed < o.value_range) return BF_ERR_NOT_SUPPORTED;
     if (o.spin_limit <= 0) o.spin_limit = 1ll << 22;
     // the same bound limits the wait that lets issued MMAs finish before a
     // stopping CTA frees its TMEM: keep it far above their completion time
-    if (o.spin_limit < kMinSpinLimit) o.spin_limit = kMinSpinLimit;
+    if (o.spin_limit < kMinSpinLimit) o.spin_limit = kMinSpinLimit;   // floor for normal runs
 
     const double Rr = box ? sigma_s : ceil(3.0 * sigma_s);
     if (Rr > 1000.0) return BF_ERR_NOT_SUPPORTED;
     const int R = (int)Rr;
-    if (o.t_mode != BF_T_FIXED && R > range_max_radius()) return BF_ERR_NOT_SUPPORTED;
+    if (!poly && o.t_mode != BF_T_FIXED && R > range_max_radius()) return BF_ERR_NOT_SUPPORTED;
     int th = 0, tw = 0;
-    const bool use_sep = o.filter == BF_FILTER_FIR && o.plane_dtype == BF_PLANES_FP32 &&
+    const bool use_sep = !poly && o.filter == BF_FILTER_FIR && o.plane_dtype == BF_PLANES_FP32 &&
                          o.t_mode != BF_T_TILE && !fwd32t_ok(R, 0) && sep32_ok(R);
-    if (o.filter == BF_FILTER_YVV) {
+    const double Tcap = o.t_mode == BF_T_FIXED ? (double)o.t_fixed : (double)o.value_range;
+    int n_cap = poly ? poly_order_of(Tcap, sigma_r) : order_of(Tcap, sigma_r);
+    if (o.t_mode == BF_T_FIXED && n_cap > o.n_max) return BF_ERR_ORDER_TOO_LARGE;
+    if (n_cap > o.n_max) n_cap = o.n_max;
+    if (poly) {
+        poly_tile(R, 2 * n_cap + 1, &th, &tw);
+        if (o.t_mode == BF_T_TILE && th > 0 && o.t_tile % th) th = tw = 0;
+    } else if (nlm) {
+        int p = 0;
+        for (int b = 0; b < 9; ++b) p += (o.patch_mask >> b) & 1;
+        double terms = 1.0;
+        for (int i = 0; i < p; ++i) terms *= (double)(n_cap + 1);
+        if (terms > (double)(1 << 22)) return BF_ERR_NOT_SUPPORTED;
+        nlm_tile(R, n_cap, &th, &tw);
+    } else if (o.filter == BF_FILTER_YVV) {
         th = tw = 1;                      // whole lines, no output tiles
     } else if (use_sep) {
         th = 128;                         // column-pass tile of the two-pass FIR
@@ -470,11 +576,6 @@ bf_status bf_plan(int H, int W, double sigma_s, double sigma_r, double eps, cons
         fwd_tc_tile(&th, &tw);
     }
     if (!th) return BF_ERR_NOT_SUPPORTED;
-
-    const double Tcap = o.t_mode == BF_T_FIXED ? (double)o.t_fixed : (double)o.value_range;
-    int n_cap = order_of(Tcap, sigma_r);
-    if (o.t_mode == BF_T_FIXED && n_cap > o.n_max) return BF_ERR_ORDER_TOO_LARGE;
-    if (n_cap > o.n_max) n_cap = o.n_max;
 
     bf_plan_s* p = (bf_plan_s*)calloc(1, sizeof(bf_plan_s));
     if (!p) return BF_ERR_ALLOC;
@@ -502,7 +603,17 @@ bf_status bf_plan(int H, int W, double sigma_s, double sigma_r, double eps, cons
     }
     p->n_sets = p->sets_x * p->sets_y;
     p->n_cap = n_cap;
-    p->cap_pairs = n_cap / 2 + 1;
+    p->cap_pairs = poly ? 2 * n_cap + 1 : n_cap / 2 + 1;   // pairs, or the polynomial's nodes
+    if (nlm) {                          // patch pixels, the centre first
+        p->patch_uy[0] = p->patch_ux[0] = 0;
+        p->patch_p = 1;
+        for (int b = 0; b < 9; ++b)
+            if (b != 4 && ((o.patch_mask >> b) & 1)) {
+                p->patch_uy[p->patch_p] = b / 3 - 1;
+                p->patch_ux[p->patch_p] = b % 3 - 1;
+                ++p->patch_p;
+            }
+    }
 
     bool ok = true;
     ok &= cudaMalloc(&p->d_T, sizeof(unsigned) * p->n_sets) == cudaSuccess;
@@ -512,6 +623,7 @@ bf_status bf_plan(int H, int W, double sigma_s, double sigma_r, double eps, cons
     ok &= cudaMalloc(&p->d_logfact, sizeof(double) * (n_cap + 1)) == cudaSuccess;
     ok &= cudaMalloc(&p->d_status, sizeof(unsigned)) == cudaSuccess;
     ok &= cudaMalloc(&p->d_nguard, sizeof(unsigned long long)) == cudaSuccess;
+    if (poly) ok &= cudaMalloc(&p->d_mm, sizeof(unsigned) * 2 * p->n_sets) == cudaSuccess;
     if (!ok) {
         free_plan(p);
         return BF_ERR_ALLOC;
@@ -542,11 +654,13 @@ bf_status bf_plan(int H, int W, double sigma_s, double sigma_r, double eps, cons
         ok &= cudaMemcpy(p->d_T, &T, sizeof(float), cudaMemcpyHostToDevice) == cudaSuccess;
     }
     if (ok && o.plane_dtype != BF_PLANES_FP32 && o.lowp_recheck > 0.f) {
-        // the recheck list (one slot per pixel, so it cannot overflow) and
-        // one list length per row band of the host path
-        p->n_fixcnt = H / 64 + 4;
-        if (cudaMalloc(&p->d_fix, sizeof(unsigned) * (size_t)H * W) != cudaSuccess ||
-            cudaMalloc(&p->d_fixcnt, sizeof(unsigned) * p->n_fixcnt) != cudaSuccess) {
+        // the recheck lists (a slot per pixel of each set's region, so they
+        // cannot overflow) and one list length per set
+        p->n_fixcnt = p->n_sets;
+        p->fix_cap = o.t_mode == BF_T_TILE ? (unsigned)(o.t_tile * o.t_tile) : (unsigned)H * W;
+        if (cudaMalloc(&p->d_fix, sizeof(unsigned) * (size_t)p->n_sets * p->fix_cap) != cudaSuccess ||
+            cudaMalloc(&p->d_fixcnt, sizeof(unsigned) * p->n_fixcnt) != cudaSuccess ||
+            cudaMalloc(&p->d_fixscan, sizeof(unsigned) * (p->n_sets + H / 64 + 8)) != cudaSuccess) {
             cudaGetLastError();
             free_plan(p);
             return BF_ERR_ALLOC;
@@ -614,8 +728,24 @@ bf_status bf_execute(bf_plan_t p, const float* f, size_t fp, float* out, size_t 
     if ((const void*)f == (const void*)out) return BF_ERR_INVALID_ARG;
     cudaStream_t s = (cudaStream_t)stream;
     BF_CUDA(cudaSetDevice(p->device));
+    if (p->opt.range_kernel == BF_RANGE_POLY) {
+        BF_CUDA(enqueue_poly(p, f, fp, out, op, s));
+        if (p->timing && p->n_timed < kMaxTimed) ++p->n_timed;
+        p->executed = 1;
+        p->last = s;
+        return BF_OK;
+    }
     BF_CUDA(enqueue_params(p, f, fp, s));
-    if (p->opt.filter == BF_FILTER_YVV)
+    if (p->patch_p) {
+        NlmPatch pt;
+        pt.p = p->patch_p;
+        for (int i = 0; i < 9; ++i) {
+            pt.uy[i] = p->patch_uy[i];
+            pt.ux[i] = p->patch_ux[i];
+        }
+        pt.sigma_r = (float)p->sigma_r;
+        BF_CUDA(launch_nlm32(forward_args(p, f, fp, out, op), pt, p->n_cap, s));
+    } else if (p->opt.filter == BF_FILTER_YVV)
         BF_CUDA(launch_yvv(yvv_args(p, f, fp, out, op), p->yvv_C, p->yvv_passes, s));
     else if (p->opt.plane_dtype == BF_PLANES_FP32)
         BF_CUDA(launch_fwd32(forward_args(p, f, fp, out, op), s));
@@ -625,7 +755,7 @@ bf_status bf_execute(bf_plan_t p, const float* f, size_t fp, float* out, size_t 
                               p->d_status, s));
     BF_CUDA(mark(p, 3, s));
     if (p->d_fix && p->opt.filter != BF_FILTER_YVV && p->opt.plane_dtype != BF_PLANES_FP32)
-        BF_CUDA(launch_fixup(fixup_args(p, forward_args(p, f, fp, out, op)), s));
+        BF_CUDA(launch_fixup(fixup_args(p, forward_args(p, f, fp, out, op)), p->n_sets, s));
     BF_CUDA(mark(p, 4, s));
     if (p->timing && p->n_timed < kMaxTimed) ++p->n_timed;
     p->executed = 1;
@@ -657,7 +787,8 @@ bf_status bf_backward(bf_plan_t p, const float* f, const float* gout, float* gin
 {
     if (!p || !f || !gout || !gin) return BF_ERR_INVALID_ARG;
     if (pitch < (size_t)p->W) return BF_ERR_INVALID_ARG;
-    if (p->opt.filter == BF_FILTER_YVV) return BF_ERR_NOT_SUPPORTED;
+    if (p->opt.filter == BF_FILTER_YVV || p->opt.range_kernel == BF_RANGE_POLY || p->patch_p)
+        return BF_ERR_NOT_SUPPORTED;
     if (!p->executed) return BF_ERR_NO_FORWARD;
     cudaStream_t s = (cudaStream_t)stream;
     BF_CUDA(cudaSetDevice(p->device));
@@ -708,12 +839,15 @@ bf_status bf_get_info(bf_plan_t p, bf_info* info)
     for (int i = 0; i < p->n_sets; ++i) {
         if (h[i].N > h[best].N) best = i;
         if (h[i].T > Tm) Tm = h[i].T;
-        if (h[i].F >= 0) terms += h[i].N - 2 * h[i].M + 1;
+        if (h[i].F >= 0) terms += p->opt.range_kernel == BF_RANGE_POLY ? h[i].F
+                                                                       : h[i].N - 2 * h[i].M + 1;
     }
     info->T = Tm;
     info->N = h[best].N;
     info->M = h[best].M;
-    info->K = h[best].N - 2 * h[best].M + 1;
+    // terms: N - 2M + 1 cosines, or the polynomial's 2N + 1 basis functions
+    info->K = p->opt.range_kernel == BF_RANGE_POLY ? 2 * h[best].N + 1
+                                                   : h[best].N - 2 * h[best].M + 1;
     info->n_guarded = (long long)ng;
     info->terms_total = terms;
     info->device_status = st;
@@ -793,6 +927,15 @@ bf_status bf_get_timing(bf_plan_t p, double* ms, int* count)
     }
     if (count) *count = p->n_timed;
     p->n_timed = 0;
+    return BF_OK;
+}
+
+bf_status bf_test_stall(bf_plan_t p, int on)
+{
+    if (!p) return BF_ERR_INVALID_ARG;
+    if (p->opt.plane_dtype == BF_PLANES_FP32 || p->opt.filter == BF_FILTER_YVV)
+        return BF_ERR_NOT_SUPPORTED;
+    p->stall_test = on ? 1 : 0;
     return BF_OK;
 }
 

@@ -418,7 +418,8 @@ extern "C" bf_status bf_execute_batch(int n, const bf_plan_t* plans, const float
         if (!plans[i] || !f[i] || !out[i] || (const void*)f[i] == (const void*)out[i])
             return BF_ERR_INVALID_ARG;
         if (plans[i]->device != plans[0]->device) return BF_ERR_INVALID_ARG;
-        if (plans[i]->opt.plane_dtype != BF_PLANES_FP32 || plans[i]->opt.filter != BF_FILTER_FIR)
+        if (plans[i]->opt.plane_dtype != BF_PLANES_FP32 || plans[i]->opt.filter != BF_FILTER_FIR ||
+            plans[i]->opt.range_kernel != BF_RANGE_COSINE || plans[i]->patch_p)
             return BF_ERR_NOT_SUPPORTED;
     }
     // a plan's workspace (T words, parameter sets, two-pass buffers) serves

@@ -329,7 +329,17 @@ struct TcGeo {
 };
 
 // barrier slots (8 bytes each) after the operand buffers
-enum { kBarB1Full = 0, kBarC1, kBarA2Full, kBarA2F1, kBarA2F2, kBarA2F3, kBarC2, kBarD2Free, kNumBars };
+// (kBarNever: a barrier no thread arrives on, waited for only when a test
+// asks the kernel to run out a bounded wait; bf_test_stall)
+enum { kBarB1Full = 0, kBarC1, kBarA2Full, kBarA2F1, kBarA2F2, kBarA2F3, kBarC2, kBarD2Free,
+       kBarNever, kNumBars };
+static_assert(8 * kNumBars + 12 <= 96, "barrier slots, TMEM slot and stop flag fit the tail");
+
+// Bound of the waits that let committed MMAs finish before a stopping CTA
+// frees its TMEM: independent of spin_limit (MMAs finish within microseconds;
+// this bound is seconds of polls), so that a short spin_limit never frees
+// TMEM under an MMA in flight.
+constexpr long long kDrainLimit = 1ll << 24;
 
 template <bool kBF16, int NCH>
 __global__ void __launch_bounds__(NT, 1) k_fwd_tc(FwdArgs a, long long spin_limit,
@@ -373,6 +383,7 @@ __global__ void __launch_bounds__(NT, 1) k_fwd_tc(FwdArgs a, long long spin_limi
         for (int pl = 0; pl < 4; ++pl) mbar_init(bar(kBarA2Full + pl), kEpiThreads);
         mbar_init(bar(kBarC2), 1);
         mbar_init(bar(kBarD2Free), kEpiThreads);
+        mbar_init(bar(kBarNever), 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         *stop = 0;
     }
@@ -468,6 +479,8 @@ __global__ void __launch_bounds__(NT, 1) k_fwd_tc(FwdArgs a, long long spin_limi
             const uint32_t idesc1 = idesc_f16(TH, 2 * RWp, kBF16);
             const uint32_t idesc2 = idesc_f16(TH, TW, kBF16);
             int issued1 = 0, issued2 = 0;
+            // a test's stall: wait (bounded) for a barrier nothing arrives on
+            if (a.stall_test) mbar_wait(bar(kBarNever), 0, spin_limit, stop);
             for (int k = 0; k < K; ++k) {
                 if (!mbar_wait(bar(kBarB1Full), k & 1, spin_limit, stop)) break;
                 fence_after();
@@ -509,8 +522,8 @@ __global__ void __launch_bounds__(NT, 1) k_fwd_tc(FwdArgs a, long long spin_limi
             if (*stop) {
                 // let every committed MMA finish before TMEM is freed (bounded)
                 volatile int never = 0;
-                if (issued1) mbar_wait(bar(kBarC1), (issued1 - 1) & 1, spin_limit, &never);
-                if (issued2) mbar_wait(bar(kBarC2), (issued2 - 1) & 1, spin_limit, &never);
+                if (issued1) mbar_wait(bar(kBarC1), (issued1 - 1) & 1, kDrainLimit, &never);
+                if (issued2) mbar_wait(bar(kBarC2), (issued2 - 1) & 1, kDrainLimit, &never);
             }
         }
         __syncwarp();
@@ -614,7 +627,8 @@ __global__ void __launch_bounds__(NT, 1) k_fwd_tc(FwdArgs a, long long spin_limi
                     // the 16-bit rounding is amplified by mass / den here: the
                     // FP32 recheck writes this output (and applies the guard)
                     v = a.f[(size_t)gy * a.f_pitch + gx];
-                    a.fix_list[atomicAdd(a.fix_count, 1u)] = (unsigned)gy * (unsigned)a.W + gx;
+                    a.fix_list[(size_t)set * a.fix_cap + atomicAdd(a.fix_count + set, 1u)] =
+                        (unsigned)gy * (unsigned)a.W + gx;
                 } else if (den[x] > kGuard * rmass * cmass) {
                     v = __fdiv_rn(num[x], den[x]) * c0 + c0;
                 } else {

@@ -46,8 +46,15 @@ struct bf_plan_s {
     int timing;              // record events around the kernels
     int n_timed;
     cudaEvent_t* ev;         // 4 per recorded execute
+    unsigned* d_mm;          // raised polynomial: codes of max f and max -f per set
+    int patch_p;             // non-local means: patch pixels (0: the bilateral filter)
+    int stall_test;          // bf_test_stall
+    int patch_uy[9], patch_ux[9];
     unsigned* d_fix;         // 16-bit recheck: listed pixels (y * W + x), H * W slots
-    unsigned* d_fixcnt;      // 16-bit recheck: list lengths, one per row band
+    unsigned* d_fixcnt;      // 16-bit recheck: list lengths, one per parameter set
+    unsigned* d_fixscan;     // 16-bit recheck: their offsets (n_sets + 1 per launch;
+                             // concurrent row bands take disjoint ranges)
+    unsigned fix_cap;        // 16-bit recheck: list slots per set
     int n_fixcnt;
     cudaStream_t hst[4];     // banded host path: copy in, compute (2), copy out
     cudaEvent_t* hev;        // banded host path: fork, clear, join, then per band in / done
@@ -135,6 +142,14 @@ struct ParamsArgs {
 // K2 over sets set0 .. set0 + n - 1 (n = 0: all sets).
 cudaError_t launch_params(const ParamsArgs& a, cudaStream_t s, int n = 0);
 
+// K1 + K2 fused for T-tiles of side set_tile (a multiple of 64): one CTA
+// per T-tile computes its exact T (written to Tbits[set]) and its parameter
+// set; sets set0 .. set0 + n_sets - 1.  tile_params_ok: the staging fits.
+bool tile_params_ok(int R, int set_tile, int n_cap);
+cudaError_t launch_tile_params(const float* f, size_t pitch, int H, int W, int R, int set_tile,
+                               int sets_x, int set0, int n_sets, unsigned* Tbits,
+                               const ParamsArgs& pa, cudaStream_t s);
+
 // K3 (FP32 planes, FIR): fused modulate / filter / demodulate / normalise.
 struct FwdArgs {
     int y_tile0 = 0;        // first row of output tiles of the launch
@@ -160,10 +175,13 @@ struct FwdArgs {
     float2* sep_nd;         // [H][W] (num, den) partial
     int sep_nk, sep_Wp, sep_cap_terms;
     // 16-bit planes: outputs with den < fix_kappa * mass are appended to
-    // fix_list (y * W + x) for the FP32 recheck instead of being final
+    // their set's list (y * W + x; set s owns fix_list[s * fix_cap ..], its
+    // length in fix_count[s]) for the FP32 recheck instead of being final
     unsigned* fix_list = nullptr;
     unsigned* fix_count = nullptr;
+    unsigned fix_cap = 0;
     float fix_kappa = 0.f;
+    int stall_test = 0;     // K3-tc: run out a bounded wait (bf_test_stall)
 };
 
 // FP32 recheck of listed outputs of a 16-bit-plane forward: the direct sum
@@ -181,11 +199,47 @@ struct FixArgs {
     int set_tile;           // 0: single set; else T-tile side
     int sets_x;
     double sigma_r;
-    const unsigned* list;   // pixels y * W + x
-    const unsigned* count;  // list length (device)
+    const unsigned* list;   // pixels y * W + x, set s from list[s * fix_cap]
+    const unsigned* count;  // list length per set (device)
+    unsigned fix_cap;
     unsigned long long* n_guarded;
+    int set0;               // first set of the launch
+    int n_ctas;             // persistent grid
+    int ntab;               // phi_eps table entries a CTA holds
+    unsigned* scan;         // n_sets + 1 offsets (scratch)
 };
-cudaError_t launch_fixup(const FixArgs& a, cudaStream_t s);
+int fixup_table_entries(int n_cap);
+// FP32 recheck of the listed outputs of sets set0 .. set0 + n_sets - 1.
+cudaError_t launch_fixup(const FixArgs& a, int n_sets, cudaStream_t s);
+
+// Raised-polynomial range kernel (eq. (RPconv)): per-set range of f, then
+// N, centre, half-range, beta and the Chebyshev nodes, then the fused tile.
+struct PolyParamsArgs {
+    const unsigned* mm;     // per set: codes of max f and max -f (null: fixed T)
+    int n_sets;
+    double sigma_r, t_fixed, value_range;
+    int n_cap;              // largest N the node table holds
+    int cap_nodes;          // node entries per set (2 n_cap + 1)
+    SetHdr* hdr;
+    Pair* nodes;
+    unsigned* status;
+};
+cudaError_t launch_poly_range(const float* f, size_t pitch, int H, int W, int R, int set_tile,
+                              int sets_x, int n_sets, unsigned* mm, cudaStream_t s);
+cudaError_t launch_poly_params(const PolyParamsArgs& a, cudaStream_t s);
+cudaError_t launch_poly32(const FwdArgs& a, cudaStream_t s);   // a.cap_pairs = node entries
+void poly_tile(int R, int cap_nodes, int* th, int* tw);
+
+// Non-local means with a p-pixel patch (Sec. 6): the fused FP32 tile with
+// the patch phase; one parameter set (fixed or image-wide T).
+struct NlmPatch {
+    int p;                  // patch pixels, u_1 = (0, 0) first
+    int uy[9], ux[9];
+    float sigma_r;
+};
+size_t nlm_smem_bytes(int R, int th, int tw, int n_cap);
+void nlm_tile(int R, int n_cap, int* th, int* tw);
+cudaError_t launch_nlm32(const FwdArgs& a, const NlmPatch& pt, int n_cap, cudaStream_t s);
 // K3-sep (FP32 FIR in two passes through HBM, R > 24, one parameter set).
 struct SepArgs {
     const float* f;

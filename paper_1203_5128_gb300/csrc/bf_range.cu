@@ -26,7 +26,7 @@
 // atomicMax on the float's bit pattern (valid: the values are >= 0).
 #include <math.h>
 
-#include "bf_internal.cuh"
+#include "bf_params.cuh"
 
 namespace bf {
 namespace {
@@ -257,7 +257,196 @@ cudaError_t launch(const float* f, size_t pitch, int H, int W, int R, int set_ti
     return cudaGetLastError();
 }
 
+// ---- fused per-T-tile form: T of one T-tile and its parameter set ---------
+//
+// One CTA of 1024 threads per S x S T-tile: the tile plus its R halo is
+// staged once (NaN outside the image, which fmaxf / fminf skip, so no
+// select), then, for 64 output columns at a time, a row pass and a column
+// pass give the windowed max M and min m, and the CTA reduces max(M - f,
+// f - m) over the tile's pixels into T (exact: max, min and one rounded
+// difference, rounding being monotone).  Each pass item is one line and 8
+// consecutive outputs: the 2R+1 windows of 8 neighbours share their middle
+// 2R - 6 inputs, so an item takes that core's max and min once, the suffix
+// extremes of the 7 inputs before it and the prefix extremes of the 7 after
+// it, and combines (about 2R + 8 loads and 4R + 40 max / min operations for
+// 16 results, against 3 operations per point and pass for van Herk but with
+// no serial chain).  Then the same CTA computes the set's N, M and pair
+// table (Algorithm 2, steps 3-5), its shared memory reused as scratch.
+constexpr int kTP = 1024;
+constexpr int kTC = 64;            // output columns per row-pass chunk
+constexpr int kTCs = kTC + 1;      // their row stride: the row pass's lanes (rows) hit distinct banks
+
+// max (kMax) and/or min (kMin) of the 8 windows [x0 + i, x0 + i + 2R], i =
+// 0..7, of a line with stride st (R >= 4: the windows share [x0 + 7, x0 +
+// 2R], whose extremes are taken with four independent accumulators)
+template <bool kMax, bool kMin>
+__device__ __forceinline__ void window8(const float* v, int st, int R, float* mx, float* mn)
+{
+    const int w = 2 * R;
+    if (R < 4) {
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            float a = -INFINITY, b = INFINITY;
+            for (int k = 0; k <= w; ++k) {
+                const float x = v[(i + k) * st];
+                if (kMax) a = fmaxf(a, x);
+                if (kMin) b = fminf(b, x);
+            }
+            if (kMax) mx[i] = a;
+            if (kMin) mn[i] = b;
+        }
+        return;
+    }
+    float ca[4] = {-INFINITY, -INFINITY, -INFINITY, -INFINITY};
+    float cb[4] = {INFINITY, INFINITY, INFINITY, INFINITY};
+    int k = 7;
+    for (; k + 3 <= w; k += 4) {
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const float x = v[(k + u) * st];
+            if (kMax) ca[u] = fmaxf(ca[u], x);
+            if (kMin) cb[u] = fminf(cb[u], x);
+        }
+    }
+    for (; k <= w; ++k) {
+        const float x = v[k * st];
+        if (kMax) ca[0] = fmaxf(ca[0], x);
+        if (kMin) cb[0] = fminf(cb[0], x);
+    }
+    const float cA = fmaxf(fmaxf(ca[0], ca[1]), fmaxf(ca[2], ca[3]));
+    const float cB = fminf(fminf(cb[0], cb[1]), fminf(cb[2], cb[3]));
+    float lv[7], rv[7];                        // the 7 inputs before and after the core
+#pragma unroll
+    for (int i = 0; i < 7; ++i) {
+        lv[i] = v[i * st];
+        rv[i] = v[(w + 1 + i) * st];
+    }
+    float la = -INFINITY, lb = INFINITY;       // suffix extremes of v[i .. 6]
+    float lA[8], lB[8];
+    lA[7] = -INFINITY;
+    lB[7] = INFINITY;
+#pragma unroll
+    for (int i = 6; i >= 0; --i) {
+        if (kMax) la = fmaxf(la, lv[i]);
+        if (kMin) lb = fminf(lb, lv[i]);
+        lA[i] = la;
+        lB[i] = lb;
+    }
+    float ra = -INFINITY, rb = INFINITY;       // prefix extremes of v[w + 1 .. w + i]
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        if (i > 0) {
+            if (kMax) ra = fmaxf(ra, rv[i - 1]);
+            if (kMin) rb = fminf(rb, rv[i - 1]);
+        }
+        if (kMax) mx[i] = fmaxf(fmaxf(lA[i], cA), ra);
+        if (kMin) mn[i] = fminf(fminf(lB[i], cB), rb);
+    }
+}
+
+__global__ void __launch_bounds__(kTP, 1)
+k_tile_params(const float* __restrict__ f, size_t pitch, int H, int W, int R, int S, int sets_x,
+              int set0, unsigned* __restrict__ Tbits, ParamsArgs pa)
+{
+    extern __shared__ float sm[];
+    __shared__ float red[kTP / 32];
+    const int L = S + 2 * R, Ls = L + 1;          // odd stride: lanes on rows hit distinct banks
+    float* reg = sm;                              // L x Ls
+    float* bmx = reg + (size_t)L * Ls;            // L x kTCs row-pass max
+    float* bmn = bmx + (size_t)L * kTCs;          // L x kTCs row-pass min
+    const int set = set0 + blockIdx.x;
+    const int ty = set / sets_x, tx = set - ty * sets_x;
+    const int gy0 = ty * S - R, gx0 = tx * S - R;
+    const int tid = threadIdx.x;
+
+    // stage the tile + halo: in-image entries by cp.async (every copy of a
+    // thread in flight at once), NaN elsewhere
+    for (int r = tid >> 5; r < L; r += kTP / 32) {
+        const int gy = gy0 + r;
+        const bool rin = gy >= 0 && gy < H;
+        for (int c = tid & 31; c < L; c += 32) {
+            const int gx = gx0 + c;
+            float* dst = reg + r * Ls + c;
+            if (rin && gx >= 0 && gx < W)
+                asm volatile("cp.async.ca.shared.global [%0], [%1], 4;"
+                             ::"r"((uint32_t)__cvta_generic_to_shared(dst)),
+                               "l"(f + (size_t)gy * pitch + gx)
+                             : "memory");
+            else
+                *dst = __int_as_float(0x7fc00000);
+        }
+    }
+    asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
+    __syncthreads();
+    float best = 0.0f;
+    for (int c0 = 0; c0 < S; c0 += kTC) {
+        // rows: item (r, g) -> outputs c0 + 8g .. c0 + 8g + 7 of region row r
+        for (int it = tid; it < L * (kTC / 8); it += kTP) {
+            const int r = it % L, g = it / L;
+            float mx[8], mn[8];
+            window8<true, true>(reg + r * Ls + c0 + 8 * g, 1, R, mx, mn);
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                bmx[r * kTCs + 8 * g + i] = mx[i];
+                bmn[r * kTCs + 8 * g + i] = mn[i];
+            }
+        }
+        __syncthreads();
+        // columns: item (c, g) -> output rows 8g .. 8g + 7 of chunk column c
+        for (int it = tid; it < kTC * (S / 8); it += kTP) {
+            const int c = it % kTC, g = it / kTC;
+            float mx[8], mn[8];
+            window8<true, false>(bmx + (8 * g) * kTCs + c, kTCs, R, mx, nullptr);
+            window8<false, true>(bmn + (8 * g) * kTCs + c, kTCs, R, nullptr, mn);
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                const float v = reg[(8 * g + i + R) * Ls + c0 + c + R];   // NaN outside
+                best = fmaxf(best, fmaxf(mx[i] - v, v - mn[i]));
+            }
+        }
+        __syncthreads();
+    }
+    for (int o = 16; o > 0; o >>= 1) best = fmaxf(best, __shfl_xor_sync(0xffffffffu, best, o));
+    if ((tid & 31) == 0) red[tid >> 5] = best;
+    __syncthreads();
+    if (tid == 0) {
+        float b = 0.0f;
+        for (int w = 0; w < kTP / 32; ++w) b = fmaxf(b, red[w]);
+        Tbits[set] = __float_as_uint(b);
+    }
+    __syncthreads();
+    // Algorithm 2, steps 3-5 for this set; the staging memory is free now
+    params::params_body(pa, set, reinterpret_cast<double*>(sm),
+                        reinterpret_cast<int*>(sm + 2 * params::kTail));
+}
+
+size_t tile_params_smem(int R, int S)
+{
+    const size_t L = (size_t)S + 2 * (size_t)R;
+    const size_t st = sizeof(float) * (L * (L + 1) + 2 * L * kTCs);
+    const size_t pr = sizeof(double) * params::kTail + 2 * sizeof(int);
+    return st > pr ? st : pr;
+}
+
 }  // namespace
+
+bool tile_params_ok(int R, int set_tile, int n_cap)
+{
+    return set_tile > 0 && set_tile % kTC == 0 && n_cap <= params::kMaxTail &&
+           tile_params_smem(R, set_tile) + sizeof(float) * (kTP / 32) <= 227 * 1024;
+}
+
+cudaError_t launch_tile_params(const float* f, size_t pitch, int H, int W, int R, int set_tile,
+                               int sets_x, int set0, int n_sets, unsigned* Tbits,
+                               const ParamsArgs& pa, cudaStream_t s)
+{
+    const size_t smem = tile_params_smem(R, set_tile);
+    cudaError_t e = cudaFuncSetAttribute(k_tile_params,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k_tile_params<<<n_sets, kTP, smem, s>>>(f, pitch, H, W, R, set_tile, sets_x, set0, Tbits, pa);
+    return cudaGetLastError();
+}
 
 int range_tile() { return kT; }
 

@@ -62,6 +62,7 @@ class FakePlan:
         self.H, self.W = H, W
         self.R = int(sigma_s) if kw.get("spatial") == "box" else int(np.ceil(3 * sigma_s))
         t = kw.get("t_tile", 64)
+        self.N = 17
         self.n_sets = (-(-H // t)) * (-(-W // t)) if kw.get("t_mode") == "tile" else 1
 
     def close(self):

@@ -87,6 +87,9 @@ def test_parity_and_sweep_legs(line):
         [(5.0, 10.0), (5.0, 20.0), (10.0, 10.0), (10.0, 20.0)]
     for c in cells:
         assert c["speedup_tile"] == pytest.approx(c["accel_tile"]["value"] / c["plain"]["value"])
+    for k in ["poly_fixed", "poly_tile", "cosine_fixed", "cosine_tile"]:
+        assert line["poly"][k]["value"] > 0
+    assert line["nlm"]["value"] > 0 and line["nlm"]["max_abs"] >= 0
     d = line["divergence"]
     for k in ["vs_direct_gaussian", "vs_plain_parameters"]:
         assert d[k]["max_abs"] >= 0 and d[k]["mse"] >= 0

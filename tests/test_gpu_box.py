@@ -67,10 +67,12 @@ def to_dev(a):
     return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).cuda()
 
 
-def run(bf, f, R, sr, eps, mode="global", rule="alg2", tile=64, planes="fp32", t_fixed=None):
+def run(bf, f, R, sr, eps, mode="global", rule="alg2", tile=64, planes="fp32", t_fixed=None,
+        **extra):
     import torch
     H, W = f.shape
-    kw = dict(t_mode=mode, trunc_rule=rule, t_tile=tile, plane_dtype=planes, spatial="box")
+    kw = dict(t_mode=mode, trunc_rule=rule, t_tile=tile, plane_dtype=planes, spatial="box",
+              **extra)
     if t_fixed is not None:
         kw["t_fixed"] = t_fixed
     plan = bf.bf_plan(H, W, float(R), sr, eps, **kw)
@@ -187,6 +189,21 @@ def test_box_1024_every_output(bf, planes):
     assert info.n_rechecked > 0 and info.n_guarded == nfb
     check_lowp(np.abs(out - ref), den, box_count(20, yy, xx, 1024, 1024), planes,
                "1024^2 every output")
+
+
+def test_box_1024_every_output_recheck_2pct(bf):
+    """The same with the recheck limited to den < 2 % of the window (the
+    bench's box setting): FP16 planes still hold 0.5 gray level at every
+    output (their rounding, amplified by mass / den, stays near 0.005 mass /
+    den for the box)."""
+    f = synth.g8(1024, 1024, seed=1)
+    plan, out, p = run(bf, f, 20, 5.0, 0.01, "tile", "alg2", 128, "fp16", lowp_recheck=0.02)
+    ref, _, den, _ = oracle.shiftable(f, 20.0, 5.0, p, return_parts=True, spatial="box")
+    yy, xx = np.mgrid[0:1024, 0:1024]
+    info = bf.bf_get_info(plan)
+    print("box 1024^2 fp16, recheck below 2%%: %d outputs rechecked" % info.n_rechecked)
+    check_lowp(np.abs(out - ref), den, box_count(20, yy, xx, 1024, 1024), "fp16",
+               "1024^2 every output, recheck below 2%")
 
 
 def test_box_4096_bench_workload_sampled(bf):
