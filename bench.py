@@ -616,6 +616,17 @@ def main():
     bs_ms = max_over_ranks(time_region(separate, b_steps))
     for bp in b_plans:
         bp.close()
+    # the same batch with FP16 planes wherever the tensor-core kernel takes
+    # the radius (R <= 24), FP32 planes elsewhere
+    b16_kinds = ["fp16" if int(np.ceil(3 * bss)) <= 24 else "fp32" for _, _, bss, _ in specs]
+    b16_plans = [bf.bf_plan(bh, bw, bss, bsr, EPS, plane_dtype=k)
+                 for (bh, bw, bss, bsr), k in zip(specs, b16_kinds)]
+    bf.bf_execute_batch(b16_plans, b_fs, b_outs)
+    barrier()
+    b16_ms = max_over_ranks(time_region(lambda: bf.bf_execute_batch(b16_plans, b_fs, b_outs),
+                                        b_steps))
+    for bp in b16_plans:
+        bp.close()
     del b_fs, b_outs
 
     # ---- differentiation: 16 x 512 x 512, sigma_s = 4, sigma_r = 25, eps = 1e-2,
@@ -794,7 +805,11 @@ def main():
                   "graph": {"value": world * b_px / (bg_ms * 1e3), "unit": "Mpixel/s",
                             "ms": bg_ms},
                   "separate_calls": {"value": world * b_px / (bs_ms * 1e3), "unit": "Mpixel/s",
-                                     "ms": bs_ms}},
+                                     "ms": bs_ms},
+                  "graph_fp16": {"value": world * b_px / (b16_ms * 1e3), "unit": "Mpixel/s",
+                                 "ms": b16_ms, "fp16_images": b16_kinds.count("fp16"),
+                                 "note": "FP16 planes (tensor cores, FP32 recheck) where R <= 24, "
+                                         "FP32 planes elsewhere"}},
         "backward": {"workload": "16 x 512x512 G8, sigma_s=4, sigma_r=25, eps=1e-2, exact T; "
                                 "forward + adjoint of L = sum(w * out), w ~ N(0,1); "
                                 "4 plans on 4 streams",

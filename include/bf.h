@@ -221,7 +221,9 @@ bf_status bf_backward(bf_plan_t plan, const float *f_dev, const float *grad_out_
  * in one persistent launch fed by a tile work queue.  Images are contiguous
  * (pitch = W of their plan).  Each image needs a plan of its own (a plan
  * named twice is BF_ERR_INVALID_ARG: its workspace serves one image at a
- * time).  FP32 FIR plans only (else BF_ERR_NOT_SUPPORTED).  The results
+ * time).  FIR plans with the cosine kernel and no patch (else
+ * BF_ERR_NOT_SUPPORTED); 16-bit plans run the tensor-core kernel and its
+ * FP32 recheck as launches of their own inside the graph.  The results
  * equal n bf_execute calls bit for bit. */
 bf_status bf_execute_batch(int n, const bf_plan_t *plans, const float *const *f_dev,
                            float *const *out_dev, void *stream);

@@ -9,10 +9,11 @@
 //      time order), each item run by the same tile body as bf_execute.
 //
 // Images whose radius is beyond the fused tall tile (and whose plan holds the
-// two-pass workspace) run the two-pass FIR instead, and images large enough
-// to fill a quarter of the GPU with the fused tall tile run that kernel: both
-// as their own launches, after the batched K1 and K2, on side streams of the
-// capture that the graph runs concurrently with the queue.
+// two-pass workspace) run the two-pass FIR instead, images large enough to
+// fill a quarter of the GPU with the fused tall tile run that kernel, and
+// images with 16-bit planes run the tensor-core kernel and its FP32 recheck:
+// all as their own launches, after the batched K1 and K2, on side streams of
+// the capture that the graph runs concurrently with the queue.
 //
 // The FP32 forward's arithmetic per output does not depend on the tile shape
 // (every FIR sums its nonzero taps in increasing order; zero-padded taps add
@@ -148,7 +149,8 @@ bf_status build_state(int n, const bf_plan_t* plans, const float* const* f, floa
         const int rows = fwd32t_rows(set_tile) > 0 ? fwd32t_rows(set_tile) : 128;
         const long long tall_ctas = (long long)((p->H + rows - 1) / rows) * ((p->W + 31) / 32);
         two_pass[i] = (p->d_sep_P && set_tile == 0 && !fwd32t_ok(p->R, 0) && sep32_ok(p->R)) ||
-                      (fwd32t_ok(p->R, set_tile) && 4 * tall_ctas >= sms0);
+                      (fwd32t_ok(p->R, set_tile) && 4 * tall_ctas >= sms0) ||
+                      p->opt.plane_dtype != BF_PLANES_FP32;
     }
     // ---- tile shape per queued image (autotuned per R, remembered per process)
     std::vector<std::pair<int, int>> shape(n);
@@ -207,6 +209,10 @@ bf_status build_state(int n, const bf_plan_t* plans, const float* const* f, floa
             zero_n.push_back(p->n_sets);
         }
         zero_g.push_back(p->d_nguard);
+        if (p->d_fixcnt) {               // the recheck's list lengths start at zero
+            zero_T.push_back(p->d_fixcnt);
+            zero_n.push_back(p->n_fixcnt);
+        }
         pimg[i] = plan_params_args(p);
         for (int sI = 0; sI < p->n_sets; ++sI) {
             bimg.push_back(i);
@@ -339,8 +345,18 @@ bf_status build_state(int n, const bf_plan_t* plans, const float* const* f, floa
             return (long long)plans[x]->H * plans[x]->W * plans[x]->cap_pairs >
                    (long long)plans[y]->H * plans[y]->W * plans[y]->cap_pairs;
         });
-        for (size_t j = 0; j < own.size() && e == cudaSuccess; ++j)
-            e = launch_fwd32(fimg[own[j]], side[j % kSide]);
+        for (size_t j = 0; j < own.size() && e == cudaSuccess; ++j) {
+            bf_plan_s* p = plans[own[j]];
+            cudaStream_t ss = side[j % kSide];
+            if (p->opt.plane_dtype == BF_PLANES_FP32) {
+                e = launch_fwd32(fimg[own[j]], ss);
+            } else {
+                e = launch_fwd_tc(fimg[own[j]], p->opt.plane_dtype == BF_PLANES_BF16,
+                                  p->opt.spin_limit, p->d_status, ss);
+                if (e == cudaSuccess && p->d_fix)
+                    e = launch_fixup(fixup_args(p, fimg[own[j]]), p->n_sets, ss);
+            }
+        }
         for (size_t c = 0; c < classes.size() && e == cudaSuccess; ++c)
             e = launch_fwd32_persistent(classes[c].first, classes[c].second, cmaxR[c],
                                         reinterpret_cast<const FwdArgs*>(d + oF),
@@ -418,8 +434,8 @@ extern "C" bf_status bf_execute_batch(int n, const bf_plan_t* plans, const float
         if (!plans[i] || !f[i] || !out[i] || (const void*)f[i] == (const void*)out[i])
             return BF_ERR_INVALID_ARG;
         if (plans[i]->device != plans[0]->device) return BF_ERR_INVALID_ARG;
-        if (plans[i]->opt.plane_dtype != BF_PLANES_FP32 || plans[i]->opt.filter != BF_FILTER_FIR ||
-            plans[i]->opt.range_kernel != BF_RANGE_COSINE || plans[i]->patch_p)
+        if (plans[i]->opt.filter != BF_FILTER_FIR || plans[i]->opt.range_kernel != BF_RANGE_COSINE ||
+            plans[i]->patch_p)
             return BF_ERR_NOT_SUPPORTED;
     }
     // a plan's workspace (T words, parameter sets, two-pass buffers) serves

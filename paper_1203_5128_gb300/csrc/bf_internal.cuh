@@ -209,6 +209,8 @@ struct FixArgs {
     unsigned* scan;         // n_sets + 1 offsets (scratch)
 };
 int fixup_table_entries(int n_cap);
+// The recheck of what a 16-bit forward with arguments fa lists (bf_api.cu).
+FixArgs fixup_args(bf_plan_s* p, const FwdArgs& fa);
 // FP32 recheck of the listed outputs of sets set0 .. set0 + n_sets - 1.
 cudaError_t launch_fixup(const FixArgs& a, int n_sets, cudaStream_t s);
 

@@ -4,7 +4,9 @@ by a tile queue, captured in a CUDA graph).
 The batch must reproduce n separate bf_execute calls bit for bit (the
 forward's arithmetic does not depend on which tile shape serves an image),
 on the first call and on later calls that reuse the captured graph with new
-image contents; one image is also checked against the FP64 oracle.
+image contents, with FP32 and 16-bit planes; images are also checked against
+the FP64 oracle (one of the mixed batch, every image of the 64-image
+workload at sampled pixels).
 """
 import numpy as np
 import pytest
@@ -92,12 +94,75 @@ def test_batch_workload_bitwise(bf):
         p_.close()
 
 
-def test_batch_rejects_reduced_precision(bf):
+def test_batch_reduced_precision_bitwise(bf):
+    """16-bit plans (FP16 and BF16 planes on the tensor cores, exact T of the
+    image or per 128 x 128 T-tile) in one batch with FP32 plans: each image
+    equals its own bf_execute bit for bit (the recheck lists depend on the
+    launch order, its per-pixel results do not), on the first call and on a
+    replay of the graph with new contents."""
     import torch
-    p = bf.bf_plan(64, 64, 2.0, 20.0, 0.01, plane_dtype="fp16")
-    f = torch.zeros((64, 64), device="cuda")
-    with pytest.raises(bf.BfError):
-        bf.bf_execute_batch([p], [f])
+    rng = np.random.default_rng(17)
+    plans, fs = [], []
+    kinds = [("fp16", "global"), ("bf16", "tile"), ("fp32", "global"), ("fp16", "tile"),
+             ("bf16", "global"), ("fp32", "tile")]
+    for k, (planes, mode) in enumerate(kinds):
+        H, W = int(rng.integers(130, 400)), int(rng.integers(100, 380))
+        ss, sr = float(rng.uniform(1.5, 8.0)), float(rng.uniform(10.0, 40.0))
+        kw = dict(t_mode=mode, plane_dtype=planes)
+        if mode == "tile":
+            kw["t_tile"] = 128
+        plans.append(bf.bf_plan(H, W, ss, sr, 0.01, **kw))
+        fs.append(torch.from_numpy(synth.g8(H, W, seed=500 + k)).cuda())
+    for rep in range(2):
+        if rep:
+            for k, f in enumerate(fs):
+                f.copy_(torch.from_numpy(synth.g8(*f.shape, seed=700 + k)).cuda())
+        outs = bf.bf_execute_batch(plans, fs, None if rep == 0 else outs)
+        torch.cuda.synchronize()
+        ref = separate(bf, plans, fs)
+        for k, (o, r) in enumerate(zip(outs, ref)):
+            assert np.array_equal(o.cpu().numpy(), r), (rep, k, kinds[k])
+    for p_ in plans:
+        assert bf.bf_get_device_status(p_) == 0
+        p_.close()
+
+
+def test_batch_workload_fp16_every_image_vs_oracle(bf):
+    """The 64-image workload with FP16 planes wherever the tensor-core kernel
+    takes the radius (R <= 24) and FP32 planes elsewhere: bitwise equal to
+    64 bf_execute calls, and every image against the FP64 oracle's direct
+    form at sampled pixels (random, corners, borders): FP16 images within
+    0.5 gray level, FP32 images within the FP32 bar."""
+    import torch
+    specs = synth.batch_specs(64, seed=3)
+    plans, fs, nps, kinds = [], [], [], []
+    for k, (H, W, ss, sr) in enumerate(specs):
+        planes = "fp16" if int(np.ceil(3 * ss)) <= 24 else "fp32"
+        plans.append(bf.bf_plan(H, W, ss, sr, 0.01, plane_dtype=planes))
+        a = synth.g8(H, W, seed=3000 + k)
+        nps.append(a)
+        fs.append(torch.from_numpy(a).cuda())
+        kinds.append(planes)
+    assert "fp16" in kinds and "fp32" in kinds
+    ref = separate(bf, plans, fs)
+    outs = bf.bf_execute_batch(plans, fs)
+    torch.cuda.synchronize()
+    worst = {"fp16": 0.0, "fp32": 0.0}
+    for k, ((H, W, ss, sr), o, r) in enumerate(zip(specs, outs, ref)):
+        o = o.cpu().numpy()
+        assert np.array_equal(o, r), k
+        p = oracle.resolve(nps[k], ss, sr, 0.01, t_mode="global")
+        rng = np.random.default_rng(k)
+        ys = np.concatenate([rng.integers(0, H, 24), [0, H - 1, 0, H - 1, H // 2]])
+        xs = np.concatenate([rng.integers(0, W, 24), [0, W - 1, W - 1, 0, 0]])
+        d = oracle.direct(nps[k], ss, sr, p, points=(ys, xs))
+        err = float(np.max(np.abs(o[ys, xs] - d)))
+        worst[kinds[k]] = max(worst[kinds[k]], err)
+        assert err <= (0.5 if kinds[k] == "fp16" else 5e-3), (k, kinds[k], err)
+    print("64-image batch vs the oracle at sampled pixels: max-abs FP16 %.3g, FP32 %.3g" % (
+        worst["fp16"], worst["fp32"]))
+    for p_ in plans:
+        p_.close()
 
 
 def test_batch_rejects_a_plan_named_twice(bf):
