@@ -617,18 +617,21 @@ __global__ void __launch_bounds__(NT, 1) k_fwd_tc(FwdArgs a, long long spin_limi
             // normalise with the guard (FP32 clipped Gaussian mass) and store
             const float full = full_mass(a.taps, R);
             const float rmass = clipped_mass(a.taps, R, gy, a.H, full);
+            // outputs whose den is under fix_kappa of their mass: the 16-bit
+            // rounding is amplified by mass / den there, so the FP32 recheck
+            // writes them (and applies the guard); they are only marked in the
+            // unrolled loop and listed after it, which keeps the loop small
+            const float kap = a.fix_list ? a.fix_kappa : 0.f;
+            uint32_t listed = 0u;
 #pragma unroll
             for (int x = 0; x < TW; ++x) {
                 const int gx = bx + x;
                 if (gx >= a.W) continue;
                 const float cmass = clipped_mass(a.taps, R, gx, a.W, full);
                 float v;
-                if (a.fix_list && den[x] < a.fix_kappa * rmass * cmass) {
-                    // the 16-bit rounding is amplified by mass / den here: the
-                    // FP32 recheck writes this output (and applies the guard)
+                if (den[x] < kap * rmass * cmass) {
+                    listed |= 1u << x;
                     v = a.f[(size_t)gy * a.f_pitch + gx];
-                    a.fix_list[(size_t)set * a.fix_cap + atomicAdd(a.fix_count + set, 1u)] =
-                        (unsigned)gy * (unsigned)a.W + gx;
                 } else if (den[x] > kGuard * rmass * cmass) {
                     v = __fdiv_rn(num[x], den[x]) * c0 + c0;
                 } else {
@@ -636,6 +639,12 @@ __global__ void __launch_bounds__(NT, 1) k_fwd_tc(FwdArgs a, long long spin_limi
                     atomicAdd(a.n_guarded, 1ull);
                 }
                 a.out[(size_t)gy * a.out_pitch + gx] = v;
+            }
+            while (listed) {
+                const int x = __ffs(listed) - 1;
+                listed &= listed - 1u;
+                a.fix_list[(size_t)set * a.fix_cap + atomicAdd(a.fix_count + set, 1u)] =
+                    (unsigned)gy * (unsigned)a.W + (unsigned)(bx + x);
             }
         }
     }
