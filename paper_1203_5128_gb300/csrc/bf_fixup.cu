@@ -155,7 +155,7 @@ __device__ void load_set(const FixArgs& a, int set, float* wk, float* tab, SetCo
 // Persistent: CTA b takes items [b T / G, (b + 1) T / G) of the launch's
 // T listed outputs in set order (scan gives each set's first item), builds
 // the table of every set it meets and hands the items to its warps.
-__global__ void __launch_bounds__(kThreads) k_fixup(FixArgs a, const unsigned* __restrict__ scan,
+__global__ void __launch_bounds__(kThreads, 4) k_fixup(FixArgs a, const unsigned* __restrict__ scan,
                                                     int n_sets)
 {
     extern __shared__ float sm[];
@@ -197,49 +197,59 @@ __global__ void __launch_bounds__(kThreads) k_fixup(FixArgs a, const unsigned* _
             const float fx = a.f[(size_t)gy * a.f_pitch + gx];
             float ns = 0.f, nc = 0.f, ds = 0.f, dc = 0.f;
             constexpr int kU = 8;                      // window loads in flight per lane
+            // window position of this lane's first neighbour, then advanced by
+            // 32 positions per step without a division
+            int iy = lane / RW, ix = lane - (lane / RW) * RW;
             for (int p0 = lane; p0 < RW * RW; p0 += 32 * kU) {
-            float fv[kU];
-            int iyv[kU], ixv[kU];
+                float fv[kU], gv[kU];                  // neighbour value, spatial weight
 #pragma unroll
-            for (int u = 0; u < kU; ++u) {
-                const int p = p0 + 32 * u;
-                const int iy = p / RW, ix = p - iy * RW;
-                const int y = gy + iy - a.R, x = gx + ix - a.R;
-                const bool in = p < RW * RW && y >= 0 && y < a.H && x >= 0 && x < a.W;
-                fv[u] = in ? __ldg(a.f + (size_t)y * a.f_pitch + x) : __int_as_float(0x7fc00000);
-                iyv[u] = iy;
-                ixv[u] = ix;
-            }
-#pragma unroll
-            for (int u = 0; u < kU; ++u) {
-                const bool in = !isnan(fv[u]);
-                const int iy = iyv[u], ix = ixv[u];
-                const float fy = in ? fv[u] : fx;
-                // d = fy - fx = dh + dl exactly
-                const float dh = fy - fx;
-                const float t = dh - fy;
-                const float dl = (fy - (dh - t)) + (-fx - t);
-                const float q = fabsf(dh) * inv_h;
-                const int j0 = (int)q;
-                float phi;
-                if (use_tab && j0 + 3 <= J) {
-                    const float u = q - (float)j0;
-                    const float v0 = tab[j0], v1 = tab[j0 + 1], v2 = tab[j0 + 2], v3 = tab[j0 + 3];
-                    const float um1 = u - 1.f, um2 = u - 2.f, up1 = u + 1.f;
-                    const float wa = -u * um1 * um2 * (1.f / 6.f);
-                    const float wb = up1 * um1 * um2 * 0.5f;
-                    const float wc = -up1 * u * um2 * 0.5f;
-                    const float wd = up1 * u * um1 * (1.f / 6.f);
-                    phi = fmaf(wa, v0, fmaf(wb, v1, fmaf(wc, v2, wd * v3)));
-                    // first-order term of the tail: phi'(s) ~ (v2 - v1) / h
-                    phi = fmaf((v2 - v1) * inv_h, dh < 0.f ? -dl : dl, phi);
-                } else {
-                    phi = phi_sum(dh, dl, sc, wk);
+                for (int u = 0; u < kU; ++u) {
+                    const int y = gy + iy - a.R, x = gx + ix - a.R;
+                    const bool in = p0 + 32 * u < RW * RW && y >= 0 && y < a.H && x >= 0 &&
+                                    x < a.W;
+                    fv[u] = in ? __ldg(a.f + (size_t)y * a.f_pitch + x)
+                               : __int_as_float(0x7fc00000);
+                    gv[u] = taps[min(iy, RW - 1)] * taps[min(ix, RW - 1)];
+                    ix += 32;
+                    while (ix >= RW) {
+                        ix -= RW;
+                        ++iy;
+                    }
                 }
-                const float wgt = in ? taps[iy] * taps[ix] * phi : 0.f;
-                comp_add(ds, dc, wgt);
-                comp_add(ns, nc, wgt * dh);
-            }
+                // plain sums over the kU terms of this step, compensated across steps
+                float dsum = 0.f, nsum = 0.f;
+#pragma unroll
+                for (int u = 0; u < kU; ++u) {
+                    if (isnan(fv[u])) continue;
+                    const float fy = fv[u];
+                    // d = fy - fx = dh + dl exactly
+                    const float dh = fy - fx;
+                    const float t = dh - fy;
+                    const float dl = (fy - (dh - t)) + (-fx - t);
+                    const float q = fabsf(dh) * inv_h;
+                    const int j0 = (int)q;
+                    float phi;
+                    if (use_tab && j0 + 3 <= J) {
+                        const float uu = q - (float)j0;
+                        const float v0 = tab[j0], v1 = tab[j0 + 1], v2 = tab[j0 + 2],
+                                    v3 = tab[j0 + 3];
+                        const float um1 = uu - 1.f, um2 = uu - 2.f, up1 = uu + 1.f;
+                        const float wa = -uu * um1 * um2 * (1.f / 6.f);
+                        const float wb = up1 * um1 * um2 * 0.5f;
+                        const float wc = -up1 * uu * um2 * 0.5f;
+                        const float wd = up1 * uu * um1 * (1.f / 6.f);
+                        phi = fmaf(wa, v0, fmaf(wb, v1, fmaf(wc, v2, wd * v3)));
+                        // first-order term of the tail: phi'(s) ~ (v2 - v1) / h
+                        phi = fmaf((v2 - v1) * inv_h, dh < 0.f ? -dl : dl, phi);
+                    } else {
+                        phi = phi_sum(dh, dl, sc, wk);
+                    }
+                    const float wgt = gv[u] * phi;
+                    dsum += wgt;
+                    nsum = fmaf(wgt, dh, nsum);
+                }
+                comp_add(ds, dc, dsum);
+                comp_add(ns, nc, nsum);
             }
 #pragma unroll
             for (int off = 16; off > 0; off >>= 1) {
