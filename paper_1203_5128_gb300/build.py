@@ -18,7 +18,7 @@ OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libbf.so")
 INCLUDE = os.path.join(ROOT, "include")
 
-SOURCES = ["bf_api.cu", "bf_range.cu", "bf_params.cu", "bf_fwd32.cu", "bf_fwd_tc.cu", "bf_fixup.cu", "bf_poly.cu", "bf_nlm.cu",
+SOURCES = ["bf_api.cu", "bf_range.cu", "bf_params.cu", "bf_fwd32.cu", "bf_fwd_tc.cu", "bf_fixup.cu", "bf_poly.cu", "bf_nlm.cu", "bf_box32.cu",
            "bf_bwd32.cu", "bf_batch.cu", "bf_noalloc.cu", "bf_yvv.cu", "bf_sep32.cu"]
 HEADERS = ["bf_internal.cuh", "bf_fir32.cuh"]
 

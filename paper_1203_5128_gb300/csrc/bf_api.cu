@@ -52,6 +52,19 @@ int order_of(double T, double sigma_r)
 
 bf_status cuda_status(cudaError_t e) { return e == cudaSuccess ? BF_OK : BF_ERR_CUDA; }
 
+// The box filter's FP32 planes take the exact running-sum kernel where the
+// FIR would need its small 16 x 16 tiles (per-T-tile plans at large radii;
+// image-wide T takes the two-pass FIR, faster there).
+bool box_running_sums(const bf_options& o, int R)
+{
+    if (o.spatial != BF_SPATIAL_BOX || o.range_kernel != BF_RANGE_COSINE || o.patch_mask ||
+        o.plane_dtype != BF_PLANES_FP32 || o.filter == BF_FILTER_YVV || o.t_mode != BF_T_TILE)
+        return false;
+    int th = 0, tw = 0;
+    fwd32_tile(R, &th, &tw);
+    return th < 32 && !fwd32t_ok(R, o.t_tile) && box32_rows(R, o.t_tile) > 0;
+}
+
 #define BF_CUDA(call)                                      \
     do {                                                   \
         cudaError_t e_ = (call);                           \
@@ -177,6 +190,7 @@ FwdArgs forward_args(bf_plan_s* p, const float* f, size_t fp, float* out, size_t
     a.sep_Wp = p->sep_Wp;
     a.sep_cap_terms = p->cap_pairs + 1;
     a.stall_test = p->stall_test;
+    a.box_rs = box_running_sums(p->opt, p->R);
     if (p->d_fix) {
         a.fix_list = p->d_fix;
         a.fix_count = p->d_fixcnt;
@@ -544,8 +558,10 @@ bf_status bf_plan(int H, int W, double sigma_s, double sigma_r, double eps, cons
     const int R = (int)Rr;
     if (!poly && o.t_mode != BF_T_FIXED && R > range_max_radius()) return BF_ERR_NOT_SUPPORTED;
     int th = 0, tw = 0;
-    const bool use_sep = !poly && o.filter == BF_FILTER_FIR && o.plane_dtype == BF_PLANES_FP32 &&
-                         o.t_mode != BF_T_TILE && !fwd32t_ok(R, 0) && sep32_ok(R);
+    const bool box_rs = box_running_sums(o, R);
+    const bool use_sep = !poly && !box_rs && o.filter == BF_FILTER_FIR &&
+                         o.plane_dtype == BF_PLANES_FP32 && o.t_mode != BF_T_TILE &&
+                         !fwd32t_ok(R, 0) && sep32_ok(R);
     const double Tcap = o.t_mode == BF_T_FIXED ? (double)o.t_fixed : (double)o.value_range;
     int n_cap = poly ? poly_order_of(Tcap, sigma_r) : order_of(Tcap, sigma_r);
     if (o.t_mode == BF_T_FIXED && n_cap > o.n_max) return BF_ERR_ORDER_TOO_LARGE;
@@ -564,6 +580,9 @@ bf_status bf_plan(int H, int W, double sigma_s, double sigma_r, double eps, cons
         th = tw = 1;                      // whole lines, no output tiles
     } else if (use_sep) {
         th = 128;                         // column-pass tile of the two-pass FIR
+        tw = 32;
+    } else if (o.plane_dtype == BF_PLANES_FP32 && box_rs) {
+        th = box32_rows(R, o.t_mode == BF_T_TILE ? o.t_tile : 0);
         tw = 32;
     } else if (o.plane_dtype == BF_PLANES_FP32) {
         fwd32_tile(R, &th, &tw);

@@ -150,7 +150,8 @@ bf_status build_state(int n, const bf_plan_t* plans, const float* const* f, floa
         const long long tall_ctas = (long long)((p->H + rows - 1) / rows) * ((p->W + 31) / 32);
         two_pass[i] = (p->d_sep_P && set_tile == 0 && !fwd32t_ok(p->R, 0) && sep32_ok(p->R)) ||
                       (fwd32t_ok(p->R, set_tile) && 4 * tall_ctas >= sms0) ||
-                      p->opt.plane_dtype != BF_PLANES_FP32;
+                      p->opt.plane_dtype != BF_PLANES_FP32 ||
+                      forward_args(p, f[i], p->W, out[i], p->W).box_rs;   // running sums
     }
     // ---- tile shape per queued image (autotuned per R, remembered per process)
     std::vector<std::pair<int, int>> shape(n);

@@ -502,6 +502,7 @@ bool fwd32t_ok(int R, int set_tile)
 
 cudaError_t launch_fwd32(const FwdArgs& a, cudaStream_t s)
 {
+    if (a.box_rs) return launch_box32(a, s);     // box filter: exact running sums
     if (a.sep_P && a.set_tile == 0 && !fwd32t_ok(a.R, 0) && sep32_ok(a.R)) {
         SepArgs sa;
         sa.f = a.f;

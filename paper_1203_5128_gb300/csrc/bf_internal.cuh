@@ -182,6 +182,7 @@ struct FwdArgs {
     unsigned fix_cap = 0;
     float fix_kappa = 0.f;
     int stall_test = 0;     // K3-tc: run out a bounded wait (bf_test_stall)
+    int box_rs = 0;         // box spatial filter: FP32 planes by exact running sums
 };
 
 // FP32 recheck of listed outputs of a 16-bit-plane forward: the direct sum
@@ -242,6 +243,10 @@ struct NlmPatch {
 size_t nlm_smem_bytes(int R, int th, int tw, int n_cap);
 void nlm_tile(int R, int n_cap, int* th, int* tw);
 cudaError_t launch_nlm32(const FwdArgs& a, const NlmPatch& pt, int n_cap, cudaStream_t s);
+// Box spatial filter with FP32 planes by exact integer running sums (any R
+// up to 63): output rows of its tile (0 when none fits), the launch.
+int box32_rows(int R, int set_tile);
+cudaError_t launch_box32(const FwdArgs& a, cudaStream_t s);
 // K3-sep (FP32 FIR in two passes through HBM, R > 24, one parameter set).
 struct SepArgs {
     const float* f;

@@ -2,8 +2,10 @@
 of radius sigma_s with which Sec. 4 compares SHIFTABLE-BF and BF2) against
 the oracle's box mode, through the C ABI.
 
-The box runs through the same kernels as the Gaussian with unit taps, so the
-bars are the Gaussian's: T, N, M bit-exact; FP32 planes within 1e-3 gray
+The box runs through the same kernels as the Gaussian with unit taps, except
+per-T-tile FP32 plans at radii where the FIR would need its 16 x 16 tiles
+(R of 44 to 48), which take the exact integer running sums; the bars are the
+Gaussian's: T, N, M bit-exact; FP32 planes within 1e-3 gray
 levels of the oracle with the same (T, N, M), plus FP32 roundoff times the
 pixel's condition number mass / den where den is a small part of the
 window's mass (every pixel of the window weighs 1, so the mass is the
@@ -119,6 +121,8 @@ FP32_CASES = [
     (300, 140, 20, 5.0, 0.01, "tile", "alg2", 128),      # the paper's radius 20, sigma_r = 5
     (1, 200, 4, 20.0, 0.01, "global", "alg2", 64),       # one row
     (64, 150, 30, 25.0, 0.01, "global", "alg2", 64),     # R = 30: two passes through HBM
+    (150, 110, 48, 20.0, 0.01, "tile", "alg2", 64),      # per-tile R = 48: integer running sums
+    (97, 140, 44, 30.0, 0.0, "tile", "trunc", 64),       # per-tile R = 44, ragged, no truncation
 ]
 
 
