@@ -621,7 +621,9 @@ __global__ void __launch_bounds__(NT, 1) k_fwd_tc(FwdArgs a, long long spin_limi
             // rounding is amplified by mass / den there, so the FP32 recheck
             // writes them (and applies the guard); they are only marked in the
             // unrolled loop and listed after it, which keeps the loop small
-            const float kap = a.fix_list ? a.fix_kappa : 0.f;
+            // (no list when the recheck is off: then nothing is listed, not
+            // even an output whose den is negative)
+            const float kap = a.fix_list ? a.fix_kappa : -INFINITY;
             uint32_t listed = 0u;
 #pragma unroll
             for (int x = 0; x < TW; ++x) {

@@ -65,3 +65,31 @@ def test_guard_count_and_fallback_on_gpu(bf, planes):
             assert abs(o[i, j] - ref[i, j]) <= 1e-3 * abs(ref[i, j])
     err = np.abs(o.astype(np.float64) - ref)[mask]
     assert err.max() <= (1e-3 if planes == "fp32" else 0.5)
+
+
+def test_fp16_without_recheck_guards_negative_den(bf):
+    """16-bit planes with the FP32 recheck off (lowp_recheck = 0): K3-tc's
+    own guard takes the outputs whose den is negative -- here the two
+    outliers at den = -0.5 % of their mass, below the FP16 rounding bound of
+    den (4 u mass, u = 2^-11: 0.2 %) -- and outputs f there; nothing is
+    listed for a recheck that the plan does not run."""
+    import torch
+    H, W = 60, 80
+    N, M = nm_py()
+    f = np.zeros((H, W))
+    for i, j, ratio in SPOTS:
+        f[i, j] = outlier_height(ratio, i, j, H, W, N, M)
+    f32 = f.astype(np.float32)
+    plan = bf.bf_plan(H, W, SS, SR, EPS, t_mode="fixed", t_fixed=T, trunc_rule="trunc",
+                      plane_dtype="fp16", lowp_recheck=0.0)
+    out = bf.bf_execute(plan, torch.from_numpy(f32).cuda())
+    torch.cuda.synchronize()
+    assert bf.bf_get_device_status(plan) == 0
+    info = bf.bf_get_info(plan)
+    o = out.cpu().numpy()
+    assert np.all(np.isfinite(o))
+    assert info.n_rechecked == 0
+    clear = [(i, j) for i, j, ratio in SPOTS if ratio <= -0.005]
+    assert info.n_guarded >= len(clear) >= 2
+    for i, j in clear:
+        assert o[i, j] == f32[i, j]
