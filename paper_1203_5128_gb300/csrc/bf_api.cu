@@ -191,6 +191,7 @@ FwdArgs forward_args(bf_plan_s* p, const float* f, size_t fp, float* out, size_t
     a.sep_cap_terms = p->cap_pairs + 1;
     a.stall_test = p->stall_test;
     a.box_rs = box_running_sums(p->opt, p->R);
+    a.box = p->opt.spatial == BF_SPATIAL_BOX;
     if (p->d_fix) {
         a.fix_list = p->d_fix;
         a.fix_count = p->d_fixcnt;

@@ -138,7 +138,8 @@ bf_status build_state(int n, const bf_plan_t* plans, const float* const* f, floa
     // in the graph, after the batched K1 and K2); the others share the queue
     // (two_pass), and so do images whose fused tall tile covers at least a
     // quarter wave of the GPU (a launch of their own fills it as well as the
-    // queue would, with the faster tall kernel)
+    // queue would, with the faster tall kernel), and box images of the tall
+    // tile's radii (its sliding sums are the form a single execute takes)
     int sms0 = 0;
     if (cudaDeviceGetAttribute(&sms0, cudaDevAttrMultiProcessorCount, st->device) != cudaSuccess)
         return BF_ERR_CUDA;
@@ -151,7 +152,8 @@ bf_status build_state(int n, const bf_plan_t* plans, const float* const* f, floa
         two_pass[i] = (p->d_sep_P && set_tile == 0 && !fwd32t_ok(p->R, 0) && sep32_ok(p->R)) ||
                       (fwd32t_ok(p->R, set_tile) && 4 * tall_ctas >= sms0) ||
                       p->opt.plane_dtype != BF_PLANES_FP32 ||
-                      forward_args(p, f[i], p->W, out[i], p->W).box_rs;   // running sums
+                      forward_args(p, f[i], p->W, out[i], p->W).box_rs ||   // running sums
+                      (p->opt.spatial == BF_SPATIAL_BOX && fwd32t_ok(p->R, set_tile));   // sliding sums
     }
     // ---- tile shape per queued image (autotuned per R, remembered per process)
     std::vector<std::pair<int, int>> shape(n);

@@ -256,13 +256,42 @@ __device__ __forceinline__ void row_item_x2(const Taps2& tp, const float2* src, 
     }
 }
 
-// Row pass of a pair plane into the swizzled hz.  The first NT-multiple of the
+// Box filter (taps 1 inside [-R, R], 0 outside) on NO consecutive outputs
+// of a pair plane: the first output is the FIR sum of its window (the same
+// taps in the same order as row_item_x2), each next one the previous plus
+// the value entering the window minus the value leaving it.  The sliding sum
+// restarts every NO outputs, so an output carries at most 2 (NO - 1)
+// roundings more than the direct sum of its 2R + 1 values.
+template <int NO, int NCH>
+__device__ __forceinline__ void row_item_box_x2(const Taps2& tp, const float2* src, int R,
+                                                float2 (&acc)[NO])
+{
+    constexpr int Rp = 4 * (NCH - 1);
+    float2 s = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int q = 0; q <= Rp; ++q) {       // inputs 2q, 2q + 1 (the last one, 2 Rp + 1, unused)
+        const float4 w = *(const float4*)(src + 2 * q);
+        s = __ffma2_rn(tp.g[2 * q + 8], make_float2(w.x, w.y), s);
+        if (2 * q + 1 <= 2 * Rp) s = __ffma2_rn(tp.g[2 * q + 9], make_float2(w.z, w.w), s);
+    }
+    acc[0] = s;
+#pragma unroll
+    for (int i = 1; i < NO; ++i) {
+        s = __fadd2_rn(s, src[i + Rp + R]);
+        s = __ffma2_rn(make_float2(-1.f, -1.f), src[i - 1 + Rp - R], s);
+        acc[i] = s;
+    }
+}
+
+// Row pass of a pair plane into the swizzled hz (kBox: the sliding box sums
+// of row_item_box_x2 for radius R).  The first NT-multiple of the
 // RH x 4 items (halo row r, 8-column block) runs as 8-output items, the
 // eight rows of a quarter-warp consecutive; the rest runs, when it fits one
 // round that way, as twice as many 4-output items (the last round then takes
 // half as long), else as 8-output items too.
-template <int TH, int TW, int NCH, int NT>
-__device__ __forceinline__ void row_pass_x2(const Taps2& tp, const float2* cs, float2* hz, int tid)
+template <int TH, int TW, int NCH, int NT, bool kBox = false>
+__device__ __forceinline__ void row_pass_x2(const Taps2& tp, const float2* cs, float2* hz, int tid,
+                                            int R = 0)
 {
     using G = TallGeo<TH, TW, NCH>;
     constexpr int kItems = G::RH * (TW / 8);
@@ -274,7 +303,8 @@ __device__ __forceinline__ void row_pass_x2(const Taps2& tp, const float2* cs, f
     for (int it = tid; it < kMain; it += NT) {
         const int cb = (it >> 3) & 3, r = (it & 7) + ((it >> 5) << 3);
         float2 acc[8];
-        row_item_x2<8, NCH>(tp, cs + r * G::CSp + cb * 8, acc);
+        if constexpr (kBox) row_item_box_x2<8, NCH>(tp, cs + r * G::CSp + cb * 8, R, acc);
+        else row_item_x2<8, NCH>(tp, cs + r * G::CSp + cb * 8, acc);
 #pragma unroll
         for (int q = 0; q < 4; ++q)
             *(float4*)(hz + hz_at(r, cb * 8 + 2 * q)) =
@@ -283,7 +313,8 @@ __device__ __forceinline__ void row_pass_x2(const Taps2& tp, const float2* cs, f
     if (kHalf > 0 && tid < kHalf) {
         const int r = kFull / 4 + (tid & 7) + ((tid >> 6) << 3), x0 = ((tid >> 3) & 7) * 4;
         float2 acc[4];
-        row_item_x2<4, NCH>(tp, cs + r * G::CSp + x0, acc);
+        if constexpr (kBox) row_item_box_x2<4, NCH>(tp, cs + r * G::CSp + x0, R, acc);
+        else row_item_x2<4, NCH>(tp, cs + r * G::CSp + x0, acc);
 #pragma unroll
         for (int q = 0; q < 2; ++q)
             *(float4*)(hz + hz_at(r, x0 + 2 * q)) =

@@ -174,7 +174,7 @@ __device__ __forceinline__ void fwd32_body(const FwdArgs& a, int by, int bx, flo
 // during it, their independent SFU / FMA chains filling the issue slots the
 // packed multiply-adds leave free; the denominator's demodulation then takes
 // cos / sin of pair k at its own outputs from the same phase function.
-template <int TH, int TW, int NCH>
+template <int TH, int TW, int NCH, bool kBox>
 __device__ __forceinline__ void fwd32t_body(const FwdArgs& a, const fir32::Taps& tp,
                                             const fir32::Taps2& tp2, int by, int bx, char* sm)
 {
@@ -250,24 +250,49 @@ __device__ __forceinline__ void fwd32t_body(const FwdArgs& a, const fir32::Taps&
     // column pass of the row-filtered pair with job(m), m = ch * PPS + u, run
     // between its input steps
     auto col_pass_with = [&](float2 (&acc)[CO], auto&& job) {
+        if constexpr (kBox) {
+            // box: the FIR sum for the first output, sliding sums for the rest
+            // (as the row pass's row_item_box_x2)
+            float2 sb = make_float2(0.f, 0.f);
 #pragma unroll
-        for (int i = 0; i < CO; ++i) acc[i] = make_float2(0.f, 0.f);
+            for (int ch = 0; ch < NS; ++ch) {
 #pragma unroll
-        for (int ch = 0; ch < NS; ++ch) {
-            float2 v[8];
+                for (int j = 0; j < 8; ++j)
+                    if (ch * 8 + j <= 2 * Rp)
+                        sb = __ffma2_rn(tp2.g[ch * 8 + j + 8],
+                                        hz[fir32::hz_at(rb * CO + ch * 8 + j, o)], sb);
 #pragma unroll
-            for (int j = 0; j < 8; ++j) v[j] = hz[fir32::hz_at(rb * CO + ch * 8 + j, o)];
-            fir32::fir_x2<CO, 8, Rp>(acc, tp2, ch * 8, v);
+                for (int u = 0; u < PPS; ++u)
+                    if (ch * PPS + u < PS::ITERS) job(ch * PPS + u);
+            }
+            acc[0] = sb;
 #pragma unroll
-            for (int u = 0; u < PPS; ++u)
-                if (ch * PPS + u < PS::ITERS) job(ch * PPS + u);
+            for (int i = 1; i < CO; ++i) {
+                sb = __fadd2_rn(sb, hz[fir32::hz_at(rb * CO + i + Rp + R, o)]);
+                sb = __ffma2_rn(make_float2(-1.f, -1.f), hz[fir32::hz_at(rb * CO + i - 1 + Rp - R, o)],
+                                sb);
+                acc[i] = sb;
+            }
+        } else {
+#pragma unroll
+            for (int i = 0; i < CO; ++i) acc[i] = make_float2(0.f, 0.f);
+#pragma unroll
+            for (int ch = 0; ch < NS; ++ch) {
+                float2 v[8];
+#pragma unroll
+                for (int j = 0; j < 8; ++j) v[j] = hz[fir32::hz_at(rb * CO + ch * 8 + j, o)];
+                fir32::fir_x2<CO, 8, Rp>(acc, tp2, ch * 8, v);
+#pragma unroll
+                for (int u = 0; u < PPS; ++u)
+                    if (ch * PPS + u < PS::ITERS) job(ch * PPS + u);
+            }
         }
     };
 
     for (int k = 0; k < K; ++k) {
         // denominator pair (c, s); cos / sin at my outputs kept for both
         // demodulations, read before cs is rescaled
-        fir32::row_pass_x2<TH, TW, NCH, NT>(tp2, cs, hz, tid);
+        fir32::row_pass_x2<TH, TW, NCH, NT, kBox>(tp2, cs, hz, tid, R);
         float2 cc[CO];
 #pragma unroll
         for (int i = 0; i < CO; ++i) cc[i] = cs[(rb * CO + i + Rp) * G::CSp + o + Rp];
@@ -288,7 +313,7 @@ __device__ __forceinline__ void fwd32t_body(const FwdArgs& a, const fir32::Taps&
         }
         __syncthreads();
         // numerator pair (f'c, f's), already formed
-        fir32::row_pass_x2<TH, TW, NCH, NT>(tp2, cs, hz, tid);
+        fir32::row_pass_x2<TH, TW, NCH, NT, kBox>(tp2, cs, hz, tid, R);
         __syncthreads();
         {
             // during the column pass: the phases of pair k + 1 into cs
@@ -332,34 +357,38 @@ __device__ __forceinline__ void fwd32t_body(const FwdArgs& a, const fir32::Taps&
     }
 }
 
-template <int TH, int TW, int NCH>
+template <int TH, int TW, int NCH, bool kBox>
 __global__ void __launch_bounds__(TH * TW / 8, 1)
 k_fwd32t(FwdArgs a, const __grid_constant__ fir32::Taps tp, const __grid_constant__ fir32::Taps2 tp2)
 {
     extern __shared__ __align__(16) char smc[];
-    fwd32t_body<TH, TW, NCH>(a, tp, tp2, blockIdx.y * TH, blockIdx.x * TW, smc);
+    fwd32t_body<TH, TW, NCH, kBox>(a, tp, tp2, blockIdx.y * TH, blockIdx.x * TW, smc);
 }
 
-template <int TH, int NCH>
+template <int TH, int NCH, bool kBox>
 cudaError_t launch_tall_th(const FwdArgs& a, const fir32::Taps& tp, const fir32::Taps2& tp2,
                            cudaStream_t s)
 {
     constexpr size_t smem = fir32::TallGeo<TH, 32, NCH>::bytes;
-    cudaError_t e = cudaFuncSetAttribute(k_fwd32t<TH, 32, NCH>,
+    cudaError_t e = cudaFuncSetAttribute(k_fwd32t<TH, 32, NCH, kBox>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     dim3 grid((a.W + 31) / 32, (a.H + TH - 1) / TH);
-    k_fwd32t<TH, 32, NCH><<<grid, TH * 4, smem, s>>>(a, tp, tp2);
+    k_fwd32t<TH, 32, NCH, kBox><<<grid, TH * 4, smem, s>>>(a, tp, tp2);
     return cudaGetLastError();
 }
 
-// 128-row tiles, or 64-row tiles where the T-tiles are 64 (not 128) rows high.
+// 128-row tiles, or 64-row tiles where the T-tiles are 64 (not 128) rows
+// high; the box spatial filter takes the sliding-sum form.
 template <int NCH>
 cudaError_t launch_tall(const FwdArgs& a, const fir32::Taps& tp, const fir32::Taps2& tp2,
                         cudaStream_t s)
 {
-    if (fwd32t_rows(a.set_tile) == 64) return launch_tall_th<64, NCH>(a, tp, tp2, s);
-    return launch_tall_th<128, NCH>(a, tp, tp2, s);
+    const bool th64 = fwd32t_rows(a.set_tile) == 64;
+    if (a.box) return th64 ? launch_tall_th<64, NCH, true>(a, tp, tp2, s)
+                           : launch_tall_th<128, NCH, true>(a, tp, tp2, s);
+    return th64 ? launch_tall_th<64, NCH, false>(a, tp, tp2, s)
+                : launch_tall_th<128, NCH, false>(a, tp, tp2, s);
 }
 
 template <int TH, int TW>

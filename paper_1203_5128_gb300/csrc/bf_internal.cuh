@@ -183,6 +183,7 @@ struct FwdArgs {
     float fix_kappa = 0.f;
     int stall_test = 0;     // K3-tc: run out a bounded wait (bf_test_stall)
     int box_rs = 0;         // box spatial filter: FP32 planes by exact running sums
+    int box = 0;            // box spatial filter (unit taps): sliding sums in the tall FIR
 };
 
 // FP32 recheck of listed outputs of a 16-bit-plane forward: the direct sum
