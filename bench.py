@@ -229,6 +229,17 @@ def fp32_instr_per_px(N, M, R):
     return F * (8 * taps + 7) + z * (4 * taps + 2) + 3
 
 
+def box_instr_per_px(N, M):
+    """Algorithmic FP32 instructions per output pixel of the box filter by
+    running sums (Sec. 4: O(1) per pixel whatever the radius): per pair 4
+    planes x 2 passes x 2 (the value entering and the value leaving the
+    window), 2 plane products, 4 demodulation FMAs and 1 weight (23); per
+    zero term 2 planes x 2 x 2 + 2 (10); plus 3 for the normalisation."""
+    F = (N - M) - N // 2
+    z = 1 if N % 2 == 0 else 0
+    return F * 23 + z * 10 + 3
+
+
 def yvv_instr_per_px(N, M):
     """Algorithmic FP32 instructions per output pixel of the recursive
     filter: per plane a third-order recursion each way along rows and along
@@ -486,8 +497,11 @@ def box_leg(bf, timed, steps, world, max_over_ranks):
             work = per_set_total(lambda n, m: fir_flops_per_px(n, m, info.R), info, N_, M_, 128)
             entry["tensor_frac"] = work / (k3 * 1e-3) / 1e12 / peak_tc
         else:
-            work = per_set_total(lambda n, m: fp32_instr_per_px(n, m, info.R), info, N_, M_, 128)
+            # the FP32 box runs sliding sums (O(1) per plane value), so its
+            # algorithmic count is the running-sum form's, not the FIR's
+            work = per_set_total(box_instr_per_px, info, N_, M_, 128)
             entry["fp32_frac"] = work / (k3 * 1e-3) / 1e12 / peak_tinst
+            entry["fp32_frac_of"] = "running-sum instructions per pixel (23 per pair)"
         plan.close()
         res[name] = entry
     res["peak_source"] = pk_kind

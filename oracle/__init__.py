@@ -28,7 +28,18 @@ the direct form; the paper prints no value for it.  The box mode
 (``spatial="box"``: the constant spatial filter of radius sigma_s that
 Sec. 4 uses against BF2) is pinned by ``tests/test_oracle_box.py`` against
 running sums of an integral image, pure-Python brute force and the direct
-form.
+form.  The raised-polynomial kernel (``resolve(..., kernel="poly")``,
+``poly_direct``: Sec. 1.3, eqs. (RP), (RPconv)) is pinned by
+``tests/test_oracle_poly.py``: its Gaussian limit, positivity and
+monotonicity from N0 on, the binomial expansion in exact arithmetic, the
+region ranges and the direct sum by pure-Python brute force, the constant
+image, the sigma_r -> infinity blur, covariance and shiftability in a
+polynomial basis.  The non-local means (``nlm_direct``, ``nlm_shiftable``:
+Sec. 6, eqs. (NL1), (NL2)) are pinned by ``tests/test_oracle_nlm.py``: the
+one-pixel patch is the bilateral filter, the direct sum equals pure-Python
+brute force (raised cosine and exact Gaussian), the shiftable form equals
+the direct sum, T covers every patch difference, the constant image and
+large sigma_r, transposition.
 """
 from __future__ import annotations
 
