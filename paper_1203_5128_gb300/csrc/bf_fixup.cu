@@ -15,29 +15,35 @@
 // omega_k = omega_0 + k Delta, Delta = 2 / (sqrt(N) sigma_r) (omega_0 = Delta
 // for even N, Delta / 2 for odd N).
 //
-// phi_eps depends on d alone, so one CTA per parameter set first tabulates
-// it on a grid s_j = (j - 1) h, j = 0 .. J, of [0, T] (phi_eps is even and
-// |d| <= T within a window), then every (output, neighbour) pair reads it by
-// 4-point (cubic) Lagrange interpolation, with a first-order correction for
-// the exact tail of d.  The interpolation error is at most |phi''''| h^4
-// (9/16) / 24 <= 0.0234 (omega_max h)^4 (sum_k W_k <= 1), so h = the
-// largest power of two with omega_max h <= 0.054 keeps it under 2e-7; a power
-// of two makes every s_j and s / h exact.  A set whose table does not fit the
-// launch's shared memory (or a |d| beyond T, possible only for fixed T)
-// takes the same value from the sum itself:
+// phi_eps depends on d alone, so every CTA first tabulates it for the sets
+// its share of the list touches: nodes s_j = j h, j = 0 .. J, of [0, T]
+// (phi_eps is even and |d| <= T within a window), each holding phi_eps(s_j)
+// and h phi_eps'(s_j).  A pair (output, neighbour) reads the two nodes
+// around |d| and evaluates the cubic Hermite interpolant between them, with
+// a first-order correction for the exact tail of d.  Its error is at most
+// h^4 max|phi_eps^(4)| / 384 <= (omega_max h)^4 / 384 (sum_k W_k <= 1), so
+// h = the largest power of two with omega_max h <= 0.09 keeps it under
+// 1.8e-7; a power of two makes every s_j and |d| / h exact, and the node
+// index comes from the bits of a float (no conversion instructions).  A set whose nodes do not fit the launch's shared memory
+// (or a |d| beyond T, possible only for fixed T) takes the same value from
+// the sum itself:
 //   phi_eps(d) = Re[e^{i omega_0 d} P(z)],  P(z) = sum_k W_k z^k,  z = e^{i Delta d},
 // by Horner's rule on the unit circle, with d as an exact head + tail
 // (two-sum), Delta d as a head + tail product and one accurate sincosf
-// (|Delta d| <= pi whenever |d| <= T).  Table entries come from the same
-// routine.  num and den are compensated sums (two-sum per term), then the
-// denominator guard and the normalisation of the forward.
+// (|Delta d| <= pi whenever |d| <= T).  The nodes come from the same
+// routine, phi_eps' from the same Horner pass with the weights W_k omega_k.
+// num and den are compensated sums, then the denominator guard and the
+// normalisation of the forward.
 //
-// One warp per listed pixel (lanes over the (2R+1)^2 window).  A one-CTA
-// scan turns the per-set list lengths into offsets, and a persistent grid
-// splits all listed pixels evenly (the lists are very uneven: pixels unlike
-// their window gather at edges and in noisy tiles); every CTA builds the
-// tables of the sets its share touches.  List lengths are read on the
-// device, so the launch needs no host synchronisation.
+// One warp per listed pixel (lanes over the (2R+1)^2 window).  The window's
+// positions are a per-CTA table of (g(dy) g(dx), pointer offset dy pitch +
+// dx): an output whose window lies inside the image reads its neighbours
+// through it with no bounds test; an output near the border walks the window
+// with the bounds tests.  A one-CTA scan turns the per-set list lengths into
+// offsets, and a persistent grid splits all listed pixels evenly (the lists
+// are very uneven: pixels unlike their window gather at edges and in noisy
+// tiles).  List lengths are read on the device, so the launch needs no host
+// synchronisation.
 #include <math.h>
 
 #include "bf_internal.cuh"
@@ -47,7 +53,7 @@ namespace {
 
 constexpr int kWarps = 8;
 constexpr int kThreads = 32 * kWarps;
-constexpr float kTabStep = 0.054f;   // omega_max * h bound of the table grid
+constexpr float kTabStep = 0.09f;    // omega_max * h bound of the node grid
 
 // s + c += v, c collecting the rounding error of each addition (two-sum)
 __device__ __forceinline__ void comp_add(float& s, float& c, float v)
@@ -65,8 +71,8 @@ struct SetConst {
 };
 
 // phi_eps(dh + dl) from its pair sum (Horner on the unit circle); wk in
-// shared memory.
-__device__ __forceinline__ float phi_sum(float dh, float dl, const SetConst& c, const float* wk)
+// shared memory.  Out of line: only sets whose nodes do not fit take it.
+__device__ __noinline__ float phi_sum(float dh, float dl, const SetConst& c, const float* wk)
 {
     const float ph = c.Dhi * dh;
     float pe = fmaf(c.Dhi, dh, -ph);
@@ -86,6 +92,66 @@ __device__ __forceinline__ float phi_sum(float dh, float dl, const SetConst& c, 
         pr_ = tr;
     }
     return fmaf(mr, pr_, -mi * pi_) + c.w0;
+}
+
+// phi_eps(d) and phi_eps'(d) for a d exact in FP32 (the node grid): the
+// same Horner pass with the weights W_k and W_k omega_k
+__device__ __forceinline__ void phi_node(float d, const SetConst& c, const float* wk,
+                                         const float* wkw, float& phi, float& dphi)
+{
+    const float ph = c.Dhi * d;
+    float pe = fmaf(c.Dhi, d, -ph);
+    pe = fmaf(c.Dlo, d, pe);
+    float ang = ph + pe;
+    if (c.odd) ang *= 0.5f;
+    float s1, c1;
+    sincosf(ang, &s1, &c1);
+    const float mr = c1, mi = s1;
+    const float zr = c.odd ? fmaf(c1, c1, -s1 * s1) : c1;
+    const float zi = c.odd ? 2.f * c1 * s1 : s1;
+    float pr_ = 0.f, pi_ = 0.f, qr = 0.f, qi = 0.f;
+    for (int k = c.K - 1; k >= 0; --k) {
+        const float tr = fmaf(-pi_, zi, fmaf(pr_, zr, wk[k]));
+        pi_ = fmaf(pr_, zi, pi_ * zr);
+        pr_ = tr;
+        const float ur = fmaf(-qi, zi, fmaf(qr, zr, wkw[k]));
+        qi = fmaf(qr, zi, qi * zr);
+        qr = ur;
+    }
+    phi = fmaf(mr, pr_, -mi * pi_) + c.w0;
+    dphi = -fmaf(mr, qi, mi * qr);                     // -Im[e^{i omega_0 d} Q(z)]
+}
+
+// The node grid of one set, read by every pair of its outputs.
+struct Nodes {
+    const float2* n;        // (phi_eps(j h), h phi_eps'(j h)), j = 0 .. J
+    float inv_h;
+    int J;
+    bool use;
+};
+
+// phi_eps(dh + dl), |dl| <= ulp(dh) / 2: the Hermite cubic between the nodes
+// around |dh| plus dl times its slope, else the direct sum
+__device__ __forceinline__ float phi_eps(float dh, float dl, const Nodes& t, const SetConst& sc,
+                                         const float* wk)
+{
+    // j0 = round(|dh| / h - 1/2) by the bits of 1.5 2^23 + (|dh| / h - 1/2), where
+    // the FP32 spacing is 1: floor(|dh| / h), or one less when |dh| / h is a
+    // whole number (then u = 1 and the cubic gives the next node exactly)
+    const float ad = fabsf(dh);
+    const float tq = fmaf(ad, t.inv_h, -0.5f) + 12582912.0f;
+    const int j0 = __float_as_int(tq) - 0x4B400000;
+    if (t.use && j0 < t.J) {
+        const float u = fmaf(ad, t.inv_h, 12582912.0f - tq);   // |dh| / h - j0, exact
+        const float2 n0 = t.n[j0], n1 = t.n[j0 + 1];
+        const float dp = n1.x - n0.x;
+        const float c2 = fmaf(3.f, dp, -fmaf(2.f, n0.y, n1.y));
+        const float c3 = fmaf(-2.f, dp, n0.y + n1.y);
+        const float v = fmaf(u, fmaf(u, fmaf(u, c3, c2), n0.y), n0.x);
+        const float slope = fmaf(u, fmaf(3.f * u, c3, 2.f * c2), n0.y) * t.inv_h;
+        return fmaf(slope, dh < 0.f ? -dl : dl, v);
+    }
+    return phi_sum(dh, dl, sc, wk);
 }
 
 // Exclusive prefix sum of the per-set list lengths of the launch's sets, in
@@ -114,55 +180,73 @@ __global__ void __launch_bounds__(1024) k_fixup_scan(const unsigned* __restrict_
     if (threadIdx.x == 1023) scan[n_sets] = part[1023];
 }
 
-// Per-set constants and the phi_eps table of `set` (whole CTA).
-__device__ void load_set(const FixArgs& a, int set, float* wk, float* tab, SetConst& sc, float& h,
-                         float& inv_h, int& J, bool& use_tab)
+// Per-set constants and the node grid of `set` (whole CTA).
+__device__ void load_set(const FixArgs& a, int set, float* wk, float* wkw, float2* nodes,
+                         int n_nodes, SetConst& sc, Nodes& t)
 {
     const SetHdr hd = a.hdr[set];
     const Pair* pr = a.pairs + (size_t)set * a.cap_pairs;
-    __syncthreads();                                   // the previous set's table is done with
-    for (int k = threadIdx.x; k < hd.F; k += kThreads) wk[k] = pr[k].W;
-    const double scale = sqrt((double)hd.N) * a.sigma_r;
-    const double D = 2.0 / scale;
-    sc.Dhi = (float)D;
-    sc.Dlo = (float)(D - (double)sc.Dhi);
+    __syncthreads();                                   // the previous set's nodes are done with
+    for (int k = threadIdx.x; k < hd.F; k += kThreads) {
+        const Pair q = pr[k];
+        wk[k] = q.W;
+        wkw[k] = q.W * q.om_hi;
+    }
+    // Delta = 2 / (sqrt(N) sigma_r) as FP32 head + tail: the first pair's
+    // frequency is Delta (even N) or Delta / 2 (odd N), stored the same way
+    // (all in FP32: these are per-set constants every thread forms)
     sc.odd = hd.N & 1;
     sc.w0 = hd.z ? hd.w0 : 0.f;
     sc.K = hd.F;
-    // the table grid: omega_max of the set's largest kept pair
-    const double om_max = hd.F > 0 ? (sc.odd ? 2.0 * hd.F - 1.0 : 2.0 * hd.F) / scale : 0.0;
-    h = inv_h = 0.f;
-    J = 0;
-    use_tab = false;
-    if (om_max > 0.0) {
-        const int e = (int)floor(log2((double)kTabStep / om_max));
-        h = ldexpf(1.0f, e);
-        inv_h = ldexpf(1.0f, -e);
-        const double jd = (double)hd.T / (double)h + 4.0;
-        if (jd <= (double)a.ntab) {
-            J = (int)jd;
-            use_tab = true;
+    t.n = nodes;
+    t.inv_h = 0.f;
+    t.J = 0;
+    t.use = false;
+    sc.Dhi = sc.Dlo = 0.f;
+    float h = 0.f;
+    if (hd.F > 0) {
+        const Pair first = pr[0];
+        const float two = sc.odd ? 2.f : 1.f;
+        sc.Dhi = first.om_hi * two;
+        sc.Dlo = first.om_lo * two;
+        // the node grid: h = the largest power of two with omega_max h <= kTabStep,
+        // omega_max the set's largest kept frequency
+        const float x = kTabStep / pr[hd.F - 1].om_hi;
+        const int e = ((__float_as_int(x) >> 23) & 255) - 127;          // floor(log2 x)
+        if (e > -120 && e < 120) {
+            h = __int_as_float((e + 127) << 23);
+            t.inv_h = __int_as_float((127 - e) << 23);
+            const float jd = ceilf(hd.T * t.inv_h) + 1.f;   // nodes 0 .. J cover [0, T + h]
+            if (jd < (float)n_nodes) {
+                t.J = (int)jd;
+                t.use = true;
+            }
         }
     }
     __syncthreads();
-    if (use_tab) {
-        for (int j = threadIdx.x; j <= J; j += kThreads)
-            tab[j] = phi_sum((float)(j - 1) * h, 0.f, sc, wk);
+    if (t.use) {
+        for (int j = threadIdx.x; j <= t.J; j += kThreads) {
+            float v, dv;
+            phi_node((float)j * h, sc, wk, wkw, v, dv);
+            nodes[j] = make_float2(v, dv * h);
+        }
         __syncthreads();
     }
 }
 
 // Persistent: CTA b takes items [b T / G, (b + 1) T / G) of the launch's
 // T listed outputs in set order (scan gives each set's first item), builds
-// the table of every set it meets and hands the items to its warps.
-__global__ void __launch_bounds__(kThreads, 4) k_fixup(FixArgs a, const unsigned* __restrict__ scan,
+// the nodes of every set it meets and hands the items to its warps.
+__global__ void __launch_bounds__(kThreads, 3) k_fixup(FixArgs a, const unsigned* __restrict__ scan,
                                                     int n_sets)
 {
     extern __shared__ float sm[];
-    const int RW = 2 * a.R + 1;
-    float* taps = sm;                                  // 2R+1
-    float* wk = taps + ((RW + 3) & ~3);                // cap_pairs
-    float* tab = wk + ((a.cap_pairs + 3) & ~3);        // phi_eps((j - 1) h), j <= J
+    const int RW = 2 * a.R + 1, RW2 = RW * RW;
+    float* taps = sm;                                              // 2R+1
+    float* wk = taps + ((RW + 3) & ~3);                            // cap_pairs
+    float* wkw = wk + ((a.cap_pairs + 3) & ~3);                    // cap_pairs
+    float2* win = reinterpret_cast<float2*>(wkw + ((a.cap_pairs + 3) & ~3));   // RW^2
+    float2* nodes = win + ((RW2 + 1) & ~1);                        // ntab / 2
 
     const unsigned total = scan[n_sets];
     const unsigned b0 = (unsigned)(((unsigned long long)blockIdx.x * total) / gridDim.x);
@@ -170,6 +254,12 @@ __global__ void __launch_bounds__(kThreads, 4) k_fixup(FixArgs a, const unsigned
     if (b0 >= b1) return;                              // whole CTA
     for (int i = threadIdx.x; i < RW; i += kThreads) taps[i] = a.taps[i];
     __syncthreads();
+    // window positions: spatial weight and pointer offset from the centre
+    for (int p = threadIdx.x; p < RW2; p += kThreads) {
+        const int iy = p / RW, ix = p - iy * RW;
+        const int off = (iy - a.R) * (int)a.f_pitch + (ix - a.R);
+        win[p] = make_float2(taps[iy] * taps[ix], __int_as_float(off));
+    }
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const float full = full_mass(taps, a.R);
 
@@ -186,70 +276,68 @@ __global__ void __launch_bounds__(kThreads, 4) k_fixup(FixArgs a, const unsigned
         if (s0 >= s1) continue;                        // (uniform) empty set
         const int set = a.set0 + si;
         SetConst sc;
-        float h, inv_h;
-        int J;
-        bool use_tab;
-        load_set(a, set, wk, tab, sc, h, inv_h, J, use_tab);
+        Nodes t;
+        load_set(a, set, wk, wkw, nodes, a.ntab / 2, sc, t);   // (its first barrier covers win)
         const unsigned* list = a.list + (size_t)set * a.fix_cap;
         for (unsigned g = s0 + warp; g < s1; g += kWarps) {
             const unsigned idx = list[g - scan[si]];
             const int gy = (int)(idx / (unsigned)a.W), gx = (int)(idx - (unsigned)gy * a.W);
-            const float fx = a.f[(size_t)gy * a.f_pitch + gx];
+            const float* fc = a.f + (size_t)gy * a.f_pitch + gx;
+            const float fx = *fc;
             float ns = 0.f, nc = 0.f, ds = 0.f, dc = 0.f;
             constexpr int kU = 8;                      // window loads in flight per lane
-            // window position of this lane's first neighbour, then advanced by
-            // 32 positions per step without a division
-            int iy = lane / RW, ix = lane - (lane / RW) * RW;
-            for (int p0 = lane; p0 < RW * RW; p0 += 32 * kU) {
-                float fv[kU], gv[kU];                  // neighbour value, spatial weight
+            // one neighbour: d = fy - fx = dh + dl exactly, its weight g phi_eps(d)
+            auto pair = [&](float fy, float gw, float& dsum, float& nsum) {
+                const float dh = fy - fx;
+                const float tt = dh - fy;
+                const float dl = (fy - (dh - tt)) + (-fx - tt);
+                const float wgt = gw * phi_eps(dh, dl, t, sc, wk);
+                dsum += wgt;
+                nsum = fmaf(wgt, dh, nsum);
+            };
+            const bool inside = gy >= a.R && gy + a.R < a.H && gx >= a.R && gx + a.R < a.W;
+            if (inside) {
+                // the window lies in the image: positions from the table, no tests
+                for (int p0 = lane; p0 < RW2; p0 += 32 * kU) {
+                    float fv[kU], gv[kU];
 #pragma unroll
-                for (int u = 0; u < kU; ++u) {
-                    const int y = gy + iy - a.R, x = gx + ix - a.R;
-                    const bool in = p0 + 32 * u < RW * RW && y >= 0 && y < a.H && x >= 0 &&
-                                    x < a.W;
-                    fv[u] = in ? __ldg(a.f + (size_t)y * a.f_pitch + x)
-                               : __int_as_float(0x7fc00000);
-                    gv[u] = taps[min(iy, RW - 1)] * taps[min(ix, RW - 1)];
-                    ix += 32;
-                    while (ix >= RW) {
-                        ix -= RW;
-                        ++iy;
+                    for (int u = 0; u < kU; ++u) {
+                        const int p = p0 + 32 * u;
+                        const float2 e = win[min(p, RW2 - 1)];
+                        fv[u] = __ldg(fc + __float_as_int(e.y));
+                        gv[u] = p < RW2 ? e.x : 0.f;
                     }
-                }
-                // plain sums over the kU terms of this step, compensated across steps
-                float dsum = 0.f, nsum = 0.f;
+                    // plain sums over the kU terms of this step, compensated across steps
+                    float dsum = 0.f, nsum = 0.f;
 #pragma unroll
-                for (int u = 0; u < kU; ++u) {
-                    if (isnan(fv[u])) continue;
-                    const float fy = fv[u];
-                    // d = fy - fx = dh + dl exactly
-                    const float dh = fy - fx;
-                    const float t = dh - fy;
-                    const float dl = (fy - (dh - t)) + (-fx - t);
-                    const float q = fabsf(dh) * inv_h;
-                    const int j0 = (int)q;
-                    float phi;
-                    if (use_tab && j0 + 3 <= J) {
-                        const float uu = q - (float)j0;
-                        const float v0 = tab[j0], v1 = tab[j0 + 1], v2 = tab[j0 + 2],
-                                    v3 = tab[j0 + 3];
-                        const float um1 = uu - 1.f, um2 = uu - 2.f, up1 = uu + 1.f;
-                        const float wa = -uu * um1 * um2 * (1.f / 6.f);
-                        const float wb = up1 * um1 * um2 * 0.5f;
-                        const float wc = -up1 * uu * um2 * 0.5f;
-                        const float wd = up1 * uu * um1 * (1.f / 6.f);
-                        phi = fmaf(wa, v0, fmaf(wb, v1, fmaf(wc, v2, wd * v3)));
-                        // first-order term of the tail: phi'(s) ~ (v2 - v1) / h
-                        phi = fmaf((v2 - v1) * inv_h, dh < 0.f ? -dl : dl, phi);
-                    } else {
-                        phi = phi_sum(dh, dl, sc, wk);
-                    }
-                    const float wgt = gv[u] * phi;
-                    dsum += wgt;
-                    nsum = fmaf(wgt, dh, nsum);
+                    for (int u = 0; u < kU; ++u) pair(fv[u], gv[u], dsum, nsum);
+                    comp_add(ds, dc, dsum);
+                    comp_add(ns, nc, nsum);
                 }
-                comp_add(ds, dc, dsum);
-                comp_add(ns, nc, nsum);
+            } else {
+                // near the border: walk the window, neighbours outside the image skipped
+                int iy = lane / RW, ix = lane - (lane / RW) * RW;
+                for (int p0 = lane; p0 < RW2; p0 += 32 * kU) {
+                    float fv[kU], gv[kU];
+#pragma unroll
+                    for (int u = 0; u < kU; ++u) {
+                        const int y = gy + iy - a.R, x = gx + ix - a.R;
+                        const bool in = p0 + 32 * u < RW2 && y >= 0 && y < a.H && x >= 0 &&
+                                        x < a.W;
+                        fv[u] = in ? __ldg(a.f + (size_t)y * a.f_pitch + x) : fx;
+                        gv[u] = in ? taps[min(iy, RW - 1)] * taps[min(ix, RW - 1)] : 0.f;
+                        ix += 32;
+                        while (ix >= RW) {
+                            ix -= RW;
+                            ++iy;
+                        }
+                    }
+                    float dsum = 0.f, nsum = 0.f;
+#pragma unroll
+                    for (int u = 0; u < kU; ++u) pair(fv[u], gv[u], dsum, nsum);
+                    comp_add(ds, dc, dsum);
+                    comp_add(ns, nc, nsum);
+                }
             }
 #pragma unroll
             for (int off = 16; off > 0; off >>= 1) {
@@ -284,35 +372,44 @@ __global__ void __launch_bounds__(kThreads, 4) k_fixup(FixArgs a, const unsigned
 size_t fixup_smem_bytes(int R, int cap_pairs, int ntab)
 {
     const size_t RW = 2 * (size_t)R + 1;
-    return sizeof(float) * (((RW + 3) & ~(size_t)3) + (((size_t)cap_pairs + 3) & ~(size_t)3) +
-                            (size_t)ntab + 1);
+    return sizeof(float) * (((RW + 3) & ~(size_t)3) + 2 * (((size_t)cap_pairs + 3) & ~(size_t)3) +
+                            2 * ((RW * RW + 1) & ~(size_t)1) + (size_t)ntab);
 }
 
-// Table entries for a plan: enough for every set whose N fits n_cap (T <=
-// pi sigma_r sqrt(N) / 2 and omega_max <= sqrt(N) / sigma_r, with the step
-// at least 0.027 / omega_max, give J <= (pi / 2) N / 0.027 + 4 < 59 N + 4),
-// but at most kMaxTab entries; sets with a
-// longer table take the direct sums.  48 KB: four CTAs (32 warps) per SM.
+// Node-grid floats for a plan (two per node): enough for every set whose N
+// fits n_cap (T <= pi sigma_r sqrt(N) / 2 and omega_max <= sqrt(N) /
+// sigma_r, with the step at least 0.045 / omega_max, give J <= (pi / 2) N /
+// 0.045 + 2 < 35 N + 2 nodes), but at most kMaxTab floats; sets with more
+// nodes take the direct sums.  With the window table (19 KB at R = 24) and
+// 48 KB of nodes, three CTAs (24 warps) fit an SM.
 int fixup_table_entries(int n_cap)
 {
     constexpr long long kMaxTab = 12288;
-    long long want = 59ll * n_cap + 8;
+    long long want = 2 * (35ll * n_cap + 4);
     return (int)(want < kMaxTab ? want : kMaxTab);
 }
 
 cudaError_t launch_fixup(const FixArgs& a, int n_sets, cudaStream_t s)
 {
     const size_t smem = fixup_smem_bytes(a.R, a.cap_pairs, a.ntab);
-    if (smem > 227 * 1024 || n_sets < 1 || !a.scan) return cudaErrorInvalidValue;
+    if (smem > 227 * 1024 || n_sets < 1 || !a.scan || a.R > 63) return cudaErrorInvalidValue;
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(k_fixup, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)smem);
         if (e != cudaSuccess) return e;
     }
-    k_fixup_scan<<<1, 1024, 0, s>>>(a.count, a.set0, n_sets, a.scan);
-    cudaError_t e = cudaGetLastError();
+    // one wave of the CTAs that fit (the grid splits the listed outputs evenly)
+    int dev = 0, sms = 0, per = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_fixup, kThreads, smem);
     if (e != cudaSuccess) return e;
-    k_fixup<<<a.n_ctas, kThreads, smem, s>>>(a, a.scan, n_sets);
+    const int n_ctas = max(1, sms * max(per, 1));
+    k_fixup_scan<<<1, 1024, 0, s>>>(a.count, a.set0, n_sets, a.scan);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_fixup<<<n_ctas, kThreads, smem, s>>>(a, a.scan, n_sets);
     return cudaGetLastError();
 }
 
