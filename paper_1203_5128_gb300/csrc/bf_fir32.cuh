@@ -300,6 +300,21 @@ __device__ __forceinline__ void row_pass_x2(const Taps2& tp, const float2* cs, f
     constexpr int kMain = kSplit ? kFull : kItems;
     constexpr int kHalf = kSplit ? 2 * (kItems - kFull) : 0;
     static_assert(kItems % 32 == 0 && kFull % 32 == 0, "row pass items");
+    if constexpr (kBox) {
+        // box: 16-output items (two per row), so that each window's direct
+        // sum serves 16 sliding outputs; the eight rows of a quarter-warp
+        // consecutive, as below
+        for (int it = tid; it < 2 * G::RH; it += NT) {
+            const int hb = (it >> 3) & 1, r = (it & 7) + ((it >> 4) << 3);
+            float2 acc[16];
+            row_item_box_x2<16, NCH>(tp, cs + r * G::CSp + hb * 16, R, acc);
+#pragma unroll
+            for (int q = 0; q < 8; ++q)
+                *(float4*)(hz + hz_at(r, hb * 16 + 2 * q)) =
+                    make_float4(acc[2 * q].x, acc[2 * q].y, acc[2 * q + 1].x, acc[2 * q + 1].y);
+        }
+        return;
+    }
     for (int it = tid; it < kMain; it += NT) {
         const int cb = (it >> 3) & 3, r = (it & 7) + ((it >> 5) << 3);
         float2 acc[8];
