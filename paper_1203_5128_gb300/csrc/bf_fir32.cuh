@@ -283,8 +283,33 @@ __device__ __forceinline__ void row_item_box_x2(const Taps2& tp, const float2* s
     }
 }
 
+// Box row run of NO outputs (even) stored into hz as they are formed: the
+// window's FIR sum for the first output, then sliding sums as in
+// row_item_box_x2 (no accumulator array, so the run can be a whole row).
+template <int NO, int NCH>
+__device__ __forceinline__ void row_run_box_x2(const Taps2& tp, const float2* src, int R,
+                                               float2* hz, int r, int x0)
+{
+    constexpr int Rp = 4 * (NCH - 1);
+    float2 s = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int q = 0; q <= Rp; ++q) {
+        const float4 w = *(const float4*)(src + 2 * q);
+        s = __ffma2_rn(tp.g[2 * q + 8], make_float2(w.x, w.y), s);
+        if (2 * q + 1 <= 2 * Rp) s = __ffma2_rn(tp.g[2 * q + 9], make_float2(w.z, w.w), s);
+    }
+    float2 prev = s;
+#pragma unroll
+    for (int i = 1; i < NO; ++i) {
+        s = __fadd2_rn(s, src[i + Rp + R]);
+        s = __ffma2_rn(make_float2(-1.f, -1.f), src[i - 1 + Rp - R], s);
+        if (i & 1) *(float4*)(hz + hz_at(r, x0 + i - 1)) = make_float4(prev.x, prev.y, s.x, s.y);
+        prev = s;
+    }
+}
+
 // Row pass of a pair plane into the swizzled hz (kBox: the sliding box sums
-// of row_item_box_x2 for radius R).  The first NT-multiple of the
+// of row_run_box_x2 for radius R, one run per row).  The first NT-multiple of the
 // RH x 4 items (halo row r, 8-column block) runs as 8-output items, the
 // eight rows of a quarter-warp consecutive; the rest runs, when it fits one
 // round that way, as twice as many 4-output items (the last round then takes
@@ -301,18 +326,9 @@ __device__ __forceinline__ void row_pass_x2(const Taps2& tp, const float2* cs, f
     constexpr int kHalf = kSplit ? 2 * (kItems - kFull) : 0;
     static_assert(kItems % 32 == 0 && kFull % 32 == 0, "row pass items");
     if constexpr (kBox) {
-        // box: 16-output items (two per row), so that each window's direct
-        // sum serves 16 sliding outputs; the eight rows of a quarter-warp
-        // consecutive, as below
-        for (int it = tid; it < 2 * G::RH; it += NT) {
-            const int hb = (it >> 3) & 1, r = (it & 7) + ((it >> 4) << 3);
-            float2 acc[16];
-            row_item_box_x2<16, NCH>(tp, cs + r * G::CSp + hb * 16, R, acc);
-#pragma unroll
-            for (int q = 0; q < 8; ++q)
-                *(float4*)(hz + hz_at(r, hb * 16 + 2 * q)) =
-                    make_float4(acc[2 * q].x, acc[2 * q].y, acc[2 * q + 1].x, acc[2 * q + 1].y);
-        }
+        // box: one run per row, so that each window's direct sum serves the
+        // row's 32 sliding outputs (consecutive threads on consecutive rows)
+        for (int r = tid; r < G::RH; r += NT) row_run_box_x2<TW, NCH>(tp, cs + r * G::CSp, R, hz, r, 0);
         return;
     }
     for (int it = tid; it < kMain; it += NT) {
