@@ -100,7 +100,7 @@ void free_plan(bf_plan_s* p)
             if (p->ev[i]) cudaEventDestroy(p->ev[i]);
         free(p->ev);
     }
-    for (int i = 0; i < 4; ++i)
+    for (int i = 0; i < 5; ++i)
         if (p->hst[i]) cudaStreamDestroy(p->hst[i]);
     if (p->hev) {
         for (int i = 0; i < p->n_hev; ++i)
@@ -333,9 +333,13 @@ cudaError_t enqueue_poly(bf_plan_s* p, const float* f, size_t fp, float* out, si
 // sooner: band b is filtered once the chunk holding its last halo row is on
 // the device, while later chunks are copied in and earlier bands out.  Two
 // compute streams alternate so that one band's last wave of tiles overlaps
-// the next band's first.  Same kernels, same arithmetic per pixel as
-// bf_execute.
-constexpr int kHostBandRows = 512;
+// the next band's first.  A band's FP32 recheck (16-bit planes) runs on a
+// fifth stream of the lowest priority, the compute streams at the highest:
+// pending forward tiles take the SMs first and the rechecks fill the gaps;
+// a band is copied out after its recheck.  Same kernels, same arithmetic
+// per pixel as bf_execute.  (4096^2, tuned: 1024-row bands 2.49 ms per call,
+// 768 2.51, 512 2.54; with the rechecks on the compute streams 2.71 at 512.)
+constexpr int kHostBandRows = 1024;
 constexpr long long kMinSpinLimit = 1ll << 16;   // polls; see bf_plan
 
 int host_band_rows(const bf_plan_s* p)
@@ -372,10 +376,17 @@ bf_status execute_host_banded(bf_plan_s* p, const float* fh, float* oh, cudaStre
     }
     const int nb = (int)cut.size() - 1;
     const int nc = (H + C - 1) / C;                  // copy chunks of one T-tile row
-    const int need = 3 + nc + nb;
+    const int need = 3 + nc + 2 * nb;
     if (!p->hst[0]) {
-        for (int i = 0; i < 4; ++i)
-            BF_CUDA(cudaStreamCreateWithFlags(&p->hst[i], cudaStreamNonBlocking));
+        // the compute streams at the highest priority, the recheck stream at
+        // the lowest: pending forward tiles take the SMs first, and the
+        // rechecks run in the gaps (a band's last partial wave)
+        int least = 0, greatest = 0;
+        BF_CUDA(cudaDeviceGetStreamPriorityRange(&least, &greatest));
+        for (int i = 0; i < 5; ++i) {
+            const int prio = (i == 1 || i == 2) ? greatest : (i == 4 ? least : 0);
+            BF_CUDA(cudaStreamCreateWithPriority(&p->hst[i], cudaStreamNonBlocking, prio));
+        }
     }
     if (p->n_hev < need) {
         if (p->hev) {
@@ -393,9 +404,10 @@ bf_status execute_host_banded(bf_plan_s* p, const float* fh, float* oh, cudaStre
     cudaEvent_t ev_fork = p->hev[0], ev_clear = p->hev[1], ev_join = p->hev[2];
     cudaEvent_t* ev_in = p->hev + 3;                 // per chunk
     cudaEvent_t* ev_done = p->hev + 3 + nc;          // per band
-    cudaStream_t s_in = p->hst[0], s_out = p->hst[3];
+    cudaEvent_t* ev_fwd = p->hev + 3 + nc + nb;      // per band: forward done
+    cudaStream_t s_in = p->hst[0], s_out = p->hst[3], s_fix = p->hst[4];
     BF_CUDA(cudaEventRecord(ev_fork, s));
-    for (int i = 0; i < 4; ++i) BF_CUDA(cudaStreamWaitEvent(p->hst[i], ev_fork, 0));
+    for (int i = 0; i < 5; ++i) BF_CUDA(cudaStreamWaitEvent(p->hst[i], ev_fork, 0));
     // T words and the guard counter start at zero for every band's kernels
     BF_CUDA(cudaMemsetAsync(p->d_T, 0, sizeof(unsigned) * p->n_sets, p->hst[1]));
     BF_CUDA(cudaMemsetAsync(p->d_nguard, 0, sizeof(unsigned long long), p->hst[1]));
@@ -435,13 +447,17 @@ bf_status execute_host_banded(bf_plan_s* p, const float* fh, float* oh, cudaStre
         fa.y_tiles = (rows + th - 1) / th;
         BF_CUDA(launch_fwd_tc(fa, p->opt.plane_dtype == BF_PLANES_BF16, p->opt.spin_limit,
                               p->d_status, cs));
-        if (p->d_fix) {                          // the band's own sets
+        if (p->d_fix) {                          // the band's own sets, on the recheck stream
+            BF_CUDA(cudaEventRecord(ev_fwd[b], cs));
+            BF_CUDA(cudaStreamWaitEvent(s_fix, ev_fwd[b], 0));
             FixArgs xa = fixup_args(p, fa);
             xa.set0 = r0 / C * p->sets_x;
-            xa.scan = p->d_fixscan + xa.set0 + b;    // bands run concurrently: own offsets
-            BF_CUDA(launch_fixup(xa, (rows + C - 1) / C * p->sets_x, cs));
+            xa.scan = p->d_fixscan + xa.set0 + b;    // own offsets per band
+            BF_CUDA(launch_fixup(xa, (rows + C - 1) / C * p->sets_x, s_fix));
+            BF_CUDA(cudaEventRecord(ev_done[b], s_fix));
+        } else {
+            BF_CUDA(cudaEventRecord(ev_done[b], cs));
         }
-        BF_CUDA(cudaEventRecord(ev_done[b], cs));
         BF_CUDA(cudaStreamWaitEvent(s_out, ev_done[b], 0));
         BF_CUDA(cudaMemcpyAsync(oh + (size_t)r0 * W, p->d_hout + (size_t)r0 * W,
                                 (size_t)rows * row_bytes, cudaMemcpyDeviceToHost, s_out));

@@ -56,7 +56,7 @@ struct bf_plan_s {
                              // concurrent row bands take disjoint ranges)
     unsigned fix_cap;        // 16-bit recheck: list slots per set
     int n_fixcnt;
-    cudaStream_t hst[4];     // banded host path: copy in, compute (2), copy out
+    cudaStream_t hst[5];     // banded host path: copy in, compute (2), copy out, recheck
     cudaEvent_t* hev;        // banded host path: fork, clear, join, then per band in / done
     int n_hev;
 };

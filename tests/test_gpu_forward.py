@@ -153,13 +153,15 @@ def test_host_entry_point_matches_device(bf):
     assert torch.equal(dev, host)
 
 
-@pytest.mark.parametrize("H,W,planes,tile", [(1100, 300, "fp16", 128), (1536, 256, "bf16", 256),
+@pytest.mark.parametrize("H,W,planes,tile", [(2300, 200, "fp16", 128), (3072, 128, "bf16", 256),
                                              (2048, 160, "fp16", 128)])
 def test_host_entry_point_banded(bf, H, W, planes, tile):
     """Per-tile T with 16-bit planes: the host entry point copies, filters
-    and copies back in row bands that overlap one another; its output, the
-    T, N, M of every T-tile and the guard count equal one bf_execute on the
-    device (ragged last band, two band sizes)."""
+    and copies back in row bands that overlap one another (images of at
+    least two bands), with the FP32 recheck of each band on a stream of its
+    own; its output, the T, N, M of every T-tile and the guard count equal
+    one bf_execute on the device (ragged last band, 128- and 256-row
+    T-tiles)."""
     import torch
     f = synth.g8(H, W, seed=H + W)
     plan = bf.bf_plan(H, W, 8.0, 10.0, 0.01, t_mode="tile", t_tile=tile, plane_dtype=planes)
