@@ -224,7 +224,6 @@ FixArgs fixup_args(bf_plan_s* p, const FwdArgs& fa)
     x.fix_cap = fa.fix_cap;
     x.n_guarded = p->d_nguard;
     x.set0 = 0;
-    x.n_ctas = 4 * 152;                 // four 48 KB-table CTAs per SM
     x.ntab = fixup_table_entries(p->n_cap);
     x.scan = p->d_fixscan;
     return x;

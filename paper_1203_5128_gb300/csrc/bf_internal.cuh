@@ -206,8 +206,7 @@ struct FixArgs {
     unsigned fix_cap;
     unsigned long long* n_guarded;
     int set0;               // first set of the launch
-    int n_ctas;             // persistent grid
-    int ntab;               // phi_eps table entries a CTA holds
+    int ntab;               // floats of phi_eps nodes a CTA holds (two per node)
     unsigned* scan;         // n_sets + 1 offsets (scratch)
 };
 int fixup_table_entries(int n_cap);
