@@ -199,8 +199,9 @@ bf_status bf_execute(bf_plan_t plan, const float *f_dev, size_t f_pitch,
  * allocated by the first call on a plan and reused.  Plans with exact T per
  * T-tile and 16-bit planes run in row bands (copy in, filter, copy out of
  * different bands overlap, on streams and events the plan creates on this
- * first call and owns); the result is the same, bit for bit, as copying the
- * whole image and calling bf_execute. */
+ * first call and owns: the compute streams at the device's highest stream
+ * priority, the FP32 recheck's at its lowest); the result is the same, bit
+ * for bit, as copying the whole image and calling bf_execute. */
 bf_status bf_execute_host(bf_plan_t plan, const float *f_host, float *out_host,
                           void *stream);
 
