@@ -173,7 +173,18 @@ typedef struct bf_options {
                             Takes FP32 planes, the FIR filter, t_mode FIXED or
                             GLOBAL and the cosine kernel, and no bf_backward or
                             bf_execute_batch (else BF_ERR_NOT_SUPPORTED).     */
-    int reserved[4];     /* must be zero                                          */
+    float fp32_recheck;  /* FP32 planes with R > 24 (the two-pass FIR, the small
+                            FIR tiles, the box's integer running sums): an
+                            output whose denominator is below fp32_recheck x
+                            its clipped spatial mass is recomputed by the same
+                            FP32 direct sum as lowp_recheck's.  Over a large
+                            window the terms of eqs. (f1), (f2) are of the
+                            order of the window's mass and cancel down to den,
+                            so at a pixel unlike most of its window the FP32
+                            rounding of the planes is amplified by mass / den.
+                            Default 0.05; 0 turns the recheck off; must lie in
+                            [0, 1); plans with R > 63 take no recheck.       */
+    int reserved[3];     /* must be zero                                          */
 } bf_options;
 
 /* Fills *opt with the defaults listed above. */
@@ -239,7 +250,7 @@ typedef struct bf_info {
     unsigned device_status; /* BF_DEV_* bits (not cleared)                      */
     int filter, plane_dtype, t_mode;
     int tile_h, tile_w;     /* output tile of the forward kernel                */
-    long long n_rechecked;  /* outputs recomputed in FP32 (lowp_recheck)        */
+    long long n_rechecked;  /* outputs recomputed in FP32 (lowp_recheck, fp32_recheck) */
 } bf_info;
 
 /* Synchronises the plan's last stream and reports the parameters the last

@@ -46,7 +46,8 @@ class bf_options(ctypes.Structure):
         ("lowp_recheck", ctypes.c_float),
         ("range_kernel", ctypes.c_int),
         ("patch_mask", ctypes.c_int),
-        ("reserved", ctypes.c_int * 4),
+        ("fp32_recheck", ctypes.c_float),
+        ("reserved", ctypes.c_int * 3),
     ]
 
 

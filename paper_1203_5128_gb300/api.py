@@ -42,7 +42,7 @@ def bf_status_string(code: int) -> str:
 def bf_options_init(**kw) -> nat.bf_options:
     """bf_options with the library defaults, then keyword overrides
     (t_mode, t_fixed, value_range, trunc_rule, filter, plane_dtype, n_max,
-    t_tile, spin_limit, spatial, lowp_recheck, range_kernel, patch_mask;
+    t_tile, spin_limit, spatial, lowp_recheck, range_kernel, patch_mask, fp32_recheck;
     enum fields accept their lower-case names)."""
     o = nat.bf_options()
     nat.lib().bf_options_init(ctypes.byref(o))

@@ -196,7 +196,8 @@ FwdArgs forward_args(bf_plan_s* p, const float* f, size_t fp, float* out, size_t
         a.fix_list = p->d_fix;
         a.fix_count = p->d_fixcnt;
         a.fix_cap = p->fix_cap;
-        a.fix_kappa = p->opt.lowp_recheck;
+        a.fix_kappa = p->opt.plane_dtype == BF_PLANES_FP32 ? p->opt.fp32_recheck
+                                                           : p->opt.lowp_recheck;
     }
     return a;
 }
@@ -493,6 +494,7 @@ void bf_options_init(bf_options* o)
     o->spin_limit = 1ll << 22;
     o->spatial = BF_SPATIAL_GAUSS;
     o->lowp_recheck = 0.05f;
+    o->fp32_recheck = 0.05f;
 }
 
 const char* bf_status_string(bf_status s)
@@ -528,6 +530,7 @@ bf_status bf_plan(int H, int W, double sigma_s, double sigma_r, double eps, cons
     if (!(o.value_range > 0.f) || !isfinite(o.value_range)) return BF_ERR_INVALID_ARG;
     if (o.n_max < 1) return BF_ERR_INVALID_ARG;
     if (!(o.lowp_recheck >= 0.f) || !(o.lowp_recheck < 1.f)) return BF_ERR_INVALID_ARG;
+    if (!(o.fp32_recheck >= 0.f) || !(o.fp32_recheck < 1.f)) return BF_ERR_INVALID_ARG;
     if (o.n_max > 4096) return BF_ERR_NOT_SUPPORTED;
     for (int i = 0; i < (int)(sizeof(o.reserved) / sizeof(o.reserved[0])); ++i)
         if (o.reserved[i]) return BF_ERR_INVALID_ARG;
@@ -688,7 +691,13 @@ bf_status bf_plan(int H, int W, double sigma_s, double sigma_r, double eps, cons
         float T = o.t_fixed;
         ok &= cudaMemcpy(p->d_T, &T, sizeof(float), cudaMemcpyHostToDevice) == cudaSuccess;
     }
-    if (ok && o.plane_dtype != BF_PLANES_FP32 && o.lowp_recheck > 0.f) {
+    // FP32 planes take the recheck where the window is large (R > 24: the
+    // two-pass FIR, the small FIR tiles, the box's running sums) and the
+    // recheck kernel's window fits (R <= 63); the FIR of the cosine kernel
+    // only (not the recursive filter, the polynomial or the patch kernels)
+    const bool fp32_fix = o.plane_dtype == BF_PLANES_FP32 && o.fp32_recheck > 0.f && R > 24 &&
+                          R <= 63 && o.filter == BF_FILTER_FIR && !poly && !nlm;
+    if (ok && ((o.plane_dtype != BF_PLANES_FP32 && o.lowp_recheck > 0.f) || fp32_fix)) {
         // the recheck lists (a slot per pixel of each set's region, so they
         // cannot overflow) and one list length per set
         p->n_fixcnt = p->n_sets;
@@ -789,7 +798,7 @@ bf_status bf_execute(bf_plan_t p, const float* f, size_t fp, float* out, size_t 
                               p->opt.plane_dtype == BF_PLANES_BF16, p->opt.spin_limit,
                               p->d_status, s));
     BF_CUDA(mark(p, 3, s));
-    if (p->d_fix && p->opt.filter != BF_FILTER_YVV && p->opt.plane_dtype != BF_PLANES_FP32)
+    if (p->d_fix)          // 16-bit planes, or FP32 planes with R > 24: the FP32 recheck
         BF_CUDA(launch_fixup(fixup_args(p, forward_args(p, f, fp, out, op)), p->n_sets, s));
     BF_CUDA(mark(p, 4, s));
     if (p->timing && p->n_timed < kMaxTimed) ++p->n_timed;
@@ -1012,6 +1021,8 @@ cudaError_t launch_backward(bf_plan_s* p, const float* f, const float* gout, flo
     fa.den_out = s_den;
     fa.den_pitch = p->W;
     fa.n_guarded = s_cnt;
+    fa.fix_list = nullptr;     // the adjoint's forward is the FP32-plane filter itself, no recheck
+    fa.fix_count = nullptr;
     cudaError_t e = launch_fwd32(fa, s);
     if (e != cudaSuccess) return e;
     BwdArgs ba;

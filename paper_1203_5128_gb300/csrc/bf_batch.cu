@@ -353,6 +353,8 @@ bf_status build_state(int n, const bf_plan_t* plans, const float* const* f, floa
             cudaStream_t ss = side[j % kSide];
             if (p->opt.plane_dtype == BF_PLANES_FP32) {
                 e = launch_fwd32(fimg[own[j]], ss);
+                if (e == cudaSuccess && p->d_fix)      // R > 24: the FP32 recheck
+                    e = launch_fixup(fixup_args(p, fimg[own[j]]), p->n_sets, ss);
             } else {
                 e = launch_fwd_tc(fimg[own[j]], p->opt.plane_dtype == BF_PLANES_BF16,
                                   p->opt.spin_limit, p->d_status, ss);
@@ -366,6 +368,10 @@ bf_status build_state(int n, const bf_plan_t* plans, const float* const* f, floa
                                         reinterpret_cast<const int4*>(d + oI[c]),
                                         (int)items[c].size(),
                                         reinterpret_cast<unsigned*>(d + oH) + c, ctas[c], cs);
+        // the FP32 recheck of queued images with large windows, after the queue
+        for (int i = 0; i < n && e == cudaSuccess; ++i)
+            if (!two_pass[i] && plans[i]->d_fix)
+                e = launch_fixup(fixup_args(plans[i], fimg[i]), plans[i]->n_sets, cs);
         for (int k = 0; k < kSide && e == cudaSuccess; ++k) {
             e = cudaEventRecord(join_ev[k], side[k]);
             if (e == cudaSuccess) e = cudaStreamWaitEvent(cs, join_ev[k], 0);

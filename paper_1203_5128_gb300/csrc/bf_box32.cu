@@ -184,13 +184,18 @@ __global__ void __launch_bounds__(4 * TH) k_box32(FwdArgs a)
     }
 
     if (gx < a.W) {
+        const float kap = a.fix_list ? a.fix_kappa : -INFINITY;   // FP32 recheck list
+        uint32_t listed = 0u;
 #pragma unroll
         for (int i = 0; i < 8; ++i) {
             const int gy = by + cg * 8 + i;
             if (gy >= a.H) continue;
             const float rmass = clipped_mass(a.taps, R, gy, a.H, full);
             float v;
-            if (den[i] > kGuard * rmass * cmass) {
+            if (den[i] < kap * rmass * cmass) {
+                listed |= 1u << i;
+                v = a.f[(size_t)gy * a.f_pitch + gx];
+            } else if (den[i] > kGuard * rmass * cmass) {
                 v = fmaf(__fdiv_rn(num[i], den[i]), c0, c0);
             } else {
                 v = a.f[(size_t)gy * a.f_pitch + gx];
@@ -198,6 +203,12 @@ __global__ void __launch_bounds__(4 * TH) k_box32(FwdArgs a)
             }
             a.out[(size_t)gy * a.out_pitch + gx] = v;
             if (a.den_out) a.den_out[(size_t)gy * a.den_pitch + gx] = den[i];
+        }
+        while (listed) {
+            const int i = __ffs(listed) - 1;
+            listed &= listed - 1u;
+            a.fix_list[(size_t)set * a.fix_cap + atomicAdd(a.fix_count + set, 1u)] =
+                (unsigned)(by + cg * 8 + i) * (unsigned)a.W + (unsigned)gx;
         }
     }
 }

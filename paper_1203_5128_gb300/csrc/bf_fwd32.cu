@@ -137,15 +137,23 @@ __device__ __forceinline__ void fwd32_body(const FwdArgs& a, int by, int bx, flo
         __syncthreads();
     }
 
-    // normalise (eq. (f1) over eq. (f2)) with the guard, write out
+    // normalise (eq. (f1) over eq. (f2)) with the guard, write out; outputs
+    // whose den is under fix_kappa of their mass are listed for the FP32
+    // recheck (large windows: the FP32 rounding of the planes is amplified by
+    // mass / den there), which writes them
     if (gx < a.W) {
+        const float kap = a.fix_list ? a.fix_kappa : -INFINITY;
+        uint32_t listed = 0u;
 #pragma unroll
         for (int i = 0; i < 8; ++i) {
             const int gy = by + rb * 8 + i;
             if (gy >= a.H) continue;
             const float rmass = clipped_mass(a.taps, R, gy, a.H, full);
             float v;
-            if (den[i] > kGuard * rmass * cmass) {
+            if (den[i] < kap * rmass * cmass) {
+                listed |= 1u << i;
+                v = a.f[(size_t)gy * a.f_pitch + gx];
+            } else if (den[i] > kGuard * rmass * cmass) {
                 v = __fdiv_rn(num[i], den[i]) + a.c0;
             } else {
                 v = a.f[(size_t)gy * a.f_pitch + gx];
@@ -153,6 +161,12 @@ __device__ __forceinline__ void fwd32_body(const FwdArgs& a, int by, int bx, flo
             }
             a.out[(size_t)gy * a.out_pitch + gx] = v;
             if (a.den_out) a.den_out[(size_t)gy * a.den_pitch + gx] = den[i];
+        }
+        while (listed) {
+            const int i = __ffs(listed) - 1;
+            listed &= listed - 1u;
+            a.fix_list[(size_t)set * a.fix_cap + atomicAdd(a.fix_count + set, 1u)] =
+                (unsigned)(by + rb * 8 + i) * (unsigned)a.W + (unsigned)gx;
         }
     }
 }
@@ -553,6 +567,9 @@ cudaError_t launch_fwd32(const FwdArgs& a, cudaStream_t s)
         sa.n_guarded = a.n_guarded;
         sa.den_out = a.den_out;
         sa.den_pitch = a.den_pitch;
+        sa.fix_list = a.fix_list;
+        sa.fix_count = a.fix_count;
+        sa.fix_kappa = a.fix_kappa;
         return launch_sep32(sa, a.sep_cap_terms, s);
     }
     if (a.h_taps && fwd32t_ok(a.R, a.set_tile)) {

@@ -265,6 +265,9 @@ struct SepArgs {
     unsigned long long* n_guarded;
     float* den_out;
     size_t den_pitch;
+    unsigned* fix_list = nullptr;   // FP32 recheck list of the one set (null: off)
+    unsigned* fix_count = nullptr;
+    float fix_kappa = 0.f;
 };
 bool sep32_ok(int R);
 int sep32_width(int W);

@@ -285,7 +285,11 @@ __global__ void k_sep_final(SepArgs a)
             const float rmass = clipped_mass(a.taps, R, y, a.H, full);
             const float2 nd = a.nd[(size_t)y * a.W + x];
             den = nd.y;
-            if (nd.y > kGuard * rmass * cmass) {
+            if (a.fix_list && nd.y < a.fix_kappa * rmass * cmass) {
+                // den a small part of the mass: the FP32 recheck writes it
+                v = fv;
+                a.fix_list[atomicAdd(a.fix_count, 1u)] = (unsigned)y * (unsigned)a.W + (unsigned)x;
+            } else if (nd.y > kGuard * rmass * cmass) {
                 v = __fdiv_rn(nd.x, nd.y) + a.c0;
             } else {
                 v = fv;

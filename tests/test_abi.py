@@ -54,7 +54,7 @@ def test_options_defaults(lib):
     assert o.t_mode == nat.BF_T_GLOBAL and o.value_range == 255.0
     assert o.trunc_rule == nat.BF_RULE_ALG2 and o.n_max == 4096 and o.t_tile == 64
     assert o.plane_dtype == nat.BF_PLANES_FP32 and o.spatial == nat.BF_SPATIAL_GAUSS
-    assert abs(o.lowp_recheck - 0.05) < 1e-7
+    assert abs(o.lowp_recheck - 0.05) < 1e-7 and abs(o.fp32_recheck - 0.05) < 1e-7
     # the struct has the size the header gives it (reserved words included)
     assert ctypes.sizeof(nat.bf_options) == 4 * 8 + 8 + 4 + 4 + 4 * 6
 
@@ -84,6 +84,8 @@ def test_plan_rejects_bad_options(lib):
                              ("n_max", 0, nat.BF_ERR_INVALID_ARG),
                              ("lowp_recheck", -0.1, nat.BF_ERR_INVALID_ARG),
                              ("lowp_recheck", 1.0, nat.BF_ERR_INVALID_ARG),
+                             ("fp32_recheck", -0.1, nat.BF_ERR_INVALID_ARG),
+                             ("fp32_recheck", 1.0, nat.BF_ERR_INVALID_ARG),
                              ("n_max", 100000, nat.BF_ERR_NOT_SUPPORTED)]:
         o = nat.bf_options()
         lib.bf_options_init(ctypes.byref(o))
@@ -95,7 +97,7 @@ def test_plan_rejects_bad_options(lib):
     o.t_tile = 48                              # must be a multiple of 64
     assert lib.bf_plan(64, 64, 1.0, 10.0, 0.0, ctypes.byref(o), ctypes.byref(h)) == \
         nat.BF_ERR_INVALID_ARG
-    o.reserved[3] = 1
+    o.reserved[2] = 1
     o.t_tile = 64
     assert lib.bf_plan(64, 64, 1.0, 10.0, 0.0, ctypes.byref(o), ctypes.byref(h)) == \
         nat.BF_ERR_INVALID_ARG

@@ -132,7 +132,8 @@ def test_batch_workload_fp16_every_image_vs_oracle(bf):
     takes the radius (R <= 24) and FP32 planes elsewhere: bitwise equal to
     64 bf_execute calls, and every image against the FP64 oracle's direct
     form at sampled pixels (random, corners, borders): FP16 images within
-    0.5 gray level, FP32 images within the FP32 bar."""
+    0.5 gray level, FP32 images (R > 24, with the FP32 recheck) within
+    1e-3."""
     import torch
     specs = synth.batch_specs(64, seed=3)
     plans, fs, nps, kinds = [], [], [], []
@@ -158,7 +159,7 @@ def test_batch_workload_fp16_every_image_vs_oracle(bf):
         d = oracle.direct(nps[k], ss, sr, p, points=(ys, xs))
         err = float(np.max(np.abs(o[ys, xs] - d)))
         worst[kinds[k]] = max(worst[kinds[k]], err)
-        assert err <= (0.5 if kinds[k] == "fp16" else 5e-3), (k, kinds[k], err)
+        assert err <= (0.5 if kinds[k] == "fp16" else 1e-3), (k, kinds[k], err)
     print("64-image batch vs the oracle at sampled pixels: max-abs FP16 %.3g, FP32 %.3g" % (
         worst["fp16"], worst["fp32"]))
     for p_ in plans:

@@ -142,6 +142,8 @@ def test_box_fp32_matches_oracle(bf, case):
     assert np.all(err <= tol_fp32(den, mass, float(p.T.max())))
     if well.any():
         assert np.max(err[well]) <= TOL8
+    if R > 24:       # the FP32 recheck takes den < 5 % of the window: the flat bar
+        assert np.max(err) <= TOL8
 
 
 @pytest.mark.parametrize("planes", ["fp16", "bf16"])

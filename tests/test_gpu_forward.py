@@ -261,17 +261,6 @@ def test_plain_1024_sampled(bf):
 
 
 # ---------------------------------------------------------------- two-pass FIR (R > 24)
-def tol_fp32(den, mass, T):
-    """FP32 bar per pixel: 1e-3 gray levels, plus the FP32 unit roundoff
-    times the pixel's condition number mass / den times T.  The terms of
-    the shiftable sums are of the order of the window's Gaussian mass and
-    cancel down to den, so where den is a small part of the mass (a pixel
-    unlike all of its neighbours, in a large window) the FP32 rounding of
-    the filtered planes is amplified by mass / den (about 200 at worst in
-    these cases, against 1.4 for a typical pixel)."""
-    return 1e-3 + 2.0 ** -24 * (mass / np.maximum(den, 1e-300)) * T
-
-
 def window_mass(sigma_s, R, ys, xs, H, W):
     g = oracle.taps(sigma_s, R)
     def line(i, n):
@@ -288,27 +277,34 @@ def window_mass(sigma_s, R, ys, xs, H, W):
     (70, 1, 10.0, 25.0, 0.01, "global", "alg2"),        # a single column
 ])
 def test_two_pass_matches_oracle(bf, H, W, ss, sr, eps, mode, rule):
-    """Radii beyond the fused tall tile run in two passes through HBM."""
+    """Radii beyond the fused tall tile run in two passes through HBM; the
+    outputs whose den is under 5 % of the window's mass (where the FP32
+    rounding of the planes is amplified by mass / den) are recomputed by the
+    FP32 recheck, so every output holds the flat 1e-3 bar."""
     f = synth.g8(H, W, seed=H + 7 * W)
     plan, out, p = run(bf, f, ss, sr, eps, mode, rule, 64, 255.0, 255.0 if mode == "fixed" else None)
     ref, _, den, _ = oracle.shiftable(f, ss, sr, p, return_parts=True)
     yy, xx = np.mgrid[0:H, 0:W]
     mass = window_mass(ss, p.R, yy.ravel(), xx.ravel(), H, W).reshape(H, W)
-    assert np.all(np.abs(out - ref) <= tol_fp32(den, mass, float(p.T.max())))
-    # and the plain 1e-3 bar everywhere the denominator is not a tiny part of the mass
-    well = den > 0.05 * mass
-    assert np.max(np.abs(out - ref)[well]) <= TOL8
+    err = np.abs(out - ref)
+    info = bf.bf_get_info(plan)
+    print("two-pass %dx%d R=%d: max-abs %.3g gray levels, %d outputs rechecked in FP32" % (
+        H, W, p.R, err.max(), info.n_rechecked))
+    assert np.max(err) <= TOL8
+    # every output whose den is clearly under the threshold was rechecked
+    assert info.n_rechecked >= int(np.sum(den < 0.04 * mass))
 
 
 def test_two_pass_4096_chunks_sampled(bf):
     """4096^2, sigma_s = 10 (R = 30), sigma_r = 10, Algorithm 2: the row-
-    filtered planes of the 78 terms pass through HBM in several chunks."""
+    filtered planes of the 78 terms pass through HBM in several chunks;
+    flat 1e-3 at the sampled outputs (the FP32 recheck takes the ill-
+    conditioned ones)."""
     f = synth.g8(4096, 4096, seed=5)
     plan, out, p = run(bf, f, 10.0, 10.0, 0.01, "global", "alg2", 64)
     ys, xs = sample_points(4096, 4096, 40, seed=17, R=p.R)
     ref, _, den, _ = oracle.direct(f, 10.0, 10.0, p, points=(ys, xs), return_parts=True)
-    mass = window_mass(10.0, p.R, ys, xs, 4096, 4096)
-    assert np.all(np.abs(out[ys, xs] - ref) <= tol_fp32(den, mass, float(p.T.max())))
+    assert np.max(np.abs(out[ys, xs] - ref)) <= TOL8
 
 
 def test_two_pass_backward_and_fused_agree(bf):
@@ -322,7 +318,7 @@ def test_two_pass_backward_and_fused_agree(bf):
     H, W, ss, sr = 160, 200, 9.0, 25.0
     f = synth.g8(H, W, seed=21)
     fd = to_dev(f)
-    plan = bf.bf_plan(H, W, ss, sr, 0.01)
+    plan = bf.bf_plan(H, W, ss, sr, 0.01, fp32_recheck=0.0)     # the two FIR forms alone
     out = bf.bf_execute(plan, fd)
     fused = torch.empty_like(fd)
     code = nat.lib().bf_execute_noalloc(fd.data_ptr(), W, fused.data_ptr(), W, H, W, ss, sr, 0.01,
@@ -331,6 +327,7 @@ def test_two_pass_backward_and_fused_agree(bf):
     assert code == nat.BF_OK
     torch.cuda.synchronize()
     assert np.max(np.abs(out.cpu().numpy() - fused.cpu().numpy())) <= 1e-5
+    assert bf.bf_get_info(plan).n_rechecked == 0      # fp32_recheck = 0: no list
     u = torch.from_numpy(synth.weights_normal((H, W), seed=4)).cuda()
     g = bf.bf_backward(plan, fd, u)
     torch.cuda.synchronize()
