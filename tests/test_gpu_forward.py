@@ -41,10 +41,11 @@ def check_sets(bf, plan, p):
     assert np.array_equal(M, p.M.ravel().astype(np.int32)), (M, p.M.ravel())
 
 
-def run(bf, f_np, ss, sr, eps, mode="global", rule="alg2", tile=64, vr=255.0, t_fixed=None):
+def run(bf, f_np, ss, sr, eps, mode="global", rule="alg2", tile=64, vr=255.0, t_fixed=None,
+        **extra):
     import torch
     H, W = f_np.shape
-    kw = dict(t_mode=mode, trunc_rule=rule, t_tile=tile, value_range=vr)
+    kw = dict(t_mode=mode, trunc_rule=rule, t_tile=tile, value_range=vr, **extra)
     if t_fixed is not None:
         kw["t_fixed"] = t_fixed
     plan = bf.bf_plan(H, W, ss, sr, eps, **kw)
@@ -280,9 +281,11 @@ def test_two_pass_matches_oracle(bf, H, W, ss, sr, eps, mode, rule):
     """Radii beyond the fused tall tile run in two passes through HBM; the
     outputs whose den is under 5 % of the window's mass (where the FP32
     rounding of the planes is amplified by mass / den) are recomputed by the
-    FP32 recheck, so every output holds the flat 1e-3 bar."""
+    FP32 recheck (fp32_recheck = 0.05), so every output holds the flat 1e-3
+    bar."""
     f = synth.g8(H, W, seed=H + 7 * W)
-    plan, out, p = run(bf, f, ss, sr, eps, mode, rule, 64, 255.0, 255.0 if mode == "fixed" else None)
+    plan, out, p = run(bf, f, ss, sr, eps, mode, rule, 64, 255.0, 255.0 if mode == "fixed" else None,
+                       fp32_recheck=0.05)
     ref, _, den, _ = oracle.shiftable(f, ss, sr, p, return_parts=True)
     yy, xx = np.mgrid[0:H, 0:W]
     mass = window_mass(ss, p.R, yy.ravel(), xx.ravel(), H, W).reshape(H, W)
@@ -301,7 +304,7 @@ def test_two_pass_4096_chunks_sampled(bf):
     flat 1e-3 at the sampled outputs (the FP32 recheck takes the ill-
     conditioned ones)."""
     f = synth.g8(4096, 4096, seed=5)
-    plan, out, p = run(bf, f, 10.0, 10.0, 0.01, "global", "alg2", 64)
+    plan, out, p = run(bf, f, 10.0, 10.0, 0.01, "global", "alg2", 64, fp32_recheck=0.05)
     ys, xs = sample_points(4096, 4096, 40, seed=17, R=p.R)
     ref, _, den, _ = oracle.direct(f, 10.0, 10.0, p, points=(ys, xs), return_parts=True)
     assert np.max(np.abs(out[ys, xs] - ref)) <= TOL8
@@ -318,7 +321,7 @@ def test_two_pass_backward_and_fused_agree(bf):
     H, W, ss, sr = 160, 200, 9.0, 25.0
     f = synth.g8(H, W, seed=21)
     fd = to_dev(f)
-    plan = bf.bf_plan(H, W, ss, sr, 0.01, fp32_recheck=0.0)     # the two FIR forms alone
+    plan = bf.bf_plan(H, W, ss, sr, 0.01)     # the two FIR forms alone (no FP32 recheck)
     out = bf.bf_execute(plan, fd)
     fused = torch.empty_like(fd)
     code = nat.lib().bf_execute_noalloc(fd.data_ptr(), W, fused.data_ptr(), W, H, W, ss, sr, 0.01,
@@ -327,7 +330,7 @@ def test_two_pass_backward_and_fused_agree(bf):
     assert code == nat.BF_OK
     torch.cuda.synchronize()
     assert np.max(np.abs(out.cpu().numpy() - fused.cpu().numpy())) <= 1e-5
-    assert bf.bf_get_info(plan).n_rechecked == 0      # fp32_recheck = 0: no list
+    assert bf.bf_get_info(plan).n_rechecked == 0      # the default: no FP32 recheck
     u = torch.from_numpy(synth.weights_normal((H, W), seed=4)).cuda()
     g = bf.bf_backward(plan, fd, u)
     torch.cuda.synchronize()
