@@ -182,13 +182,10 @@ typedef struct bf_options {
                             order of the window's mass and cancel down to den,
                             so at a pixel unlike most of its window the FP32
                             rounding of the planes is amplified by mass / den.
-                            Default 0 (off): with narrow range kernels a large
-                            share of outputs can lie under 5 % of their mass
-                            (a third at sigma_r = 10 on a textured image), and
-                            the recheck then costs several forward passes.
-                            0.05 keeps every output within 1e-3 gray levels of
-                            the exact filter with the same T, N, M; must lie
-                            in [0, 1); plans with R > 63 take no recheck.    */
+                            Default 0.05, which keeps every output within 1e-3
+                            gray levels of the exact filter with the same T,
+                            N, M; 0 turns the recheck off; must lie in [0, 1);
+                            plans with R > 63 take no recheck.               */
     int reserved[3];     /* must be zero                                          */
 } bf_options;
 

@@ -494,7 +494,7 @@ void bf_options_init(bf_options* o)
     o->spin_limit = 1ll << 22;
     o->spatial = BF_SPATIAL_GAUSS;
     o->lowp_recheck = 0.05f;
-    o->fp32_recheck = 0.f;     // opt-in: its cost grows with the share of ill-conditioned outputs
+    o->fp32_recheck = 0.05f;
 }
 
 const char* bf_status_string(bf_status s)

@@ -398,17 +398,18 @@ cudaError_t launch_fixup(const FixArgs& a, int n_sets, cudaStream_t s)
                                              (int)smem);
         if (e != cudaSuccess) return e;
     }
-    // one wave of the CTAs that fit (the grid splits the listed outputs
-    // evenly), but no more CTAs than parameter sets: every CTA builds the
-    // node grids of the sets it meets, so a launch over a few sets (a band of
-    // the host path) with a full wave would build each grid several times
+    // the grid splits the listed outputs evenly; every CTA builds the node
+    // grids of the sets it meets, so a launch over few sets (a band of the
+    // host path) takes one CTA per set, never fewer than one per SM (an
+    // image-wide T is one set with all of the image's listed outputs), and
+    // at most the CTAs that fit at once
     int dev = 0, sms = 0, per = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e == cudaSuccess)
         e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_fixup, kThreads, smem);
     if (e != cudaSuccess) return e;
-    const int n_ctas = max(1, min(sms * max(per, 1), n_sets));
+    const int n_ctas = max(1, min(sms * max(per, 1), max(n_sets, sms)));
     k_fixup_scan<<<1, 1024, 0, s>>>(a.count, a.set0, n_sets, a.scan);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;

@@ -321,7 +321,7 @@ def test_two_pass_backward_and_fused_agree(bf):
     H, W, ss, sr = 160, 200, 9.0, 25.0
     f = synth.g8(H, W, seed=21)
     fd = to_dev(f)
-    plan = bf.bf_plan(H, W, ss, sr, 0.01)     # the two FIR forms alone (no FP32 recheck)
+    plan = bf.bf_plan(H, W, ss, sr, 0.01, fp32_recheck=0.0)     # the two FIR forms alone
     out = bf.bf_execute(plan, fd)
     fused = torch.empty_like(fd)
     code = nat.lib().bf_execute_noalloc(fd.data_ptr(), W, fused.data_ptr(), W, H, W, ss, sr, 0.01,
@@ -330,7 +330,7 @@ def test_two_pass_backward_and_fused_agree(bf):
     assert code == nat.BF_OK
     torch.cuda.synchronize()
     assert np.max(np.abs(out.cpu().numpy() - fused.cpu().numpy())) <= 1e-5
-    assert bf.bf_get_info(plan).n_rechecked == 0      # the default: no FP32 recheck
+    assert bf.bf_get_info(plan).n_rechecked == 0      # fp32_recheck = 0: nothing listed
     u = torch.from_numpy(synth.weights_normal((H, W), seed=4)).cuda()
     g = bf.bf_backward(plan, fd, u)
     torch.cuda.synchronize()
