@@ -173,3 +173,39 @@ def test_batch_rejects_a_plan_named_twice(bf):
     with pytest.raises(bf.BfError):
         bf.bf_execute_batch([p, p], [f, f.clone()])
     p.close()
+
+
+def test_batch_fp32_recheck_large_windows(bf):
+    """FP32 images with R > 24 in a batch: per-tile T (the persistent queue,
+    then the FP32 recheck after it), image-wide T (the two-pass FIR on a
+    launch of its own, then its recheck) and fixed T.  Bitwise equal to
+    separate bf_execute calls, outputs listed for the recheck, and every
+    output within 1e-3 of the FP64 oracle with the same T, N, M."""
+    import torch
+    specs = [(200, 180, 10.0, 8.0, "tile"), (150, 210, 9.0, 8.0, "global"),
+             (120, 160, 11.0, 10.0, "fixed")]
+    plans, fs, nps = [], [], []
+    for k, (H, W, ss, sr, mode) in enumerate(specs):
+        kw = dict(t_mode=mode, t_tile=64)
+        if mode == "fixed":
+            kw["t_fixed"] = 255.0
+        plans.append(bf.bf_plan(H, W, ss, sr, 0.01, **kw))
+        a = synth.g8(H, W, seed=4100 + k)
+        nps.append(a)
+        fs.append(torch.from_numpy(a).cuda())
+    ref = separate(bf, plans, fs)
+    listed = [bf.bf_get_info(p_).n_rechecked for p_ in plans]
+    outs = bf.bf_execute_batch(plans, fs)
+    torch.cuda.synchronize()
+    assert sum(listed) > 0, listed
+    for k, ((H, W, ss, sr, mode), o, r) in enumerate(zip(specs, outs, ref)):
+        o = o.cpu().numpy()
+        assert np.array_equal(o, r), k
+        p = oracle.resolve(nps[k], ss, sr, 0.01, t_mode=mode, t_tile=64,
+                           t_fixed=255.0 if mode == "fixed" else None)
+        err = np.max(np.abs(o - oracle.shiftable(nps[k], ss, sr, p)))
+        print("batch FP32 R=%d %s: %d outputs rechecked, max-abs %.3g" % (
+            int(np.ceil(3 * ss)), mode, listed[k], err))
+        assert err <= 1e-3, (k, err)
+    for p_ in plans:
+        p_.close()
