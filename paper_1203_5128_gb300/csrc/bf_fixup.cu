@@ -16,17 +16,20 @@
 // for even N, Delta / 2 for odd N).
 //
 // phi_eps depends on d alone, so every CTA first tabulates it for the sets
-// its share of the list touches: nodes s_j = j h, j = 0 .. J, of [0, T]
-// (phi_eps is even and |d| <= T within a window), each holding phi_eps(s_j)
-// and h phi_eps'(s_j).  A pair (output, neighbour) reads the two nodes
-// around |d| and evaluates the cubic Hermite interpolant between them, with
-// a first-order correction for the exact tail of d.  Its error is at most
-// h^4 max|phi_eps^(4)| / 384 <= (omega_max h)^4 / 384 (sum_k W_k <= 1), so
-// h = the largest power of two with omega_max h <= 0.09 keeps it under
-// 1.8e-7; a power of two makes every s_j and |d| / h exact, and the node
-// index comes from the bits of a float (no conversion instructions).  A set whose nodes do not fit the launch's shared memory
-// (or a |d| beyond T, possible only for fixed T) takes the same value from
-// the sum itself:
+// its share of the list touches: nodes s_j = j h of [0, T] (phi_eps is even
+// and |d| <= T within a window), each interval [s_j, s_j+1] holding the
+// coefficients of the cubic Hermite interpolant of phi_eps (values and
+// slopes at both ends) in u = |d| / h - j.  A pair (output, neighbour)
+// reads the float4 of the interval around |d| and evaluates the cubic at u,
+// the exact tail of d folded into u.  The interpolant's error is at most
+// h^4 max|phi_eps''''| / 384 <= h^4 S4 / 384, S4 = sum_k W_k omega_k^4 (the
+// kernel's fourth spectral moment, about 3 / sigma_r^4 for the binomial
+// weights, far below omega_max^4), so h = the largest power of two with
+// h^4 S4 <= 384e-8 keeps it under 1e-8; a power of two makes every s_j and
+// |d| / h exact, and the interval index comes from the bits of a float (no
+// conversion instructions).  A set whose table does not fit the launch's
+// shared memory takes phi_eps from the sum itself, and so does an output
+// with a |d| beyond T (possible only for fixed T), which is redone:
 //   phi_eps(d) = Re[e^{i omega_0 d} P(z)],  P(z) = sum_k W_k z^k,  z = e^{i Delta d},
 // by Horner's rule on the unit circle, with d as an exact head + tail
 // (two-sum), Delta d as a head + tail product and one accurate sincosf
@@ -37,9 +40,12 @@
 //
 // One warp per listed pixel (lanes over the (2R+1)^2 window).  The window's
 // positions are a per-CTA table of (g(dy) g(dx), pointer offset dy pitch +
-// dx): an output whose window lies inside the image reads its neighbours
-// through it with no bounds test; an output near the border walks the window
-// with the bounds tests.  A one-CTA scan turns the per-set list lengths into
+// dx) as two arrays, padded with zero weights to whole steps of the
+// lanes' loads (the offsets are read to issue the loads, the weights when
+// the terms are summed, so that no weight waits in a register): an
+// output whose window lies inside the image reads its neighbours through it
+// with no bounds test; an output near the border walks the window with the
+// bounds tests.  A one-CTA scan turns the per-set list lengths into
 // offsets, and a persistent grid splits all listed pixels evenly (the lists
 // are very uneven: pixels unlike their window gather at edges and in noisy
 // tiles).  List lengths are read on the device, so the launch needs no host
@@ -53,7 +59,9 @@ namespace {
 
 constexpr int kWarps = 8;
 constexpr int kThreads = 32 * kWarps;
-constexpr float kTabStep = 0.09f;    // omega_max * h bound of the node grid
+constexpr int kU = 16;               // window loads in flight per lane (inside the image)
+constexpr int kUB = 8;               // the same near the border
+constexpr float kTabTol4 = 3.84e-6f; // 384 * 1e-8: h^4 S4 bound of the node grid
 
 // s + c += v, c collecting the rounding error of each addition (two-sum)
 __device__ __forceinline__ void comp_add(float& s, float& c, float v)
@@ -122,36 +130,40 @@ __device__ __forceinline__ void phi_node(float d, const SetConst& c, const float
     dphi = -fmaf(mr, qi, mi * qr);                     // -Im[e^{i omega_0 d} Q(z)]
 }
 
-// The node grid of one set, read by every pair of its outputs.
-struct Nodes {
-    const float2* n;        // (phi_eps(j h), h phi_eps'(j h)), j = 0 .. J
+// The interpolation table of one set, read by every pair of its outputs.
+struct Tab {
+    const float4* c;        // interval j: (phi_eps(s_j), h phi_eps'(s_j), c2_j, c3_j)
     float inv_h;
-    int J;
-    bool use;
+    unsigned J;             // intervals, j = 0 .. J - 1 (0: no table)
 };
 
-// phi_eps(dh + dl), |dl| <= ulp(dh) / 2: the Hermite cubic between the nodes
-// around |dh| plus dl times its slope, else the direct sum
-__device__ __forceinline__ float phi_eps(float dh, float dl, const Nodes& t, const SetConst& sc,
-                                         const float* wk)
+// phi_eps(dh + dl), |dl| <= ulp(dh) / 2: the cubic of the interval around
+// |dh| at u = |dh| / h - j (exact) plus the tail dl / h (its rounding in u
+// moves phi_eps by at most h max|phi_eps'| 2^-24 < 3e-9).  kGeneral takes
+// the pair sum where the table does not reach (or there is none); else the
+// index is clamped to the table and jmax records it, so that the caller
+// can redo an output where some lane left the table.
+template <bool kGeneral>
+__device__ __forceinline__ float phi_at(float dh, float dl, const Tab& t, const SetConst& sc,
+                                        const float* wk, unsigned& jmax)
 {
-    // j0 = round(|dh| / h - 1/2) by the bits of 1.5 2^23 + (|dh| / h - 1/2), where
+    // j = round(|dh| / h - 1/2) by the bits of 1.5 2^23 + (|dh| / h - 1/2), where
     // the FP32 spacing is 1: floor(|dh| / h), or one less when |dh| / h is a
     // whole number (then u = 1 and the cubic gives the next node exactly)
     const float ad = fabsf(dh);
     const float tq = fmaf(ad, t.inv_h, -0.5f) + 12582912.0f;
-    const int j0 = __float_as_int(tq) - 0x4B400000;
-    if (t.use && j0 < t.J) {
-        const float u = fmaf(ad, t.inv_h, 12582912.0f - tq);   // |dh| / h - j0, exact
-        const float2 n0 = t.n[j0], n1 = t.n[j0 + 1];
-        const float dp = n1.x - n0.x;
-        const float c2 = fmaf(3.f, dp, -fmaf(2.f, n0.y, n1.y));
-        const float c3 = fmaf(-2.f, dp, n0.y + n1.y);
-        const float v = fmaf(u, fmaf(u, fmaf(u, c3, c2), n0.y), n0.x);
-        const float slope = fmaf(u, fmaf(3.f * u, c3, 2.f * c2), n0.y) * t.inv_h;
-        return fmaf(slope, dh < 0.f ? -dl : dl, v);
+    unsigned j = (unsigned)(__float_as_int(tq) - 0x4B400000);
+    if (kGeneral) {
+        if (j >= t.J) return phi_sum(dh, dl, sc, wk);
+    } else {
+        jmax = max(jmax, j);
+        j = min(j, t.J - 1u);
     }
-    return phi_sum(dh, dl, sc, wk);
+    const float4 c = t.c[j];
+    // |d| = |dh| + sign(dh) dl
+    const float sdl = __int_as_float(__float_as_int(dl) ^ (__float_as_int(dh) & (int)0x80000000));
+    const float u = fmaf(sdl, t.inv_h, fmaf(ad, t.inv_h, 12582912.0f - tq));
+    return fmaf(u, fmaf(u, fmaf(u, c.w, c.z), c.y), c.x);
 }
 
 // Exclusive prefix sum of the per-set list lengths of the launch's sets, in
@@ -180,28 +192,38 @@ __global__ void __launch_bounds__(1024) k_fixup_scan(const unsigned* __restrict_
     if (threadIdx.x == 1023) scan[n_sets] = part[1023];
 }
 
-// Per-set constants and the node grid of `set` (whole CTA).
-__device__ void load_set(const FixArgs& a, int set, float* wk, float* wkw, float2* nodes,
-                         int n_nodes, SetConst& sc, Nodes& t)
+// Per-set constants and the interpolation table of `set` (whole CTA);
+// n_tab float4 entries fit.
+__device__ void load_set(const FixArgs& a, int set, float* wk, float* wkw, float4* tab,
+                         int n_tab, SetConst& sc, Tab& t)
 {
     const SetHdr hd = a.hdr[set];
     const Pair* pr = a.pairs + (size_t)set * a.cap_pairs;
-    __syncthreads();                                   // the previous set's nodes are done with
+    __syncthreads();                                   // the previous set's table is done with
     for (int k = threadIdx.x; k < hd.F; k += kThreads) {
         const Pair q = pr[k];
         wk[k] = q.W;
         wkw[k] = q.W * q.om_hi;
     }
+    // S4 = sum_k W_k omega_k^4, by every warp alike (the butterfly leaves the
+    // same sum in every lane)
+    float s4 = 0.f;
+    for (int k = threadIdx.x & 31; k < hd.F; k += 32) {
+        const Pair q = pr[k];
+        const float o2 = q.om_hi * q.om_hi;
+        s4 = fmaf(q.W * o2, o2, s4);
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) s4 += __shfl_xor_sync(0xffffffffu, s4, off);
     // Delta = 2 / (sqrt(N) sigma_r) as FP32 head + tail: the first pair's
     // frequency is Delta (even N) or Delta / 2 (odd N), stored the same way
     // (all in FP32: these are per-set constants every thread forms)
     sc.odd = hd.N & 1;
     sc.w0 = hd.z ? hd.w0 : 0.f;
     sc.K = hd.F;
-    t.n = nodes;
+    t.c = tab;
     t.inv_h = 0.f;
     t.J = 0;
-    t.use = false;
     sc.Dhi = sc.Dlo = 0.f;
     float h = 0.f;
     if (hd.F > 0) {
@@ -209,44 +231,115 @@ __device__ void load_set(const FixArgs& a, int set, float* wk, float* wkw, float
         const float two = sc.odd ? 2.f : 1.f;
         sc.Dhi = first.om_hi * two;
         sc.Dlo = first.om_lo * two;
-        // the node grid: h = the largest power of two with omega_max h <= kTabStep,
-        // omega_max the set's largest kept frequency
-        const float x = kTabStep / pr[hd.F - 1].om_hi;
+        // h = the largest power of two with h^4 S4 <= 384e-8
+        const float x = sqrtf(sqrtf(kTabTol4 / s4));
         const int e = ((__float_as_int(x) >> 23) & 255) - 127;          // floor(log2 x)
-        if (e > -120 && e < 120) {
-            h = __int_as_float((e + 127) << 23);
-            t.inv_h = __int_as_float((127 - e) << 23);
-            const float jd = ceilf(hd.T * t.inv_h) + 1.f;   // nodes 0 .. J cover [0, T + h]
-            if (jd < (float)n_nodes) {
-                t.J = (int)jd;
-                t.use = true;
+        if (s4 > 0.f && e > -120 && e < 120) {
+            const float inv_h = __int_as_float((127 - e) << 23);
+            const float jd = ceilf(hd.T * inv_h) + 1.f;   // intervals 0 .. J - 1 cover [0, T + h]
+            if (jd < (float)n_tab) {                     // entries 0 .. J
+                h = __int_as_float((e + 127) << 23);
+                t.inv_h = inv_h;
+                t.J = (unsigned)jd;
             }
         }
     }
     __syncthreads();
-    if (t.use) {
-        for (int j = threadIdx.x; j <= t.J; j += kThreads) {
+    if (t.J) {
+        // nodes: (phi_eps(s_j), h phi_eps'(s_j)) in the first half of entry j
+        float2* e2 = reinterpret_cast<float2*>(tab);
+        for (int j = threadIdx.x; j <= (int)t.J; j += kThreads) {
             float v, dv;
             phi_node((float)j * h, sc, wk, wkw, v, dv);
-            nodes[j] = make_float2(v, dv * h);
+            e2[2 * j] = make_float2(v, dv * h);
+        }
+        __syncthreads();
+        // the cubic of interval j, v(u) = p0 + u (m0 + u (c2 + u c3)), in the second half
+        for (int j = threadIdx.x; j < (int)t.J; j += kThreads) {
+            const float2 n0 = e2[2 * j], n1 = e2[2 * j + 2];
+            const float dp = n1.x - n0.x;
+            e2[2 * j + 1] = make_float2(fmaf(3.f, dp, -fmaf(2.f, n0.y, n1.y)),
+                                        fmaf(-2.f, dp, n0.y + n1.y));
         }
         __syncthreads();
     }
 }
 
+// The partial sums (per lane, compensated across steps) of num and den of
+// one output over its window.
+template <bool kGeneral>
+__device__ __forceinline__ void window_sums(const FixArgs& a, const int* woff, const float* wwt,
+                                            int RW2p, const float* taps, const Tab& t,
+                                            const SetConst& sc, const float* wk, int gy, int gx,
+                                            float fx, bool inside, float& ns, float& nc,
+                                            float& ds, float& dc, unsigned& jmax)
+{
+    const int lane = threadIdx.x & 31, RW = 2 * a.R + 1, RW2 = RW * RW;
+    ns = nc = ds = dc = 0.f;
+    // one neighbour: d = fy - fx = dh + dl exactly, its weight g phi_eps(d)
+    auto pair = [&](float fy, float gw, float& dsum, float& nsum) {
+        const float dh = fy - fx;
+        const float tt = dh - fy;
+        const float dl = (fy - (dh - tt)) + (-fx - tt);
+        const float wgt = gw * phi_at<kGeneral>(dh, dl, t, sc, wk, jmax);
+        dsum += wgt;
+        nsum = fmaf(wgt, dh, nsum);
+    };
+    if (inside) {
+        // the window lies in the image: positions from the table, no tests
+        const float* fc = a.f + (size_t)gy * a.f_pitch + gx;
+        for (int p0 = lane; p0 < RW2p; p0 += 32 * kU) {
+            float fv[kU];
+#pragma unroll
+            for (int u = 0; u < kU; ++u) fv[u] = __ldg(fc + woff[p0 + 32 * u]);
+            // plain sums over the kU terms of this step, compensated across steps
+            float dsum = 0.f, nsum = 0.f;
+#pragma unroll
+            for (int u = 0; u < kU; ++u) pair(fv[u], wwt[p0 + 32 * u], dsum, nsum);
+            comp_add(ds, dc, dsum);
+            comp_add(ns, nc, nsum);
+        }
+    } else {
+        // near the border: walk the window, neighbours outside the image skipped
+        int iy = lane / RW, ix = lane - (lane / RW) * RW;
+        for (int p0 = lane; p0 < RW2; p0 += 32 * kUB) {
+            float fv[kUB], gv[kUB];
+#pragma unroll
+            for (int u = 0; u < kUB; ++u) {
+                const int y = gy + iy - a.R, x = gx + ix - a.R;
+                const bool in = p0 + 32 * u < RW2 && y >= 0 && y < a.H && x >= 0 && x < a.W;
+                fv[u] = in ? __ldg(a.f + (size_t)y * a.f_pitch + x) : fx;
+                gv[u] = in ? taps[min(iy, RW - 1)] * taps[min(ix, RW - 1)] : 0.f;
+                ix += 32;
+                while (ix >= RW) {
+                    ix -= RW;
+                    ++iy;
+                }
+            }
+            float dsum = 0.f, nsum = 0.f;
+#pragma unroll
+            for (int u = 0; u < kUB; ++u) pair(fv[u], gv[u], dsum, nsum);
+            comp_add(ds, dc, dsum);
+            comp_add(ns, nc, nsum);
+        }
+    }
+}
+
 // Persistent: CTA b takes items [b T / G, (b + 1) T / G) of the launch's
 // T listed outputs in set order (scan gives each set's first item), builds
-// the nodes of every set it meets and hands the items to its warps.
+// the table of every set it meets and hands the items to its warps.
 __global__ void __launch_bounds__(kThreads, 3) k_fixup(FixArgs a, const unsigned* __restrict__ scan,
                                                     int n_sets)
 {
-    extern __shared__ float sm[];
+    extern __shared__ float4 sm4[];
     const int RW = 2 * a.R + 1, RW2 = RW * RW;
-    float* taps = sm;                                              // 2R+1
+    const int RW2p = (RW2 + 32 * kU - 1) / (32 * kU) * (32 * kU);
+    float4* tab = sm4;                                             // ntab / 4
+    int* woff = reinterpret_cast<int*>(tab + a.ntab / 4);          // RW2p
+    float* wwt = reinterpret_cast<float*>(woff + RW2p);            // RW2p
+    float* taps = wwt + RW2p;                                      // 2R+1
     float* wk = taps + ((RW + 3) & ~3);                            // cap_pairs
     float* wkw = wk + ((a.cap_pairs + 3) & ~3);                    // cap_pairs
-    float2* win = reinterpret_cast<float2*>(wkw + ((a.cap_pairs + 3) & ~3));   // RW^2
-    float2* nodes = win + ((RW2 + 1) & ~1);                        // ntab / 2
 
     const unsigned total = scan[n_sets];
     const unsigned b0 = (unsigned)(((unsigned long long)blockIdx.x * total) / gridDim.x);
@@ -255,10 +348,12 @@ __global__ void __launch_bounds__(kThreads, 3) k_fixup(FixArgs a, const unsigned
     for (int i = threadIdx.x; i < RW; i += kThreads) taps[i] = a.taps[i];
     __syncthreads();
     // window positions: spatial weight and pointer offset from the centre
-    for (int p = threadIdx.x; p < RW2; p += kThreads) {
+    // (zero weight, offset 0 in the padding)
+    for (int p = threadIdx.x; p < RW2p; p += kThreads) {
         const int iy = p / RW, ix = p - iy * RW;
         const int off = (iy - a.R) * (int)a.f_pitch + (ix - a.R);
-        win[p] = make_float2(taps[iy] * taps[ix], __int_as_float(off));
+        woff[p] = p < RW2 ? off : 0;
+        wwt[p] = p < RW2 ? taps[iy] * taps[ix] : 0.f;
     }
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const float full = full_mass(taps, a.R);
@@ -276,69 +371,25 @@ __global__ void __launch_bounds__(kThreads, 3) k_fixup(FixArgs a, const unsigned
         if (s0 >= s1) continue;                        // (uniform) empty set
         const int set = a.set0 + si;
         SetConst sc;
-        Nodes t;
-        load_set(a, set, wk, wkw, nodes, a.ntab / 2, sc, t);   // (its first barrier covers win)
+        Tab t;
+        load_set(a, set, wk, wkw, tab, a.ntab / 4, sc, t);   // (its first barrier covers the window table)
         const unsigned* list = a.list + (size_t)set * a.fix_cap;
         for (unsigned g = s0 + warp; g < s1; g += kWarps) {
             const unsigned idx = list[g - scan[si]];
             const int gy = (int)(idx / (unsigned)a.W), gx = (int)(idx - (unsigned)gy * a.W);
-            const float* fc = a.f + (size_t)gy * a.f_pitch + gx;
-            const float fx = *fc;
-            float ns = 0.f, nc = 0.f, ds = 0.f, dc = 0.f;
-            constexpr int kU = 8;                      // window loads in flight per lane
-            // one neighbour: d = fy - fx = dh + dl exactly, its weight g phi_eps(d)
-            auto pair = [&](float fy, float gw, float& dsum, float& nsum) {
-                const float dh = fy - fx;
-                const float tt = dh - fy;
-                const float dl = (fy - (dh - tt)) + (-fx - tt);
-                const float wgt = gw * phi_eps(dh, dl, t, sc, wk);
-                dsum += wgt;
-                nsum = fmaf(wgt, dh, nsum);
-            };
+            const float fx = a.f[(size_t)gy * a.f_pitch + gx];
             const bool inside = gy >= a.R && gy + a.R < a.H && gx >= a.R && gx + a.R < a.W;
-            if (inside) {
-                // the window lies in the image: positions from the table, no tests
-                for (int p0 = lane; p0 < RW2; p0 += 32 * kU) {
-                    float fv[kU], gv[kU];
-#pragma unroll
-                    for (int u = 0; u < kU; ++u) {
-                        const int p = p0 + 32 * u;
-                        const float2 e = win[min(p, RW2 - 1)];
-                        fv[u] = __ldg(fc + __float_as_int(e.y));
-                        gv[u] = p < RW2 ? e.x : 0.f;
-                    }
-                    // plain sums over the kU terms of this step, compensated across steps
-                    float dsum = 0.f, nsum = 0.f;
-#pragma unroll
-                    for (int u = 0; u < kU; ++u) pair(fv[u], gv[u], dsum, nsum);
-                    comp_add(ds, dc, dsum);
-                    comp_add(ns, nc, nsum);
-                }
-            } else {
-                // near the border: walk the window, neighbours outside the image skipped
-                int iy = lane / RW, ix = lane - (lane / RW) * RW;
-                for (int p0 = lane; p0 < RW2; p0 += 32 * kU) {
-                    float fv[kU], gv[kU];
-#pragma unroll
-                    for (int u = 0; u < kU; ++u) {
-                        const int y = gy + iy - a.R, x = gx + ix - a.R;
-                        const bool in = p0 + 32 * u < RW2 && y >= 0 && y < a.H && x >= 0 &&
-                                        x < a.W;
-                        fv[u] = in ? __ldg(a.f + (size_t)y * a.f_pitch + x) : fx;
-                        gv[u] = in ? taps[min(iy, RW - 1)] * taps[min(ix, RW - 1)] : 0.f;
-                        ix += 32;
-                        while (ix >= RW) {
-                            ix -= RW;
-                            ++iy;
-                        }
-                    }
-                    float dsum = 0.f, nsum = 0.f;
-#pragma unroll
-                    for (int u = 0; u < kU; ++u) pair(fv[u], gv[u], dsum, nsum);
-                    comp_add(ds, dc, dsum);
-                    comp_add(ns, nc, nsum);
-                }
+            float ns, nc, ds, dc;
+            unsigned jmax = 0;
+            bool general = t.J == 0;                   // (uniform)
+            if (!general) {
+                window_sums<false>(a, woff, wwt, RW2p, taps, t, sc, wk, gy, gx, fx, inside, ns, nc, ds,
+                                   dc, jmax);
+                general = __any_sync(0xffffffffu, jmax >= t.J);
             }
+            if (general)                               // a |d| beyond the table: the pair sums
+                window_sums<true>(a, woff, wwt, RW2p, taps, t, sc, wk, gy, gx, fx, inside, ns, nc, ds,
+                                  dc, jmax);
 #pragma unroll
             for (int off = 16; off > 0; off >>= 1) {
                 const float ns2 = __shfl_xor_sync(0xffffffffu, ns, off);
@@ -371,21 +422,21 @@ __global__ void __launch_bounds__(kThreads, 3) k_fixup(FixArgs a, const unsigned
 
 size_t fixup_smem_bytes(int R, int cap_pairs, int ntab)
 {
-    const size_t RW = 2 * (size_t)R + 1;
-    return sizeof(float) * (((RW + 3) & ~(size_t)3) + 2 * (((size_t)cap_pairs + 3) & ~(size_t)3) +
-                            2 * ((RW * RW + 1) & ~(size_t)1) + (size_t)ntab);
+    const size_t RW = 2 * (size_t)R + 1, step = 32 * kU;
+    const size_t RW2p = (RW * RW + step - 1) / step * step;
+    return sizeof(float) * ((size_t)ntab + 2 * RW2p + ((RW + 3) & ~(size_t)3) +
+                            2 * (((size_t)cap_pairs + 3) & ~(size_t)3));
 }
 
-// Node-grid floats for a plan (two per node): enough for every set whose N
-// fits n_cap (T <= pi sigma_r sqrt(N) / 2 and omega_max <= sqrt(N) /
-// sigma_r, with the step at least 0.045 / omega_max, give J <= (pi / 2) N /
-// 0.045 + 2 < 35 N + 2 nodes), but at most kMaxTab floats; sets with more
-// nodes take the direct sums.  With the window table (19 KB at R = 24) and
-// 48 KB of nodes, three CTAs (24 warps) fit an SM.
+// Table floats for a plan (four per entry): enough for every set whose N
+// fits n_cap (T <= pi sigma_r sqrt(N) / 2, S4 < 3 / sigma_r^4 and h above
+// half its bound give J + 1 < 93.4 sqrt(N) + 3 entries), but at most
+// kMaxTab floats; sets with more take the pair sums.  With the window table
+// (20 KB at R = 24) three CTAs (24 warps) fit an SM.
 int fixup_table_entries(int n_cap)
 {
     constexpr long long kMaxTab = 12288;
-    long long want = 2 * (35ll * n_cap + 4);
+    const long long want = 4 * ((long long)(93.5 * sqrt((double)n_cap)) + 4);
     return (int)(want < kMaxTab ? want : kMaxTab);
 }
 

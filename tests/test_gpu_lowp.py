@@ -230,9 +230,9 @@ def test_order_cap_passes_image_through(bf, planes):
 
 
 def test_recheck_direct_sum_fallback(bf):
-    """A set whose phi_eps node grid does not fit the recheck's shared memory
+    """A set whose phi_eps table does not fit the recheck's shared memory
     takes phi_eps from its pair sum for every neighbour: sigma_r = 2.6 gives
-    N = 3315 and about 7500 nodes (6144 fit).  Every FP16 output holds the
+    N = 3315 and 4081 table entries (3072 fit).  Every FP16 output holds the
     0.5 bar, and the rechecked outputs (den under 4 % of the mass) carry the
     FP32 direct sum's error."""
     import torch
@@ -256,3 +256,35 @@ def test_recheck_direct_sum_fallback(bf):
     assert info.n_rechecked > 0 and sel.any()
     assert np.max(err) <= 0.5
     assert np.max(err[sel]) <= 1e-3
+
+
+def test_recheck_beyond_fixed_T(bf):
+    """Fixed T below the image's range: neighbours with |d| > T lie beyond
+    the recheck's phi_eps table (it covers [0, T]), and every output that
+    meets one is redone with the pair sums.  With lowp_recheck = 0.9 nearly
+    every output is listed; those (den under 85 % of the mass) are within
+    1e-3 gray levels of the FP64 oracle with the same (T, N, M), the rest
+    within the FP16 bar."""
+    import torch
+    H, W, ss, sr, eps, tf = 150, 130, 3.0, 20.0, 0.01, 100.0
+    f = (synth.g8(H, W, seed=81).astype(np.float64) * (120.0 / 255.0)).astype(np.float32)
+    p = oracle.resolve(f, ss, sr, eps, t_mode="fixed", t_fixed=tf, rule="alg2")
+    assert np.max(oracle.local_range(f, p.R)) > tf          # some |d| beyond T
+    plan = bf.bf_plan(H, W, ss, sr, eps, t_mode="fixed", t_fixed=tf, trunc_rule="alg2",
+                      plane_dtype="fp16", lowp_recheck=0.9)
+    out = bf.bf_execute(plan, to_dev(f))
+    torch.cuda.synchronize()
+    assert bf.bf_get_device_status(plan) == 0
+    T, N, M = bf.bf_get_sets(plan)
+    assert T[0] == p.T[0, 0] and N[0] == p.N[0, 0] and M[0] == p.M[0, 0]
+    ref, _, den, _ = oracle.shiftable(f, ss, sr, p, return_parts=True)
+    mass = mass_image(H, W, oracle.taps(ss, p.R), p.R)
+    err = np.abs(out.cpu().numpy().astype(np.float64) - ref)
+    info = bf.bf_get_info(plan)
+    sel = den < 0.85 * mass
+    print("fixed T below the range: %d outputs rechecked, max-abs %.3g where den < 85%% of the "
+          "mass (%d), %.3g elsewhere" % (info.n_rechecked, err[sel].max(), int(sel.sum()),
+                                         err[~sel].max() if (~sel).any() else 0.0))
+    assert sel.sum() > H * W // 4 and info.n_rechecked >= sel.sum()
+    assert np.max(err[sel]) <= 1e-3
+    assert np.max(err) <= TOL["fp16"]
