@@ -206,7 +206,7 @@ struct FixArgs {
     unsigned fix_cap;
     unsigned long long* n_guarded;
     int set0;               // first set of the launch
-    int ntab;               // floats of phi_eps nodes a CTA holds (two per node)
+    int ntab;               // floats of phi_eps table a CTA holds (four per interval)
     unsigned* scan;         // n_sets + 1 offsets (scratch)
 };
 int fixup_table_entries(int n_cap);
