@@ -92,21 +92,23 @@ def test_lowp_16bit_image(bf, planes):
     assert err <= 257 * TOL[planes]
 
 
-@pytest.mark.parametrize("mode,tile", [("global", 128), ("tile", 128)])
-def test_tuned_metric_workload_sampled(bf, mode, tile):
+@pytest.mark.parametrize("mode,tile,rule", [("global", 128, "alg2"), ("tile", 128, "alg2"),
+                                            ("tile", 128, "trunc")])
+def test_tuned_metric_workload_sampled(bf, mode, tile, rule):
     """The metric's tuned forms at full size (4096^2 G8, sigma_s = 8,
-    sigma_r = 10, Algorithm 2 with eps = 1e-2, FP16 planes; exact T of the
-    whole image or of each 128 x 128 T-tile): <= 0.5 gray level against the
-    oracle with the same (T, N, M) per tile, at sampled pixels (random,
-    corners, T-tile seams)."""
+    sigma_r = 10, eps = 1e-2 with M by Algorithm 2's bands or by eq. (trunc),
+    FP16 planes; exact T of the whole image or of each 128 x 128 T-tile):
+    <= 0.5 gray level against the oracle with the same (T, N, M) per tile, at
+    sampled pixels (random, corners, T-tile seams)."""
     f = synth.g8(4096, 4096, seed=5)
-    out, p = run(bf, f, 8.0, 10.0, 0.01, "fp16", mode, "alg2", tile)
+    out, p = run(bf, f, 8.0, 10.0, 0.01, "fp16", mode, rule, tile)
     rng = np.random.default_rng(9)
     ys = np.concatenate([rng.integers(0, 4096, 150), [0, 4095, 0, 4095, 127, 128, 2048]])
     xs = np.concatenate([rng.integers(0, 4096, 150), [0, 4095, 4095, 0, 31, 32, 2048]])
     ref = oracle.direct(f, 8.0, 10.0, p, points=(ys, xs))
     err = np.max(np.abs(out[ys, xs] - ref))
-    print("tuned fp16 4096^2 %s: max-abs %.4f gray levels at %d pixels" % (mode, err, ys.size))
+    print("tuned fp16 4096^2 %s %s: max-abs %.4f gray levels at %d pixels" % (
+        mode, rule, err, ys.size))
     assert err <= 0.5
 
 
@@ -118,21 +120,23 @@ def mass_image(H, W, g, R):
     return np.outer(line(H), line(W))
 
 
-@pytest.fixture(scope="module")
-def tuned_4096(bf):
-    """The tuned 4096^2 workload (exact T per 128 x 128 T-tile, Algorithm 2
-    with eps = 1e-2, sigma_s = 8, sigma_r = 10) and the FP64 oracle's output,
-    den and clipped mass at every pixel, with the oracle's own (T, N, M)."""
+@pytest.fixture(scope="module", params=["trunc", "alg2"])
+def tuned_4096(bf, request):
+    """The tuned 4096^2 workload (exact T per 128 x 128 T-tile, eps = 1e-2
+    with M from eq. (trunc), the benchmark's form, or by Algorithm 2's
+    bands, sigma_s = 8, sigma_r = 10) and the FP64 oracle's output, den and
+    clipped mass at every pixel, with the oracle's own (T, N, M)."""
+    rule = request.param
     f = synth.g8(4096, 4096, seed=5)
-    p = oracle.resolve(f, 8.0, 10.0, 0.01, t_mode="tile", t_tile=128, rule="alg2")
+    p = oracle.resolve(f, 8.0, 10.0, 0.01, t_mode="tile", t_tile=128, rule=rule)
     ref, _, den, nfb = oracle.shiftable(f, 8.0, 10.0, p, return_parts=True)
     mass = mass_image(4096, 4096, oracle.taps(8.0, p.R), p.R)
-    return f, p, ref, den, mass, nfb
+    return f, p, ref, den, mass, nfb, rule
 
 
-def run_tuned(bf, f, p, planes="fp16", **kw):
+def run_tuned(bf, f, p, rule, planes="fp16", **kw):
     import torch
-    plan = bf.bf_plan(4096, 4096, 8.0, 10.0, 0.01, t_mode="tile", t_tile=128, trunc_rule="alg2",
+    plan = bf.bf_plan(4096, 4096, 8.0, 10.0, 0.01, t_mode="tile", t_tile=128, trunc_rule=rule,
                       plane_dtype=planes, **kw)
     out = bf.bf_execute(plan, to_dev(f))
     torch.cuda.synchronize()
@@ -167,14 +171,14 @@ def test_tuned_metric_workload_every_pixel(bf, tuned_4096):
     is printed by den / mass band: there the 16-bit rounding of the planes,
     amplified by mass / den, exceeds 0.5 at a few pixels unlike their whole
     window."""
-    f, p, ref, den, mass, nfb = tuned_4096
-    out, info = run_tuned(bf, f, p)
+    f, p, ref, den, mass, nfb, rule = tuned_4096
+    out, info = run_tuned(bf, f, p, rule)
     err = np.abs(out - ref)
-    raw, info0 = run_tuned(bf, f, p, lowp_recheck=0.0)
+    raw, info0 = run_tuned(bf, f, p, rule, lowp_recheck=0.0)
     err0 = np.abs(raw - ref)
-    print("tuned fp16 4096^2, every pixel: max-abs %.4g gray levels (%d outputs rechecked in "
+    print("tuned fp16 4096^2 (M by %s), every pixel: max-abs %.4g gray levels (%d outputs rechecked in "
           "FP32, %d guarded; oracle %d guarded)\n  without the recheck: max-abs %.4g, %d outputs "
-          "above 0.5\n  %s" % (err.max(), info.n_rechecked, info.n_guarded, nfb, err0.max(),
+          "above 0.5\n  %s" % (rule, err.max(), info.n_rechecked, info.n_guarded, nfb, err0.max(),
                                int(np.sum(err0 > 0.5)), error_by_conditioning(err0, den, mass)))
     assert info0.n_rechecked == 0
     assert info.n_rechecked > 0
@@ -187,8 +191,8 @@ def test_recheck_is_fp32_accurate(bf, tuned_4096):
     direct sum's error, not the 16-bit planes': within 1e-3 gray levels of
     the oracle wherever den is under 4 % of the mass (listed by the
     tensor-core pass, whose den is within 2^-9 of the mass of the true one)."""
-    f, p, ref, den, mass, nfb = tuned_4096
-    out, info = run_tuned(bf, f, p)
+    f, p, ref, den, mass, nfb, rule = tuned_4096
+    out, info = run_tuned(bf, f, p, rule)
     sel = den < 0.04 * mass
     err = np.abs(out - ref)[sel]
     print("rechecked outputs: %d with den < 4%% of the mass, max-abs %.3g gray levels "
