@@ -41,8 +41,9 @@
 // One warp per listed pixel (lanes over the (2R+1)^2 window).  The window's
 // positions are a per-CTA table of (g(dy) g(dx), pointer offset dy pitch +
 // dx) as two arrays, padded with zero weights to whole steps of the
-// lanes' loads (the offsets are read to issue the loads, the weights when
-// the terms are summed, so that no weight waits in a register): an
+// lanes' loads (steps of 16 loads per lane, the last one of 8 where that
+// pads less; the offsets are read to issue the loads, the weights when the
+// terms are summed, so that no weight waits in a register): an
 // output whose window lies inside the image reads its neighbours through it
 // with no bounds test; an output near the border walks the window with the
 // bounds tests.  A one-CTA scan turns the per-set list lengths into
@@ -60,7 +61,13 @@ namespace {
 constexpr int kWarps = 8;
 constexpr int kThreads = 32 * kWarps;
 constexpr int kU = 16;               // window loads in flight per lane (inside the image)
-constexpr int kUB = 8;               // the same near the border
+constexpr int kUB = 8;               // the same near the border, and in a last half step
+constexpr int kPad = 32 * kUB;       // the window table's length is a multiple of this
+
+template <int N>
+struct Int {
+    static constexpr int value = N;
+};
 constexpr float kTabTol4 = 3.84e-6f; // 384 * 1e-8: h^4 S4 bound of the node grid
 
 // s + c += v, c collecting the rounding error of each addition (two-sum)
@@ -288,17 +295,22 @@ __device__ __forceinline__ void window_sums(const FixArgs& a, const int* woff, c
     if (inside) {
         // the window lies in the image: positions from the table, no tests
         const float* fc = a.f + (size_t)gy * a.f_pitch + gx;
-        for (int p0 = lane; p0 < RW2p; p0 += 32 * kU) {
-            float fv[kU];
+        // one step of kN positions per lane: plain sums over its terms,
+        // compensated across steps
+        auto step = [&](int p0, auto n_tag) {
+            constexpr int kN = decltype(n_tag)::value;
+            float fv[kN];
 #pragma unroll
-            for (int u = 0; u < kU; ++u) fv[u] = __ldg(fc + woff[p0 + 32 * u]);
-            // plain sums over the kU terms of this step, compensated across steps
+            for (int u = 0; u < kN; ++u) fv[u] = __ldg(fc + woff[p0 + 32 * u]);
             float dsum = 0.f, nsum = 0.f;
 #pragma unroll
-            for (int u = 0; u < kU; ++u) pair(fv[u], wwt[p0 + 32 * u], dsum, nsum);
+            for (int u = 0; u < kN; ++u) pair(fv[u], wwt[p0 + 32 * u], dsum, nsum);
             comp_add(ds, dc, dsum);
             comp_add(ns, nc, nsum);
-        }
+        };
+        int p0 = lane;
+        for (; p0 + 32 * (kU - 1) < RW2p; p0 += 32 * kU) step(p0, Int<kU>{});
+        if (p0 < RW2p) step(p0, Int<kUB>{});          // RW2p a multiple of 32 kUB
     } else {
         // near the border: walk the window, neighbours outside the image skipped
         int iy = lane / RW, ix = lane - (lane / RW) * RW;
@@ -333,7 +345,7 @@ __global__ void __launch_bounds__(kThreads, 3) k_fixup(FixArgs a, const unsigned
 {
     extern __shared__ float4 sm4[];
     const int RW = 2 * a.R + 1, RW2 = RW * RW;
-    const int RW2p = (RW2 + 32 * kU - 1) / (32 * kU) * (32 * kU);
+    const int RW2p = (RW2 + kPad - 1) / kPad * kPad;
     float4* tab = sm4;                                             // ntab / 4
     int* woff = reinterpret_cast<int*>(tab + a.ntab / 4);          // RW2p
     float* wwt = reinterpret_cast<float*>(woff + RW2p);            // RW2p
@@ -422,7 +434,7 @@ __global__ void __launch_bounds__(kThreads, 3) k_fixup(FixArgs a, const unsigned
 
 size_t fixup_smem_bytes(int R, int cap_pairs, int ntab)
 {
-    const size_t RW = 2 * (size_t)R + 1, step = 32 * kU;
+    const size_t RW = 2 * (size_t)R + 1, step = kPad;
     const size_t RW2p = (RW * RW + step - 1) / step * step;
     return sizeof(float) * ((size_t)ntab + 2 * RW2p + ((RW + 3) & ~(size_t)3) +
                             2 * (((size_t)cap_pairs + 3) & ~(size_t)3));
