@@ -64,7 +64,14 @@ enum {
     BF_T_TILE = 2    /* T per t_tile x t_tile block of outputs, own N and M      */
 };
 
-/* Which M (Sec. 3). */
+/* Which M (Sec. 3).  eq. (trunc) is the defining criterion: the smallest M
+ * whose dropped tail mass stays within eps, so it keeps the fewest terms
+ * for a given eps.  Algorithm 2 takes M = 0 above sigma_r = 40, eq. (trunc)
+ * in (10, 40] and the Chernoff estimate of it at sigma_r <= 10, which the
+ * paper prefers there to avoid summing the tail; the estimate keeps more
+ * terms (at 4096^2, sigma_s = 8, sigma_r = 10, per 128 x 128 T-tile: 19.9
+ * against 12.1 on average).  Every rule's weights and M are computed in
+ * FP64 on the device. */
 enum {
     BF_RULE_ALG2 = 0,    /* Algorithm 2 step 4: sigma_r bands (8-bit scale)   */
     BF_RULE_TRUNC = 1,   /* eq. (trunc)                                       */
