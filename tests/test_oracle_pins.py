@@ -130,6 +130,24 @@ def test_p5_trunc_rule_exact(N, eps):
     assert 2 * exact_tail(N, M - 1) <= e
 
 
+def test_p5_trunc_every_order_up_to_300():
+    """eq. (trunc) at eps = 1e-2 for every N = 1..300 (the orders of 8-bit
+    images at sigma_r >= 10, the benchmark's range): M is the smallest index
+    whose running sum passes eps/2, the dropped mass 2 sum_{n<M} w_n is
+    within eps, and no other rule drops more terms -- eq. (Chernoff)'s M and
+    Algorithm 2's (its Chernoff band at sigma_r = 10) are at most eq.
+    (trunc)'s, since each keeps sum_{n<=M} w_n within eps/2."""
+    e = Fraction(1, 100)
+    for N in range(1, 301):
+        M = oracle.trunc_m(N, 0.01)
+        tails = [exact_tail(N, j) for j in range(M + 2)]
+        assert tails[M + 1] > e / 2 or M == N // 2, N
+        assert all(t <= e / 2 for t in tails[:M + 1]) or M == 0, N
+        assert 2 * (tails[M - 1] if M > 0 else 0) <= e, N
+        assert oracle.chernoff_m(N, 0.01) <= M, N
+        assert oracle.alg2_m(N, 10.0, 0.01) <= M, N
+
+
 @pytest.mark.parametrize("N,eps", [(263, 0.005), (264, 0.01), (66, 0.01), (436, 0.05)])
 def test_p5_truncated_kernel_within_eps(N, eps):
     """|phi(s) - phi_eps(s)| <= eps for all s (Sec. 3, after eq. (approx))."""
